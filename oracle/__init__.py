@@ -1,0 +1,309 @@
+"""FP64 CPU oracle for the FLD solver -- TEST INFRASTRUCTURE.
+
+Only `tests/`, `__graft_entry__.smoke()` and the CPU-baseline leg of
+`bench.py` may import this package.  It shares no code with the CUDA path
+(`paper_1403_8105_gb300`), and the CUDA path never imports it.
+
+The arithmetic lives in `fld_oracle.c` (plain C, double precision, written
+from Koerner et al. 2014, Sec. 3-5 and Algorithm 1); this module compiles it
+with gcc on first use and wraps it with numpy arrays.
+
+Array conventions (same as `fld_inputs`): unpadded fields are shape
+(nz, ny, nx); padded fields (phi, D) are shape (nz+2, ny+2, nx+2) with the
+Dirichlet ghost layer on the outside.
+
+Parity notes: every function here follows the paper's formula or algorithm
+step by step; "parity unpinned" items are listed in the design notes (the
+heterogeneous fixed points have no printed values in the paper and are pinned
+only through the tiny-grid brute-force solves, invariants and closed forms in
+`tests/test_oracle_*.py`).
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "fld_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libfld_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+LIMITERS = {"cda": 0, "sum": 1, "max": 2, "kershaw": 3, "larsen": 4, "lp": 5}
+EPS = 1e-20          # epsilon of Eq. 35
+_dp = ctypes.POINTER(ctypes.c_double)
+_fp = ctypes.POINTER(ctypes.c_float)
+
+
+class _Cfg(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("h", ctypes.c_double), ("limiter", ctypes.c_int), ("larsen_n", ctypes.c_double),
+                ("eps", ctypes.c_double), ("jbar", ctypes.c_double), ("omega", ctypes.c_double),
+                ("nthreads", ctypes.c_int), ("local_iters", ctypes.c_int)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (IEEE double, no FMA contraction so the
+    x86 and Arm builds round identically)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fno-fast-math",
+               "-shared", "-fPIC", "-o", tmp, _SRC, "-lpthread", "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            lib.fldo_limiter.restype = ctypes.c_double
+            lib.fldo_limiter.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
+            lib.fldo_prep.restype = None
+            lib.fldo_prep.argtypes = [ctypes.c_long, _fp, _fp, ctypes.c_double, _dp, _dp]
+            lib.fldo_rms.restype = ctypes.c_double
+            lib.fldo_rms.argtypes = [ctypes.c_long, _dp]
+            lib.fldo_rb_iteration.restype = None
+            lib.fldo_rb_iteration.argtypes = [ctypes.POINTER(_Cfg), _dp, _dp, _dp, _dp, _dp]
+            lib.fldo_pass.restype = None
+            lib.fldo_pass.argtypes = [ctypes.POINTER(_Cfg), _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
+            lib.fldo_residual.restype = ctypes.c_double
+            lib.fldo_residual.argtypes = [ctypes.POINTER(_Cfg), _dp, _dp, _dp, _dp, _dp, ctypes.c_int,
+                                          _dp, ctypes.POINTER(ctypes.c_long), _dp]
+            lib.fldo_residual_at.restype = ctypes.c_double
+            lib.fldo_residual_at.argtypes = [ctypes.POINTER(_Cfg), _dp, _dp, _dp, _dp, _dp,
+                                             ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            lib.fldo_solve.restype = ctypes.c_int
+            lib.fldo_solve.argtypes = [ctypes.POINTER(_Cfg), _dp, _dp, _dp, _dp, _dp, ctypes.c_double,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp,
+                                       ctypes.POINTER(ctypes.c_int)]
+            lib.fldo_bake_directional.restype = None
+            lib.fldo_bake_directional.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                                  _fp, _fp, _dp, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.c_int, _dp]
+            lib.fldo_limiter_array.restype = None
+            lib.fldo_limiter_array.argtypes = [ctypes.c_int, ctypes.c_double, _dp, _dp, ctypes.c_long]
+            lib.fldo_flux.restype = None
+            lib.fldo_flux.argtypes = [ctypes.POINTER(_Cfg), _dp, _dp, _dp]
+            lib.fldo_bake_point.restype = None
+            lib.fldo_bake_point.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                            _fp, _fp, _dp, ctypes.c_double, ctypes.c_double,
+                                            ctypes.c_int, _dp]
+            _lib = lib
+    return _lib
+
+
+def _d(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(_dp)
+
+
+def _f(a: np.ndarray):
+    assert a.dtype == np.float32 and a.flags.c_contiguous
+    return a.ctypes.data_as(_fp)
+
+
+def default_threads() -> int:
+    return max(1, os.cpu_count() or 1)
+
+
+# --------------------------------------------------------------------------
+# Limiters (Table 2)
+# --------------------------------------------------------------------------
+
+def limiter(kind: str, R, larsen_n: float = 2.0):
+    """F(R) for one of "cda", "sum", "max", "kershaw", "larsen", "lp"."""
+    lib = _load()
+    k = LIMITERS[kind]
+    Rs = np.ascontiguousarray(R, dtype=np.float64)
+    if Rs.ndim == 0:
+        return float(lib.fldo_limiter(k, float(larsen_n), float(Rs)))
+    out = np.empty_like(Rs)
+    lib.fldo_limiter_array(k, float(larsen_n), _d(Rs), _d(out), Rs.size)
+    return out
+
+
+# --------------------------------------------------------------------------
+# Problem state
+# --------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Problem:
+    """Inputs of Algorithm 1 after its first three steps, plus the state."""
+    nx: int
+    ny: int
+    nz: int
+    h: float
+    sp: np.ndarray      # sigma' = max(sigma_t, sigma_eps), (nz, ny, nx) float64
+    sa: np.ndarray      # sigma_a' = (1 - albedo) sigma'
+    j: np.ndarray       # emission incl. q_ri
+    jbar: float
+    limiter: str = "lp"
+    larsen_n: float = 2.0
+    omega: float = 1.0
+    eps: float = EPS
+    phi: np.ndarray | None = None   # padded
+    D: np.ndarray | None = None     # padded
+    nthreads: int = 1
+    local_iters: int = 1
+
+    def cfg(self) -> _Cfg:
+        return _Cfg(self.nx, self.ny, self.nz, float(self.h), LIMITERS[self.limiter], float(self.larsen_n),
+                    float(self.eps), float(self.jbar), float(self.omega), int(self.nthreads),
+                    int(self.local_iters))
+
+
+def sigma_eps_default(nx: int, ny: int, nz: int, h: float) -> float:
+    """sigma_eps = 1e-3 / L with L the largest grid extent (Sec. 5)."""
+    return 1e-3 / (max(nx, ny, nz) * h)
+
+
+def omega_default(nx: int, ny: int, nz: int) -> float:
+    """SOR factor used when none is given: the Laplacian estimate
+    2 / (1 + sin(pi / (n + 1))) for the largest extent n, clamped to
+    [1, 1.95].  The paper only requires 0 < omega < 2 (Eq. 36)."""
+    n = max(nx, ny, nz)
+    w = 2.0 / (1.0 + np.sin(np.pi / (n + 1)))
+    return float(min(1.95, max(1.0, w)))
+
+
+def make_problem(sigma_t: np.ndarray, albedo: np.ndarray, j: np.ndarray, h: float, *,
+                 limiter: str = "lp", larsen_n: float = 2.0, omega: float | None = None,
+                 sigma_eps: float | None = None, eps: float = EPS, nthreads: int | None = None,
+                 local_iters: int = 1) -> Problem:
+    """Algorithm 1, first three steps: floor sigma, compute sigma_a' and jbar."""
+    lib = _load()
+    sigma_t = np.ascontiguousarray(sigma_t, dtype=np.float32)
+    albedo = np.ascontiguousarray(albedo, dtype=np.float32)
+    nz, ny, nx = sigma_t.shape
+    if sigma_eps is None:
+        sigma_eps = sigma_eps_default(nx, ny, nz, h)
+    sp = np.empty(sigma_t.shape, dtype=np.float64)
+    sa = np.empty(sigma_t.shape, dtype=np.float64)
+    lib.fldo_prep(sigma_t.size, _f(sigma_t), _f(albedo), float(sigma_eps), _d(sp), _d(sa))
+    jd = np.ascontiguousarray(j, dtype=np.float64)
+    jbar = lib.fldo_rms(jd.size, _d(jd))
+    if omega is None:
+        omega = omega_default(nx, ny, nz)
+    return Problem(nx, ny, nz, float(h), sp, sa, jd, float(jbar), limiter, larsen_n, float(omega), eps,
+                   None, None, nthreads or default_threads(), int(local_iters))
+
+
+def init_state(p: Problem, phi0: float | None = None, D0: float | None = None,
+               phi_b: float | None = None, D_b: float | None = None) -> None:
+    """Algorithm 1 initialisation: phi = eps*jbar*dl, D = eps*dl everywhere,
+    including the Dirichlet ghost layer, unless values are given."""
+    pd = p.eps * p.jbar * p.h
+    dd = p.eps * p.h
+    shape = (p.nz + 2, p.ny + 2, p.nx + 2)
+    p.phi = np.full(shape, pd if phi_b is None else phi_b, dtype=np.float64)
+    p.D = np.full(shape, dd if D_b is None else D_b, dtype=np.float64)
+    p.phi[1:-1, 1:-1, 1:-1] = pd if phi0 is None else phi0
+    p.D[1:-1, 1:-1, 1:-1] = dd if D0 is None else D0
+
+
+def rb_iteration(p: Problem, iters: int = 1) -> None:
+    lib = _load()
+    c = p.cfg()
+    for _ in range(iters):
+        lib.fldo_rb_iteration(ctypes.byref(c), _d(p.sp), _d(p.sa), _d(p.j), _d(p.phi), _d(p.D))
+
+
+def colour_pass(p: Problem, colour: int) -> None:
+    lib = _load()
+    c = p.cfg()
+    lib.fldo_pass(ctypes.byref(c), _d(p.sp), _d(p.sa), _d(p.j), _d(p.phi), _d(p.D), int(colour))
+
+
+def residual(p: Problem, phi: np.ndarray | None = None, margin: int = 0, field: bool = False):
+    """Relative residual Rbar/jbar with D recomputed from phi (Eq. 37).
+
+    Returns (rel, sum_R2, count[, R field])."""
+    lib = _load()
+    c = p.cfg()
+    ph = p.phi if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
+    s = ctypes.c_double(0.0)
+    cnt = ctypes.c_long(0)
+    R = np.empty((p.nz, p.ny, p.nx), dtype=np.float64) if field else None
+    rel = lib.fldo_residual(ctypes.byref(c), _d(p.sp), _d(p.sa), _d(p.j), _d(ph), _d(p.D), int(margin),
+                            ctypes.byref(s), ctypes.byref(cnt), _d(R) if field else None)
+    if field:
+        return rel, s.value, cnt.value, R
+    return rel, s.value, cnt.value
+
+
+def residual_at(p: Problem, phi: np.ndarray, i: int, j: int, k: int) -> float:
+    """R_p at one unknown with D recomputed locally (Eq. 37)."""
+    lib = _load()
+    c = p.cfg()
+    ph = np.ascontiguousarray(phi, dtype=np.float64)
+    return lib.fldo_residual_at(ctypes.byref(c), _d(p.sp), _d(p.sa), _d(p.j), _d(ph), _d(p.D),
+                                int(i), int(j), int(k))
+
+
+def solve(p: Problem, tol: float = 1e-10, max_iters: int = 100000, check_every: int = 10,
+          margin: int = 0):
+    """Algorithm 1 until Rbar/jbar <= tol.  Returns (iterations, rel, history)."""
+    lib = _load()
+    c = p.cfg()
+    nh_max = max_iters // max(1, check_every) + 2
+    hist = np.zeros(nh_max, dtype=np.float64)
+    rel = ctypes.c_double(0.0)
+    nh = ctypes.c_int(0)
+    it = lib.fldo_solve(ctypes.byref(c), _d(p.sp), _d(p.sa), _d(p.j), _d(p.phi), _d(p.D), float(tol),
+                        int(max_iters), int(check_every), int(margin), ctypes.byref(rel), _d(hist),
+                        ctypes.byref(nh))
+    return it, rel.value, hist[: nh.value].copy()
+
+
+# --------------------------------------------------------------------------
+# Single-scatter source (Sec. 3 after Eq. 6; Sec. 6.2)
+# --------------------------------------------------------------------------
+
+def bake_directional(sigma_t: np.ndarray, albedo: np.ndarray, h: float, direction=(0.0, 0.0, -1.0),
+                     radiance: float = 1.0, step: float | None = None, nthreads: int | None = None):
+    """q_ri = L sigma_s T for a directional light travelling along `direction`."""
+    lib = _load()
+    sigma_t = np.ascontiguousarray(sigma_t, dtype=np.float32)
+    albedo = np.ascontiguousarray(albedo, dtype=np.float32)
+    nz, ny, nx = sigma_t.shape
+    q = np.empty(sigma_t.shape, dtype=np.float64)
+    d = np.asarray(direction, dtype=np.float64)
+    lib.fldo_bake_directional(nx, ny, nz, float(h), _f(sigma_t), _f(albedo), _d(d), float(radiance),
+                              float(0.5 * h if step is None else step), int(nthreads or default_threads()),
+                              _d(q))
+    return q
+
+
+def bake_point(sigma_t: np.ndarray, albedo: np.ndarray, h: float, pos, power: float = 1.0,
+               step: float | None = None, nthreads: int | None = None):
+    """q_ri = P sigma_s T / (4 pi max(r, h/2)^2) for a point light at `pos`."""
+    lib = _load()
+    sigma_t = np.ascontiguousarray(sigma_t, dtype=np.float32)
+    albedo = np.ascontiguousarray(albedo, dtype=np.float32)
+    nz, ny, nx = sigma_t.shape
+    q = np.empty(sigma_t.shape, dtype=np.float64)
+    pp = np.asarray(pos, dtype=np.float64)
+    lib.fldo_bake_point(nx, ny, nz, float(h), _f(sigma_t), _f(albedo), _d(pp), float(power),
+                        float(0.5 * h if step is None else step), int(nthreads or default_threads()), _d(q))
+    return q
+
+
+def flux_magnitude(p: Problem, phi: np.ndarray | None = None) -> np.ndarray:
+    """|E_p| = D_p |grad phi_p| with D_p recomputed from phi (Eq. 15, 33-35),
+    for the flux-limiting constraint |E| <= phi (Eq. 14)."""
+    lib = _load()
+    c = p.cfg()
+    ph = p.phi if phi is None else np.ascontiguousarray(phi, dtype=np.float64)
+    E = np.empty((p.nz, p.ny, p.nx), dtype=np.float64)
+    lib.fldo_flux(ctypes.byref(c), _d(p.sp), _d(ph), _d(E))
+    return E
