@@ -1,0 +1,206 @@
+/*
+ * fld.h -- C ABI of the GB300 flux-limited diffusion (FLD) solver.
+ *
+ * The library solves the discretised flux-limited diffusion equation of
+ * Koerner et al., "Flux-Limited Diffusion for Multiple Scattering in
+ * Participating Media" (CGF 33(2), 2014), Sec. 5:
+ *
+ *   [sum_s D_ps phi_s - phi_p sum_s D_ps] / dl^2 = (1 - albedo_p) sigma_p phi_p - j_p   (Eq. 31)
+ *
+ * over the unknown voxels p of a uniform grid, with the six face neighbours
+ * s, D_ps = (D_p + D_s)/2, and the flux-limited coefficient
+ * D_p = F(R_p) / max(sigma_p, sigma_eps) (Eq. 33) evaluated from the floored
+ * Knudsen number of Eq. 35 and a limiter of Table 2.  The solve is the
+ * red-black Gauss-Seidel relaxation with over-relaxation of Algorithm 1.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid      nx x ny x nz unknown voxels of edge h (the paper's dl), voxel
+ *           (i, j, k) centred at ((i+1/2)h, (j+1/2)h, (k+1/2)h).  A one-voxel
+ *           ghost layer outside the unknowns holds the Dirichlet boundary
+ *           values of phi and D; it is never updated by a sweep.
+ * Layout    Unpadded fields: nx*ny*nz values, x fastest
+ *           (index (k*ny + j)*nx + i).  Padded fields (phi, D incl. ghosts):
+ *           (nx+2)*(ny+2)*(nz+2) values, x fastest, unknown (i,j,k) at
+ *           ((k+1)*(ny+2) + j+1)*(nx+2) + i+1.
+ * Memory    `where` selects FLD_MEM_HOST (ordinary host memory) or
+ *           FLD_MEM_DEVICE (memory of the grid's GPU).  Input pointers are
+ *           borrowed for the duration of the call only: the library copies
+ *           or converts what it needs.  Output pointers must hold the stated
+ *           number of values.
+ * Ownership A grid owns all device memory it allocates; fld_destroy frees it.
+ * Streams   All device work of a grid is ordered on the stream given at
+ *           creation (a cudaStream_t passed as void*; NULL = a stream the
+ *           library creates and owns).  Calls that return host results
+ *           (fld_solve, fld_residual, fld_get_* to host memory) synchronise
+ *           that stream; the others only enqueue work.
+ * Errors    Every call returns an fld_status; nothing is thrown across the
+ *           ABI.  fld_last_error() gives a thread-local text for the last
+ *           failure on the calling thread.  A CUDA error is reported as
+ *           FLD_ERR_CUDA and leaves the grid usable only for fld_destroy.
+ * Threads   A grid must not be used from two threads at once.
+ */
+#ifndef FLD_H
+#define FLD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fld_grid_s *fld_grid;
+
+typedef enum {
+    FLD_OK = 0,
+    FLD_ERR_INVALID_ARG = 1,   /* bad size, pointer, parameter or input value   */
+    FLD_ERR_OOM = 2,           /* device or host allocation failed              */
+    FLD_ERR_CUDA = 3,          /* a CUDA call failed                            */
+    FLD_ERR_STATE = 4,         /* call order: e.g. solve before set_medium      */
+    FLD_ERR_NOT_CONVERGED = 5, /* max_iters reached; result still filled        */
+    FLD_ERR_DIVERGED = 6,      /* residual became NaN or infinite               */
+    FLD_ERR_NO_DEVICE = 7      /* no CUDA device / extension unusable           */
+} fld_status;
+
+/* Flux limiters F(R), Table 2 of the paper, plus the CDA constant 1/3. */
+typedef enum {
+    FLD_LIM_CDA = 0,      /* F = 1/3 (classical diffusion)            */
+    FLD_LIM_SUM = 1,      /* F = 1/(3 + R)                            */
+    FLD_LIM_MAX = 2,      /* F = 1/max(3, R)                          */
+    FLD_LIM_KERSHAW = 3,  /* F = 2/(3 + sqrt(9 + 4 R^2))              */
+    FLD_LIM_LARSEN = 4,   /* F = (3^n + R^n)^(-1/n)                   */
+    FLD_LIM_LP = 5        /* F = (coth R - 1/R)/R  Levermore-Pomraning */
+} fld_limiter;
+
+typedef enum { FLD_MEM_HOST = 0, FLD_MEM_DEVICE = 1 } fld_mem;
+
+/* Arithmetic of the sweeps.
+ * FP64  : phi, D and the medium in double precision throughout.
+ * FP32  : phi, D and the medium in single precision; the residual check is
+ *         evaluated with a double-single (float-float) sum so it is not
+ *         limited by cancellation.
+ * MIXED : single-precision sweeps until the residual stalls or falls below
+ *         fp32_switch, then correction sweeps that keep phi as a
+ *         float-float pair (about 44 significant bits) and form each update
+ *         from an accurately summed residual; reaches residuals far below
+ *         the single-precision floor (Sec. 6.2 notes 1e-4 as the practical
+ *         single-precision limit). */
+typedef enum { FLD_PREC_FP64 = 0, FLD_PREC_FP32 = 1, FLD_PREC_MIXED = 2 } fld_precision;
+
+typedef struct {
+    int limiter;          /* fld_limiter                                             */
+    double larsen_n;      /* n of Larsen-n, > 0 (default 2)                          */
+    double omega;         /* SOR factor of Eq. 36, 0 < omega < 2; <= 0 selects
+                             2/(1 + sin(pi/(n+1))) clamped to [1, 1.9], n the
+                             largest extent                                          */
+    int local_iters;      /* rounds of Knudsen -> D_p -> phi' per point before the
+                             SOR blend, >= 1.  1 is Algorithm 1 as printed; 2 makes
+                             each point's update self-consistent in its own D_p,
+                             which keeps over-relaxation stable next to vacuum.  The
+                             fixed point is the same.                                */
+    double tol;           /* stop when Rbar / jbar <= tol (Algorithm 1: 1e-6)        */
+    int max_iters;        /* iteration cap (one iteration = red + black pass)        */
+    int check_every;      /* iterations between residual evaluations, >= 1           */
+    double sigma_eps;     /* extinction floor; <= 0 selects 1e-3 / L, L the largest
+                             grid extent (Sec. 5)                                    */
+    double eps;           /* epsilon of Eq. 35; <= 0 selects 1e-20                   */
+    int precision;        /* fld_precision                                           */
+    double fp32_switch;   /* MIXED only: residual at which correction sweeps begin;
+                             <= 0 selects 2e-5                                       */
+    int residual_margin;  /* residual RMS taken over unknowns at least this many
+                             voxels from the faces (Sec. 5); default 0              */
+    int warm_start;       /* 1: keep the grid's current phi and D (from a previous
+                             solve or fld_set_state); 0: initialise them            */
+    double phi0, D0;      /* initial phi and D of the unknowns; < 0 selects the
+                             paper's eps*jbar*h and eps*h (Algorithm 1)             */
+    double phi_b, D_b;    /* Dirichlet ghost values; < 0 selects eps*jbar*h and
+                             eps*h                                                   */
+} fld_solve_params;
+
+typedef struct {
+    int status;            /* fld_status of the solve                               */
+    int iterations;        /* total iterations                                      */
+    int iterations_fp32;   /* of which single-precision sweeps (FP32 / MIXED)       */
+    int iterations_corr;   /* of which float-float correction sweeps (MIXED)        */
+    int checks;            /* residual evaluations                                  */
+    double rel_residual;   /* last Rbar / jbar                                      */
+    double jbar;           /* RMS emission over the unknowns                        */
+    double omega;          /* SOR factor used                                       */
+    double ms;             /* device time of the solve, CUDA events                 */
+} fld_solve_result;
+
+/* Fill *p with the defaults: LP limiter, Larsen n = 2, omega auto,
+ * local_iters 2, tol 1e-6, max_iters 1000000, check_every 64, paper sigma_eps
+ * and eps, MIXED precision, margin 0, cold start, paper initial/ghost values. */
+void fld_default_params(fld_solve_params *p);
+
+/* Create a grid of nx*ny*nz unknowns (each >= 1) of edge h > 0 on the
+ * current CUDA device.  stream: cudaStream_t or NULL.  *out receives the
+ * handle.  Allocates the solver fields on the device (about 40 bytes per
+ * voxel; FP64 fields are added on first FP64 use). */
+fld_status fld_create_grid(int nx, int ny, int nz, double h, void *stream, fld_grid *out);
+
+/* Medium: extinction sigma_t >= 0 and albedo in [0, 1] (unpadded, float).
+ * Values are validated (NaN, negative sigma, albedo outside [0,1] ->
+ * FLD_ERR_INVALID_ARG).  The floor sigma' = max(sigma_t, sigma_eps) and
+ * sigma_a' = (1 - albedo) sigma' of Algorithm 1 are formed at solve time. */
+fld_status fld_set_medium(fld_grid g, const float *sigma_t, const float *albedo, int where);
+
+/* Emission j >= 0 (unpadded, float): the j_p of Sec. 5, into which the
+ * single-scatter source is absorbed.  Replaces the grid's source field. */
+fld_status fld_set_source(fld_grid g, const float *j, int where);
+
+/* Copy the grid's source field (after any bake) to j (unpadded, float). */
+fld_status fld_get_source(fld_grid g, float *j, int where);
+
+/* Single-scatter source of a directional light (Sec. 3, after Eq. 6):
+ * q_ri = L sigma_s T with sigma_s = albedo * sigma_t and T the transmittance
+ * towards the light (Eq. 3) marched from each voxel centre with step `step`
+ * (<= 0 selects h/2).  dir is the direction the light travels (need not be
+ * unit length, not zero).  Light along -z takes an exact column-scan path.
+ * accumulate = 0 replaces the source field with q_ri, 1 adds q_ri to it.
+ * Needs fld_set_medium. */
+fld_status fld_bake_directional(fld_grid g, const double dir[3], double radiance, double step,
+                                int accumulate);
+
+/* Single-scatter source of an isotropic point light of power P at pos (world
+ * units, may lie outside the grid): q_ri = P sigma_s T / (4 pi max(r, h/2)^2),
+ * T marched from the voxel centre towards the light up to the grid boundary. */
+fld_status fld_bake_point(fld_grid g, const double pos[3], double power, double step,
+                          int accumulate);
+
+/* Set phi and/or D (padded, double; either may be NULL) including the ghost
+ * layer, e.g. analytic Dirichlet values or a warm start.  Allocates the FP64
+ * fields on first use so that an FP64 continuation keeps the values exactly. */
+fld_status fld_set_state(fld_grid g, const double *phi, const double *D, int where);
+
+/* Read phi and/or D (padded, double; either may be NULL) of the current state. */
+fld_status fld_get_state(fld_grid g, double *phi, double *D, int where);
+
+/* Run `iterations` red-black iterations (Algorithm 1) with the given
+ * parameters and no residual checks.  Initialises phi and D first unless
+ * p->warm_start.  Enqueues only. */
+fld_status fld_iterate(fld_grid g, const fld_solve_params *p, int iterations);
+
+/* Solve until Rbar/jbar <= p->tol or p->max_iters (Algorithm 1), checking the
+ * residual every p->check_every iterations.  r (may be NULL) receives the
+ * outcome.  Returns FLD_OK, FLD_ERR_NOT_CONVERGED or FLD_ERR_DIVERGED (r
+ * filled in every case), or an error. */
+fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r);
+
+/* Relative residual Rbar/jbar of the current phi (Eq. 37 with D recomputed
+ * from phi, RMS over the unknowns beyond p->residual_margin), evaluated in
+ * the arithmetic of p->precision with an accurate sum.  Synchronises. */
+fld_status fld_residual(fld_grid g, const fld_solve_params *p, double *rel);
+
+/* Free the grid and everything it owns (NULL is ignored). */
+void fld_destroy(fld_grid g);
+
+/* Static text for a status code. */
+const char *fld_status_string(fld_status s);
+
+/* Thread-local description of the last failure on this thread ("" if none). */
+const char *fld_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FLD_H */

@@ -1,0 +1,327 @@
+"""Python binding of the GB300 FLD solver library (argument marshalling only).
+
+Every function here forwards to the C ABI declared in ``include/fld.h``, with
+the same name; all computation runs in the CUDA kernels of
+``libfld_gb300.so``.  There is no CPU fallback: if the library cannot be
+loaded, or no GPU is present, the calls raise.
+
+Arrays may be numpy arrays (host memory) or torch tensors (host or CUDA
+memory); CUDA tensors are passed to the library as device pointers.
+Unpadded fields are float32 of shape (nz, ny, nx); padded state fields
+(phi, D) are float64 of shape (nz+2, ny+2, nx+2).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "FLD_OK", "FLD_ERR_INVALID_ARG", "FLD_ERR_OOM", "FLD_ERR_CUDA", "FLD_ERR_STATE",
+    "FLD_ERR_NOT_CONVERGED", "FLD_ERR_DIVERGED", "FLD_ERR_NO_DEVICE",
+    "LIMITERS", "PRECISIONS", "FldError", "SolveParams", "SolveResult",
+    "load", "library_path", "fld_default_params", "fld_create_grid", "fld_set_medium", "fld_set_source",
+    "fld_get_source", "fld_bake_directional", "fld_bake_point", "fld_set_state", "fld_get_state",
+    "fld_iterate", "fld_solve", "fld_residual", "fld_destroy", "fld_status_string", "fld_last_error",
+    "Grid", "params",
+]
+
+FLD_OK, FLD_ERR_INVALID_ARG, FLD_ERR_OOM, FLD_ERR_CUDA, FLD_ERR_STATE = 0, 1, 2, 3, 4
+FLD_ERR_NOT_CONVERGED, FLD_ERR_DIVERGED, FLD_ERR_NO_DEVICE = 5, 6, 7
+FLD_MEM_HOST, FLD_MEM_DEVICE = 0, 1
+LIMITERS = {"cda": 0, "sum": 1, "max": 2, "kershaw": 3, "larsen": 4, "lp": 5}
+PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2}
+
+
+class SolveParams(ctypes.Structure):
+    """Mirror of fld_solve_params (fld.h)."""
+    _fields_ = [
+        ("limiter", ctypes.c_int), ("larsen_n", ctypes.c_double), ("omega", ctypes.c_double),
+        ("local_iters", ctypes.c_int), ("tol", ctypes.c_double), ("max_iters", ctypes.c_int),
+        ("check_every", ctypes.c_int), ("sigma_eps", ctypes.c_double), ("eps", ctypes.c_double),
+        ("precision", ctypes.c_int), ("fp32_switch", ctypes.c_double), ("residual_margin", ctypes.c_int),
+        ("warm_start", ctypes.c_int), ("phi0", ctypes.c_double), ("D0", ctypes.c_double),
+        ("phi_b", ctypes.c_double), ("D_b", ctypes.c_double),
+    ]
+
+
+class SolveResult(ctypes.Structure):
+    """Mirror of fld_solve_result (fld.h)."""
+    _fields_ = [
+        ("status", ctypes.c_int), ("iterations", ctypes.c_int), ("iterations_fp32", ctypes.c_int),
+        ("iterations_corr", ctypes.c_int), ("checks", ctypes.c_int), ("rel_residual", ctypes.c_double),
+        ("jbar", ctypes.c_double), ("omega", ctypes.c_double), ("ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class FldError(RuntimeError):
+    def __init__(self, status: int, func: str, detail: str):
+        self.status = status
+        super().__init__(f"{func}: {_STATUS_NAMES.get(status, status)}: {detail}")
+
+
+_STATUS_NAMES = {0: "FLD_OK", 1: "FLD_ERR_INVALID_ARG", 2: "FLD_ERR_OOM", 3: "FLD_ERR_CUDA",
+                 4: "FLD_ERR_STATE", 5: "FLD_ERR_NOT_CONVERGED", 6: "FLD_ERR_DIVERGED", 7: "FLD_ERR_NO_DEVICE"}
+
+_lib = None
+_lock = threading.Lock()
+_vp = ctypes.c_void_p
+_dp3 = ctypes.c_double * 3
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libfld_gb300.so (building it with nvcc if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"FLD CUDA library not built: {path}")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        c_int, c_double = ctypes.c_int, ctypes.c_double
+        P, R = ctypes.POINTER(SolveParams), ctypes.POINTER(SolveResult)
+        sig = {
+            "fld_default_params": (None, [P]),
+            "fld_create_grid": (c_int, [c_int, c_int, c_int, c_double, _vp, ctypes.POINTER(_vp)]),
+            "fld_set_medium": (c_int, [_vp, _vp, _vp, c_int]),
+            "fld_set_source": (c_int, [_vp, _vp, c_int]),
+            "fld_get_source": (c_int, [_vp, _vp, c_int]),
+            "fld_bake_directional": (c_int, [_vp, _dp3, c_double, c_double, c_int]),
+            "fld_bake_point": (c_int, [_vp, _dp3, c_double, c_double, c_int]),
+            "fld_set_state": (c_int, [_vp, _vp, _vp, c_int]),
+            "fld_get_state": (c_int, [_vp, _vp, _vp, c_int]),
+            "fld_iterate": (c_int, [_vp, P, c_int]),
+            "fld_solve": (c_int, [_vp, P, R]),
+            "fld_residual": (c_int, [_vp, P, ctypes.POINTER(c_double)]),
+            "fld_destroy": (None, [_vp]),
+            "fld_status_string": (ctypes.c_char_p, [c_int]),
+            "fld_last_error": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(status: int, func: str, allow=(FLD_OK,)):
+    if status not in allow:
+        raise FldError(status, func, fld_last_error())
+    return status
+
+
+def _ptr(a, dtype):
+    """(pointer, where, keepalive) of a numpy array or torch tensor."""
+    try:
+        import torch  # noqa: F401
+        is_tensor = type(a).__module__.startswith("torch")
+    except ImportError:  # pragma: no cover
+        is_tensor = False
+    if is_tensor:
+        import torch
+        want = {np.float32: torch.float32, np.float64: torch.float64}[dtype]
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"expected a contiguous {want} tensor")
+        return ctypes.c_void_p(a.data_ptr()), (FLD_MEM_DEVICE if a.is_cuda else FLD_MEM_HOST), a
+    arr = np.ascontiguousarray(a, dtype=dtype)
+    return ctypes.c_void_p(arr.ctypes.data), FLD_MEM_HOST, arr
+
+
+# ---------------------------------------------------------------------------
+# The ABI, one wrapper per entry point
+# ---------------------------------------------------------------------------
+
+def fld_default_params() -> SolveParams:
+    p = SolveParams()
+    load().fld_default_params(ctypes.byref(p))
+    return p
+
+
+def fld_status_string(status: int) -> str:
+    return load().fld_status_string(int(status)).decode()
+
+
+def fld_last_error() -> str:
+    return load().fld_last_error().decode()
+
+
+def fld_create_grid(nx: int, ny: int, nz: int, h: float, stream=None) -> ctypes.c_void_p:
+    out = _vp()
+    s = None if stream is None else _vp(int(stream))
+    _check(load().fld_create_grid(int(nx), int(ny), int(nz), float(h), s, ctypes.byref(out)), "fld_create_grid")
+    return out
+
+
+def fld_set_medium(g, sigma_t, albedo) -> None:
+    ps, w1, k1 = _ptr(sigma_t, np.float32)
+    pa, w2, k2 = _ptr(albedo, np.float32)
+    if w1 != w2:
+        raise ValueError("sigma_t and albedo must live in the same kind of memory")
+    _check(load().fld_set_medium(g, ps, pa, w1), "fld_set_medium")
+
+
+def fld_set_source(g, j) -> None:
+    pj, w, k = _ptr(j, np.float32)
+    _check(load().fld_set_source(g, pj, w), "fld_set_source")
+
+
+def fld_get_source(g, out) -> None:
+    pj, w, k = _ptr(out, np.float32)
+    _check(load().fld_get_source(g, pj, w), "fld_get_source")
+
+
+def fld_bake_directional(g, direction, radiance: float = 1.0, step: float = 0.0, accumulate: int = 0) -> None:
+    _check(load().fld_bake_directional(g, _dp3(*map(float, direction)), float(radiance), float(step),
+                                       int(accumulate)), "fld_bake_directional")
+
+
+def fld_bake_point(g, pos, power: float = 1.0, step: float = 0.0, accumulate: int = 0) -> None:
+    _check(load().fld_bake_point(g, _dp3(*map(float, pos)), float(power), float(step), int(accumulate)),
+           "fld_bake_point")
+
+
+def fld_set_state(g, phi=None, D=None) -> None:
+    pp, w1, k1 = _ptr(phi, np.float64) if phi is not None else (None, None, None)
+    pd, w2, k2 = _ptr(D, np.float64) if D is not None else (None, None, None)
+    ws = {w for w in (w1, w2) if w is not None}
+    if len(ws) > 1:
+        raise ValueError("phi and D must live in the same kind of memory")
+    _check(load().fld_set_state(g, pp, pd, ws.pop() if ws else FLD_MEM_HOST), "fld_set_state")
+
+
+def fld_get_state(g, phi=None, D=None) -> None:
+    pp, w1, k1 = _ptr(phi, np.float64) if phi is not None else (None, None, None)
+    pd, w2, k2 = _ptr(D, np.float64) if D is not None else (None, None, None)
+    if phi is not None and w1 == FLD_MEM_HOST and not isinstance(phi, np.ndarray):
+        raise TypeError("host outputs must be numpy arrays or CPU tensors")
+    ws = {w for w in (w1, w2) if w is not None}
+    if len(ws) > 1:
+        raise ValueError("phi and D must live in the same kind of memory")
+    _check(load().fld_get_state(g, pp, pd, ws.pop() if ws else FLD_MEM_HOST), "fld_get_state")
+    for out, keep in ((phi, k1), (D, k2)):
+        if out is not None and isinstance(out, np.ndarray) and keep is not out:
+            out[...] = keep
+
+
+def fld_iterate(g, p: SolveParams, iterations: int) -> None:
+    _check(load().fld_iterate(g, ctypes.byref(p), int(iterations)), "fld_iterate")
+
+
+def fld_solve(g, p: SolveParams, check: bool = True) -> SolveResult:
+    r = SolveResult()
+    st = load().fld_solve(g, ctypes.byref(p), ctypes.byref(r))
+    if check:
+        _check(st, "fld_solve", allow=(FLD_OK, FLD_ERR_NOT_CONVERGED, FLD_ERR_DIVERGED))
+    r.status = st
+    return r
+
+
+def fld_residual(g, p: SolveParams) -> float:
+    rel = ctypes.c_double(0.0)
+    _check(load().fld_residual(g, ctypes.byref(p), ctypes.byref(rel)), "fld_residual")
+    return rel.value
+
+
+def fld_destroy(g) -> None:
+    if g:
+        load().fld_destroy(g)
+
+
+# ---------------------------------------------------------------------------
+# Convenience
+# ---------------------------------------------------------------------------
+
+def params(**kw) -> SolveParams:
+    """fld_default_params() with fields overridden by keyword; `limiter` and
+    `precision` also accept their names ("lp", "mixed", ...)."""
+    p = fld_default_params()
+    for k, v in kw.items():
+        if k == "limiter" and isinstance(v, str):
+            v = LIMITERS[v]
+        if k == "precision" and isinstance(v, str):
+            v = PRECISIONS[v]
+        if not hasattr(p, k):
+            raise AttributeError(f"SolveParams has no field {k!r}")
+        setattr(p, k, v)
+    return p
+
+
+class Grid:
+    """Owning wrapper of an fld_grid handle."""
+
+    def __init__(self, nx: int, ny: int, nz: int, h: float, stream=None):
+        self.shape = (nz, ny, nx)
+        self.h = h
+        self.handle = fld_create_grid(nx, ny, nz, h, stream)
+
+    def close(self):
+        if self.handle:
+            fld_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def padded_shape(self):
+        nz, ny, nx = self.shape
+        return (nz + 2, ny + 2, nx + 2)
+
+    def set_medium(self, sigma_t, albedo):
+        fld_set_medium(self.handle, sigma_t, albedo)
+
+    def set_source(self, j):
+        fld_set_source(self.handle, j)
+
+    def get_source(self):
+        out = np.empty(self.shape, np.float32)
+        fld_get_source(self.handle, out)
+        return out
+
+    def bake_directional(self, direction=(0.0, 0.0, -1.0), radiance=1.0, step=0.0, accumulate=0):
+        fld_bake_directional(self.handle, direction, radiance, step, accumulate)
+
+    def bake_point(self, pos, power=1.0, step=0.0, accumulate=0):
+        fld_bake_point(self.handle, pos, power, step, accumulate)
+
+    def set_state(self, phi=None, D=None):
+        fld_set_state(self.handle, phi, D)
+
+    def get_state(self):
+        phi = np.empty(self.padded_shape, np.float64)
+        D = np.empty(self.padded_shape, np.float64)
+        fld_get_state(self.handle, phi, D)
+        return phi, D
+
+    def iterate(self, p: SolveParams, iterations: int):
+        fld_iterate(self.handle, p, iterations)
+
+    def solve(self, p: SolveParams, check: bool = True) -> SolveResult:
+        return fld_solve(self.handle, p, check)
+
+    def residual(self, p: SolveParams) -> float:
+        return fld_residual(self.handle, p)

@@ -1,0 +1,703 @@
+// fld_capi.cu -- host side of the GB300 FLD solver: the grid object, the
+// solve loop of Algorithm 1 (Koerner et al. 2014) and the C ABI of fld.h.
+//
+// Each block of `check_every` red-black iterations is captured once into a
+// CUDA graph and replayed, so the host issues one launch per block instead
+// of two per iteration; the only device-to-host traffic of a solve is the
+// 16-byte residual pair read after each block.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "../../include/fld.h"
+#include "fld_device.cuh"
+#include "fld_internal.h"
+
+using namespace fld;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+fld_status fail(fld_status s, const char *what) {
+    g_last_error = what ? what : "";
+    return s;
+}
+
+fld_status cuda_fail(cudaError_t e, const char *where) {
+    g_last_error = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return FLD_ERR_CUDA;
+}
+
+#define FLD_CK(call)                                      \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+constexpr double kFloorNoEmission = 1e-30;   // floor of Eq. 35 when jbar = 0
+constexpr int kStallChecks = 48;              // checks without a new minimum before giving up
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    int fam = -1;
+    int iters = 0;
+    PassParams p{};
+};
+
+bool same_params(const PassParams &a, const PassParams &b) {
+    return a.lim == b.lim && a.local_iters == b.local_iters && a.larsen_n == b.larsen_n && a.omega == b.omega &&
+           a.inv2h == b.inv2h && a.floor_ == b.floor_;
+}
+
+}  // namespace
+
+struct fld_grid_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int nx = 0, ny = 0, nz = 0;
+    double h = 0.0;
+    Layout L{};
+    Fields f{};
+    bool has_medium = false;
+    long long version = 1;          // bumps when medium or source change
+    long long prepared_f = 0, prepared_d = 0;
+    double prepared_seps_f = -1.0, prepared_seps_d = -1.0;
+    double jbar = 0.0;
+    long long jbar_version = 0;
+    bool valid_float = false, valid_d = false;   // which family holds the state
+    bool lo_live = false;                        // phlo may be non-zero
+    GraphEntry graphs[3];
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+long long nvox(const fld_grid_s *g) { return (long long)g->nx * g->ny * g->nz; }
+
+fld_status ensure_f64(fld_grid_s *g) {
+    if (g->f.phi64) return FLD_OK;
+    const size_t bytes = sizeof(double) * (size_t)g->L.total;
+    double **ptrs[6] = {&g->f.sp64, &g->f.ah264, &g->f.jh264, &g->f.phi64, &g->f.D64, &g->f.Df64};
+    for (double **p : ptrs) {
+        cudaError_t e = cudaMalloc((void **)p, bytes);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(FLD_ERR_OOM, "cudaMalloc of the FP64 fields failed");
+        }
+        FLD_CK(cudaMemsetAsync(*p, 0, bytes, g->stream));
+    }
+    return FLD_OK;
+}
+
+// sigma_eps = 1e-3 / L with L the largest grid extent (Sec. 5), unless given.
+double sigma_eps_of(const fld_grid_s *g, const fld_solve_params *p) {
+    if (p->sigma_eps > 0.0) return p->sigma_eps;
+    int n = g->nx;
+    if (g->ny > n) n = g->ny;
+    if (g->nz > n) n = g->nz;
+    return 1e-3 / ((double)n * g->h);
+}
+
+double omega_of(const fld_grid_s *g, const fld_solve_params *p) {
+    if (p->omega > 0.0) return p->omega;
+    int n = g->nx;
+    if (g->ny > n) n = g->ny;
+    if (g->nz > n) n = g->nz;
+    double w = 2.0 / (1.0 + sin(M_PI / (n + 1.0)));
+    if (w < 1.0) w = 1.0;
+    if (w > 1.9) w = 1.9;
+    return w;
+}
+
+fld_status read_result(fld_grid_s *g, double out[2]) {
+    FLD_CK(cudaMemcpyAsync(out, g->f.result, 2 * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    FLD_CK(cudaStreamSynchronize(g->stream));
+    return FLD_OK;
+}
+
+// jbar = RMS of the source over the unknowns (Algorithm 1).
+fld_status update_jbar(fld_grid_s *g) {
+    if (g->jbar_version == g->version) return FLD_OK;
+    FLD_CK(launch_sumsq_source(g->L, g->f, g->stream));
+    double r[2];
+    fld_status st = read_result(g, r);
+    if (st != FLD_OK) return st;
+    g->jbar = sqrt(r[0] / (double)nvox(g));
+    g->jbar_version = g->version;
+    return FLD_OK;
+}
+
+fld_status prepare(fld_grid_s *g, const fld_solve_params *p, Family fam) {
+    if (!g->has_medium) return fail(FLD_ERR_STATE, "fld_set_medium has not been called");
+    fld_status st = update_jbar(g);
+    if (st != FLD_OK) return st;
+    const double seps = sigma_eps_of(g, p);
+    const double h2 = g->h * g->h;
+    if (fam == FAM_F64) {
+        st = ensure_f64(g);
+        if (st != FLD_OK) return st;
+        if (g->prepared_d != g->version || g->prepared_seps_d != seps) {
+            FLD_CK(launch_prep_d(g->L, g->f, seps, h2, g->stream));
+            g->prepared_d = g->version;
+            g->prepared_seps_d = seps;
+        }
+    } else {
+        if (g->prepared_f != g->version || g->prepared_seps_f != seps) {
+            FLD_CK(launch_prep_f(g->L, g->f, (float)seps, (float)h2, g->stream));
+            g->prepared_f = g->version;
+            g->prepared_seps_f = seps;
+        }
+    }
+    return FLD_OK;
+}
+
+PassParams pass_params(const fld_grid_s *g, const fld_solve_params *p) {
+    PassParams q;
+    q.lim = p->limiter;
+    q.local_iters = p->local_iters < 1 ? 1 : p->local_iters;
+    q.larsen_n = p->larsen_n;
+    q.omega = omega_of(g, p);
+    q.inv2h = 1.0 / (2.0 * g->h);
+    const double eps = p->eps > 0.0 ? p->eps : 1e-20;
+    q.floor_ = g->jbar > 0.0 ? eps * g->jbar : kFloorNoEmission;
+    return q;
+}
+
+// Algorithm 1 initialisation (or the caller's values) of the family's fields.
+fld_status init_state(fld_grid_s *g, const fld_solve_params *p, Family fam) {
+    const double eps = p->eps > 0.0 ? p->eps : 1e-20;
+    const double phi_def = eps * g->jbar * g->h, D_def = eps * g->h;
+    const double phi0 = p->phi0 >= 0.0 ? p->phi0 : phi_def;
+    const double D0 = p->D0 >= 0.0 ? p->D0 : D_def;
+    const double phi_b = p->phi_b >= 0.0 ? p->phi_b : phi_def;
+    const double D_b = p->D_b >= 0.0 ? p->D_b : D_def;
+    if (fam == FAM_F64) {
+        FLD_CK(launch_init_d(g->L, g->f.phi64, g->f.D64, phi0, D0, phi_b, D_b, g->stream));
+        g->valid_d = true;
+        g->valid_float = false;
+    } else {
+        FLD_CK(launch_init_f(g->L, g->f.phi, g->f.phlo, g->f.D, phi0, D0, phi_b, D_b, g->stream));
+        g->valid_float = true;
+        g->valid_d = false;
+        g->lo_live = false;
+    }
+    return FLD_OK;
+}
+
+// Make the family's fields hold the current state.
+fld_status sync_family(fld_grid_s *g, Family fam) {
+    if (fam == FAM_F64) {
+        fld_status st = ensure_f64(g);
+        if (st != FLD_OK) return st;
+        if (!g->valid_d) {
+            if (!g->valid_float) return fail(FLD_ERR_STATE, "no state to continue from");
+            FLD_CK(launch_f_to_d(g->L, g->f.phi, g->lo_live ? g->f.phlo : nullptr, g->f.phi64, g->stream));
+            FLD_CK(launch_f_to_d(g->L, g->f.D, nullptr, g->f.D64, g->stream));
+            g->valid_d = true;
+        }
+        g->valid_float = false;
+    } else {
+        if (!g->valid_float) {
+            if (!g->valid_d) return fail(FLD_ERR_STATE, "no state to continue from");
+            FLD_CK(launch_d_to_f(g->L, g->f.phi64, g->f.phi, g->f.phlo, g->stream));
+            FLD_CK(launch_d_to_f(g->L, g->f.D64, g->f.D, nullptr, g->stream));
+            g->valid_float = true;
+            g->lo_live = true;
+        }
+        if (fam == FAM_F32 && g->lo_live) {
+            // single-precision sweeps carry no low word: round the state to float
+            FLD_CK(cudaMemsetAsync(g->f.phlo, 0, sizeof(float) * (size_t)g->L.total, g->stream));
+            g->lo_live = false;
+        }
+        if (fam == FAM_FF) g->lo_live = true;
+        g->valid_d = false;
+    }
+    return FLD_OK;
+}
+
+fld_status enqueue_iterations(fld_grid_s *g, Family fam, const PassParams &pp, int iters) {
+    for (int it = 0; it < iters; ++it)
+        for (int colour = 0; colour < 2; ++colour) FLD_CK(launch_pass(fam, g->L, g->f, pp, colour, g->stream));
+    return FLD_OK;
+}
+
+// Replay (capturing on first use) a graph of `iters` iterations.
+fld_status run_block(fld_grid_s *g, Family fam, const PassParams &pp, int iters) {
+    GraphEntry &e = g->graphs[fam];
+    if (!(e.exec && e.iters == iters && same_params(e.p, pp))) {
+        if (e.exec) {
+            cudaGraphExecDestroy(e.exec);
+            e.exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        FLD_CK(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
+        fld_status st = enqueue_iterations(g, fam, pp, iters);
+        cudaError_t ce = cudaStreamEndCapture(g->stream, &graph);
+        if (st != FLD_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return st;
+        }
+        if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+        ce = cudaGraphInstantiate(&e.exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            e.exec = nullptr;
+            return cuda_fail(ce, "cudaGraphInstantiate");
+        }
+        e.fam = fam;
+        e.iters = iters;
+        e.p = pp;
+    }
+    FLD_CK(cudaGraphLaunch(e.exec, g->stream));
+    return FLD_OK;
+}
+
+fld_status residual_now(fld_grid_s *g, Family fam, const PassParams &pp, int margin, double *rel) {
+    FLD_CK(launch_residual(fam, g->L, g->f, pp, margin, g->stream));
+    double r[2];
+    fld_status st = read_result(g, r);
+    if (st != FLD_OK) return st;
+    long long ex = g->nx - 2LL * margin, ey = g->ny - 2LL * margin, ez = g->nz - 2LL * margin;
+    const long long cnt = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
+    // r[0] = sum (R_p h^2)^2 over the margin set, r[1] = sum (j_p h^2)^2
+    const double rbar_h2 = cnt > 0 ? sqrt(r[0] / (double)cnt) : 0.0;
+    const double jbar_h2 = sqrt(r[1] / (double)nvox(g));
+    *rel = jbar_h2 > 0.0 ? rbar_h2 / jbar_h2 : rbar_h2 / (g->h * g->h);
+    return FLD_OK;
+}
+
+fld_status check_params(const fld_grid_s *g, const fld_solve_params *p) {
+    if (!p) return fail(FLD_ERR_INVALID_ARG, "params is NULL");
+    if (p->limiter < FLD_LIM_CDA || p->limiter > FLD_LIM_LP) return fail(FLD_ERR_INVALID_ARG, "unknown limiter");
+    if (p->limiter == FLD_LIM_LARSEN && !(p->larsen_n > 0.0)) return fail(FLD_ERR_INVALID_ARG, "larsen_n must be > 0");
+    if (p->omega > 0.0 && !(p->omega < 2.0)) return fail(FLD_ERR_INVALID_ARG, "omega must lie in (0, 2)");
+    if (p->precision < FLD_PREC_FP64 || p->precision > FLD_PREC_MIXED)
+        return fail(FLD_ERR_INVALID_ARG, "unknown precision");
+    if (p->local_iters > 64) return fail(FLD_ERR_INVALID_ARG, "local_iters must be <= 64");
+    if (p->residual_margin < 0) return fail(FLD_ERR_INVALID_ARG, "residual_margin must be >= 0");
+    (void)g;
+    return FLD_OK;
+}
+
+fld_grid_s *as_grid(fld_grid g) { return g; }
+
+fld_status enter(fld_grid g) {
+    if (!g) return fail(FLD_ERR_INVALID_ARG, "grid is NULL");
+    FLD_CK(cudaSetDevice(g->device));
+    return FLD_OK;
+}
+
+// Copy n floats from host or device memory into a device buffer.
+fld_status copy_in(fld_grid_s *g, float *dst, const float *src, long long n, int where) {
+    const cudaMemcpyKind kind = where == FLD_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    FLD_CK(cudaMemcpyAsync(dst, src, sizeof(float) * (size_t)n, kind, g->stream));
+    return FLD_OK;
+}
+
+fld_status validate_inputs(fld_grid_s *g, const float *st, const float *alb, const float *js) {
+    FLD_CK(launch_validate(nvox(g), g->f, st, alb, js, g->stream));
+    double r[2];
+    fld_status s = read_result(g, r);
+    if (s != FLD_OK) return s;
+    if (r[0] > 0.0) return fail(FLD_ERR_INVALID_ARG, "sigma_t or j has NaN, infinite or negative values");
+    if (r[1] > 0.0) return fail(FLD_ERR_INVALID_ARG, "albedo has values outside [0, 1] or NaN");
+    return FLD_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void fld_default_params(fld_solve_params *p) {
+    if (!p) return;
+    memset(p, 0, sizeof(*p));
+    p->limiter = FLD_LIM_LP;
+    p->larsen_n = 2.0;
+    p->omega = 0.0;
+    p->local_iters = 2;
+    p->tol = 1e-6;
+    p->max_iters = 1000000;
+    p->check_every = 64;
+    p->sigma_eps = 0.0;
+    p->eps = 0.0;
+    p->precision = FLD_PREC_MIXED;
+    p->fp32_switch = 0.0;
+    p->residual_margin = 0;
+    p->warm_start = 0;
+    p->phi0 = -1.0;
+    p->D0 = -1.0;
+    p->phi_b = -1.0;
+    p->D_b = -1.0;
+}
+
+const char *fld_status_string(fld_status s) {
+    switch (s) {
+    case FLD_OK: return "FLD_OK";
+    case FLD_ERR_INVALID_ARG: return "FLD_ERR_INVALID_ARG";
+    case FLD_ERR_OOM: return "FLD_ERR_OOM";
+    case FLD_ERR_CUDA: return "FLD_ERR_CUDA";
+    case FLD_ERR_STATE: return "FLD_ERR_STATE";
+    case FLD_ERR_NOT_CONVERGED: return "FLD_ERR_NOT_CONVERGED";
+    case FLD_ERR_DIVERGED: return "FLD_ERR_DIVERGED";
+    case FLD_ERR_NO_DEVICE: return "FLD_ERR_NO_DEVICE";
+    }
+    return "FLD_ERR_UNKNOWN";
+}
+
+const char *fld_last_error(void) { return g_last_error.c_str(); }
+
+fld_status fld_create_grid(int nx, int ny, int nz, double h, void *stream, fld_grid *out) {
+    if (!out) return fail(FLD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(FLD_ERR_INVALID_ARG, "grid extents must be >= 1");
+    if (!(h > 0.0) || !isfinite(h)) return fail(FLD_ERR_INVALID_ARG, "h must be a positive finite number");
+    if ((long long)(nx + 2) * (ny + 2) * (nz + 2) > (1LL << 40))
+        return fail(FLD_ERR_INVALID_ARG, "grid too large");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        (void)cudaGetLastError();
+        return fail(FLD_ERR_NO_DEVICE, "no CUDA device available");
+    }
+    fld_grid_s *g = new (std::nothrow) fld_grid_s();
+    if (!g) return fail(FLD_ERR_OOM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&g->device);
+    if (e != cudaSuccess) {
+        delete g;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    g->nx = nx; g->ny = ny; g->nz = nz; g->h = h;
+    g->L = make_layout(nx, ny, nz);
+    if (stream) {
+        g->stream = (cudaStream_t)stream;
+    } else {
+        // a blocking stream: ordered with work on the legacy default stream
+        e = cudaStreamCreate(&g->stream);
+        if (e != cudaSuccess) {
+            delete g;
+            return cuda_fail(e, "cudaStreamCreate");
+        }
+        g->own_stream = true;
+    }
+    const size_t fb = sizeof(float) * (size_t)g->L.total;
+    const size_t ub = sizeof(float) * (size_t)nvox(g);
+    float **pf[7] = {&g->f.sp, &g->f.ah2, &g->f.jh2, &g->f.phi, &g->f.phlo, &g->f.D, &g->f.Df};
+    float **pu[3] = {&g->f.sigma_t, &g->f.albedo, &g->f.jsrc};
+    fld_status st = FLD_OK;
+    for (float **p : pf)
+        if (st == FLD_OK && cudaMalloc((void **)p, fb) != cudaSuccess) st = FLD_ERR_OOM;
+    for (float **p : pu)
+        if (st == FLD_OK && cudaMalloc((void **)p, ub) != cudaSuccess) st = FLD_ERR_OOM;
+    g->f.partial_cap = reduction_blocks(g->L);
+    if (st == FLD_OK && cudaMalloc((void **)&g->f.partials, sizeof(double) * 2 * (size_t)g->f.partial_cap) != cudaSuccess)
+        st = FLD_ERR_OOM;
+    if (st == FLD_OK && cudaMalloc((void **)&g->f.result, sizeof(double) * 2) != cudaSuccess) st = FLD_ERR_OOM;
+    if (st == FLD_OK && (cudaEventCreate(&g->ev0) != cudaSuccess || cudaEventCreate(&g->ev1) != cudaSuccess))
+        st = FLD_ERR_CUDA;
+    if (st == FLD_OK) {
+        for (float **p : pf)
+            if (cudaMemsetAsync(*p, 0, fb, g->stream) != cudaSuccess) st = FLD_ERR_CUDA;
+        for (float **p : pu)
+            if (cudaMemsetAsync(*p, 0, ub, g->stream) != cudaSuccess) st = FLD_ERR_CUDA;
+    }
+    if (st != FLD_OK) {
+        (void)cudaGetLastError();
+        fld_destroy(g);
+        return fail(st, st == FLD_ERR_OOM ? "cudaMalloc failed while creating the grid" : "CUDA setup failed");
+    }
+    *out = g;
+    return FLD_OK;
+}
+
+void fld_destroy(fld_grid g) {
+    if (!g) return;
+    cudaSetDevice(g->device);
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    for (GraphEntry &e : g->graphs)
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+    void *ptrs[] = {g->f.sp, g->f.ah2, g->f.jh2, g->f.phi, g->f.phlo, g->f.D, g->f.Df, g->f.sp64, g->f.ah264,
+                    g->f.jh264, g->f.phi64, g->f.D64, g->f.Df64, g->f.sigma_t, g->f.albedo, g->f.jsrc,
+                    g->f.partials, g->f.result};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (g->ev0) cudaEventDestroy(g->ev0);
+    if (g->ev1) cudaEventDestroy(g->ev1);
+    if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
+    delete g;
+}
+
+fld_status fld_set_medium(fld_grid g, const float *sigma_t, const float *albedo, int where) {
+    fld_status st = enter(g);
+    if (st != FLD_OK) return st;
+    if (!sigma_t || !albedo) return fail(FLD_ERR_INVALID_ARG, "sigma_t and albedo must not be NULL");
+    if (where != FLD_MEM_HOST && where != FLD_MEM_DEVICE) return fail(FLD_ERR_INVALID_ARG, "bad memory kind");
+    g->has_medium = false;
+    if ((st = copy_in(g, g->f.sigma_t, sigma_t, nvox(g), where)) != FLD_OK) return st;
+    if ((st = copy_in(g, g->f.albedo, albedo, nvox(g), where)) != FLD_OK) return st;
+    if ((st = validate_inputs(g, g->f.sigma_t, g->f.albedo, nullptr)) != FLD_OK) return st;
+    g->has_medium = true;
+    ++g->version;
+    return FLD_OK;
+}
+
+fld_status fld_set_source(fld_grid g, const float *j, int where) {
+    fld_status st = enter(g);
+    if (st != FLD_OK) return st;
+    if (!j) return fail(FLD_ERR_INVALID_ARG, "j must not be NULL");
+    if (where != FLD_MEM_HOST && where != FLD_MEM_DEVICE) return fail(FLD_ERR_INVALID_ARG, "bad memory kind");
+    if ((st = copy_in(g, g->f.jsrc, j, nvox(g), where)) != FLD_OK) return st;
+    ++g->version;
+    if ((st = validate_inputs(g, nullptr, nullptr, g->f.jsrc)) != FLD_OK) {
+        FLD_CK(cudaMemsetAsync(g->f.jsrc, 0, sizeof(float) * (size_t)nvox(g), g->stream));
+        return st;
+    }
+    return FLD_OK;
+}
+
+fld_status fld_get_source(fld_grid g, float *j, int where) {
+    fld_status st = enter(g);
+    if (st != FLD_OK) return st;
+    if (!j) return fail(FLD_ERR_INVALID_ARG, "j must not be NULL");
+    const cudaMemcpyKind kind = where == FLD_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    FLD_CK(cudaMemcpyAsync(j, g->f.jsrc, sizeof(float) * (size_t)nvox(g), kind, g->stream));
+    if (where != FLD_MEM_DEVICE) FLD_CK(cudaStreamSynchronize(g->stream));
+    return FLD_OK;
+}
+
+fld_status fld_bake_directional(fld_grid g, const double dir[3], double radiance, double step, int accumulate) {
+    fld_status st = enter(g);
+    if (st != FLD_OK) return st;
+    if (!g->has_medium) return fail(FLD_ERR_STATE, "fld_set_medium has not been called");
+    if (!dir) return fail(FLD_ERR_INVALID_ARG, "dir is NULL");
+    const double n = sqrt(dir[0] * dir[0] + dir[1] * dir[1] + dir[2] * dir[2]);
+    if (!(n > 0.0) || !isfinite(n)) return fail(FLD_ERR_INVALID_ARG, "dir must be a nonzero finite vector");
+    if (!(radiance >= 0.0) || !isfinite(radiance)) return fail(FLD_ERR_INVALID_ARG, "radiance must be >= 0");
+    if (step <= 0.0) step = 0.5 * g->h;
+    if (!isfinite(step)) return fail(FLD_ERR_INVALID_ARG, "bad step");
+    if (dir[0] == 0.0 && dir[1] == 0.0 && dir[2] < 0.0 && step == 0.5 * g->h) {
+        FLD_CK(launch_bake_scan_negz(g->L, g->f, (float)g->h, (float)radiance, accumulate, g->stream));
+    } else {
+        const double w[3] = {-dir[0] / n, -dir[1] / n, -dir[2] / n};   // towards the light
+        const double pos[3] = {0, 0, 0};
+        FLD_CK(launch_bake_march(g->L, g->f, (float)g->h, w, pos, 0, (float)radiance, (float)step, accumulate,
+                                 g->stream));
+    }
+    ++g->version;
+    return FLD_OK;
+}
+
+fld_status fld_bake_point(fld_grid g, const double pos[3], double power, double step, int accumulate) {
+    fld_status st = enter(g);
+    if (st != FLD_OK) return st;
+    if (!g->has_medium) return fail(FLD_ERR_STATE, "fld_set_medium has not been called");
+    if (!pos || !isfinite(pos[0]) || !isfinite(pos[1]) || !isfinite(pos[2]))
+        return fail(FLD_ERR_INVALID_ARG, "pos must be finite");
+    if (!(power >= 0.0) || !isfinite(power)) return fail(FLD_ERR_INVALID_ARG, "power must be >= 0");
+    if (step <= 0.0) step = 0.5 * g->h;
+    if (!isfinite(step)) return fail(FLD_ERR_INVALID_ARG, "bad step");
+    const double w[3] = {0, 0, 0};
+    FLD_CK(launch_bake_march(g->L, g->f, (float)g->h, w, pos, 1, (float)power, (float)step, accumulate, g->stream));
+    ++g->version;
+    return FLD_OK;
+}
+
+fld_status fld_set_state(fld_grid g, const double *phi, const double *D, int where) {
+    fld_status st = enter(g);
+    if (st != FLD_OK) return st;
+    if (!phi && !D) return FLD_OK;
+    const size_t n = (size_t)(g->nx + 2) * (g->ny + 2) * (g->nz + 2);
+    // Both families receive the values, so an FP64 continuation keeps them
+    // exactly (the float family rounds D to float).
+    if ((st = ensure_f64(g)) != FLD_OK) return st;
+    if (!g->valid_float && !g->valid_d) {
+        // a partial update of a grid without state: start from zeros
+        FLD_CK(launch_init_f(g->L, g->f.phi, g->f.phlo, g->f.D, 0.0, 0.0, 0.0, 0.0, g->stream));
+        FLD_CK(launch_init_d(g->L, g->f.phi64, g->f.D64, 0.0, 0.0, 0.0, 0.0, g->stream));
+    } else if (g->valid_d && !g->valid_float) {
+        FLD_CK(launch_d_to_f(g->L, g->f.phi64, g->f.phi, g->f.phlo, g->stream));
+        FLD_CK(launch_d_to_f(g->L, g->f.D64, g->f.D, nullptr, g->stream));
+    } else if (g->valid_float && !g->valid_d) {
+        FLD_CK(launch_f_to_d(g->L, g->f.phi, g->lo_live ? g->f.phlo : nullptr, g->f.phi64, g->stream));
+        FLD_CK(launch_f_to_d(g->L, g->f.D, nullptr, g->f.D64, g->stream));
+    }
+    double *stage = nullptr;
+    if (where != FLD_MEM_DEVICE) FLD_CK(cudaMalloc((void **)&stage, sizeof(double) * n));
+    const double *srcs[2] = {phi, D};
+    for (int a = 0; a < 2; ++a) {
+        if (!srcs[a]) continue;
+        const double *src = srcs[a];
+        if (stage) {
+            cudaError_t e = cudaMemcpyAsync(stage, src, sizeof(double) * n, cudaMemcpyHostToDevice, g->stream);
+            if (e != cudaSuccess) {
+                cudaFree(stage);
+                return cuda_fail(e, "cudaMemcpyAsync(set_state)");
+            }
+            src = stage;
+        }
+        cudaError_t e = a == 0 ? launch_unpack_to_f(g->L, src, g->f.phi, g->f.phlo, g->stream)
+                               : launch_unpack_to_f(g->L, src, g->f.D, nullptr, g->stream);
+        if (e == cudaSuccess) e = launch_unpack_to_d(g->L, src, a == 0 ? g->f.phi64 : g->f.D64, g->stream);
+        if (e != cudaSuccess) {
+            if (stage) cudaFree(stage);
+            return cuda_fail(e, "unpack state");
+        }
+    }
+    if (stage) {
+        cudaStreamSynchronize(g->stream);
+        cudaFree(stage);
+    }
+    g->valid_float = true;
+    g->lo_live = true;
+    g->valid_d = true;
+    return FLD_OK;
+}
+
+fld_status fld_get_state(fld_grid g, double *phi, double *D, int where) {
+    fld_status st = enter(g);
+    if (st != FLD_OK) return st;
+    if (!g->valid_float && !g->valid_d) return fail(FLD_ERR_STATE, "the grid holds no state yet");
+    const size_t n = (size_t)(g->nx + 2) * (g->ny + 2) * (g->nz + 2);
+    double *outs[2] = {phi, D};
+    double *stage = nullptr;
+    if (where != FLD_MEM_DEVICE && (phi || D)) FLD_CK(cudaMalloc((void **)&stage, sizeof(double) * n));
+    for (int a = 0; a < 2; ++a) {
+        if (!outs[a]) continue;
+        double *dst = stage ? stage : outs[a];
+        cudaError_t e;
+        if (g->valid_d)
+            e = launch_pack_from_d(g->L, a == 0 ? g->f.phi64 : g->f.D64, dst, g->stream);
+        else
+            e = a == 0 ? launch_pack_from_f(g->L, g->f.phi, g->lo_live ? g->f.phlo : nullptr, dst, g->stream)
+                       : launch_pack_from_f(g->L, g->f.D, nullptr, dst, g->stream);
+        if (e == cudaSuccess && stage)
+            e = cudaMemcpyAsync(outs[a], stage, sizeof(double) * n, cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess && stage) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) {
+            if (stage) cudaFree(stage);
+            return cuda_fail(e, "get_state");
+        }
+    }
+    if (stage) cudaFree(stage);
+    return FLD_OK;
+}
+
+fld_status fld_iterate(fld_grid g, const fld_solve_params *p, int iterations) {
+    fld_status st = enter(g);
+    if (st != FLD_OK) return st;
+    if ((st = check_params(g, p)) != FLD_OK) return st;
+    if (iterations < 0) return fail(FLD_ERR_INVALID_ARG, "iterations must be >= 0");
+    const Family fam = p->precision == FLD_PREC_FP64 ? FAM_F64 : (p->precision == FLD_PREC_FP32 ? FAM_F32 : FAM_FF);
+    if ((st = prepare(g, p, fam)) != FLD_OK) return st;
+    if (!p->warm_start) {
+        if ((st = init_state(g, p, fam)) != FLD_OK) return st;
+    }
+    if ((st = sync_family(g, fam)) != FLD_OK) return st;
+    return enqueue_iterations(g, fam, pass_params(g, p), iterations);
+}
+
+fld_status fld_residual(fld_grid g, const fld_solve_params *p, double *rel) {
+    fld_status st = enter(g);
+    if (st != FLD_OK) return st;
+    if ((st = check_params(g, p)) != FLD_OK) return st;
+    if (!rel) return fail(FLD_ERR_INVALID_ARG, "rel is NULL");
+    const Family fam = p->precision == FLD_PREC_FP64 ? FAM_F64 : (p->precision == FLD_PREC_FP32 ? FAM_F32 : FAM_FF);
+    if ((st = prepare(g, p, fam)) != FLD_OK) return st;
+    if (!g->valid_float && !g->valid_d) return fail(FLD_ERR_STATE, "the grid holds no state yet");
+    Family use = fam;
+    if (fam != FAM_F64) use = g->lo_live ? FAM_FF : FAM_F32;
+    if ((st = sync_family(g, use)) != FLD_OK) return st;
+    return residual_now(g, use, pass_params(g, p), p->residual_margin, rel);
+}
+
+fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r) {
+    fld_status st = enter(g);
+    if (st != FLD_OK) return st;
+    if ((st = check_params(g, p)) != FLD_OK) return st;
+    if (!(p->tol >= 0.0)) return fail(FLD_ERR_INVALID_ARG, "tol must be >= 0");
+    if (p->max_iters < 0 || p->check_every < 1) return fail(FLD_ERR_INVALID_ARG, "bad max_iters / check_every");
+    fld_solve_result res;
+    memset(&res, 0, sizeof(res));
+    Family fam = p->precision == FLD_PREC_FP64 ? FAM_F64 : FAM_F32;
+    if ((st = prepare(g, p, fam)) != FLD_OK) return st;
+    if (p->precision == FLD_PREC_MIXED && (st = prepare(g, p, FAM_FF)) != FLD_OK) return st;
+    if (!p->warm_start) {
+        if ((st = init_state(g, p, fam)) != FLD_OK) return st;
+    } else if (p->precision == FLD_PREC_MIXED && !g->valid_d && g->lo_live) {
+        fam = FAM_FF;   // continue a correction phase
+    }
+    if ((st = sync_family(g, fam)) != FLD_OK) return st;
+    const PassParams pp = pass_params(g, p);
+    const double sw = p->fp32_switch > 0.0 ? p->fp32_switch : 2e-5;
+    res.jbar = g->jbar;
+    res.omega = pp.omega;
+    FLD_CK(cudaEventRecord(g->ev0, g->stream));
+    double rel = INFINITY, best = INFINITY;
+    int since_best = 0;
+    int it = 0;
+    bool stalled = false;
+    fld_status outcome = FLD_ERR_NOT_CONVERGED;
+    if ((st = residual_now(g, fam, pp, p->residual_margin, &rel)) != FLD_OK) return st;
+    ++res.checks;
+    if (rel <= p->tol) outcome = FLD_OK;
+    while (outcome == FLD_ERR_NOT_CONVERGED && it < p->max_iters) {
+        int k = p->check_every;
+        if (k > p->max_iters - it) k = p->max_iters - it;
+        if ((st = run_block(g, fam, pp, k)) != FLD_OK) return st;
+        it += k;
+        if (fam == FAM_FF) res.iterations_corr += k;
+        else if (fam == FAM_F32) res.iterations_fp32 += k;
+        if ((st = residual_now(g, fam, pp, p->residual_margin, &rel)) != FLD_OK) return st;
+        ++res.checks;
+        if (!isfinite(rel)) {
+            outcome = FLD_ERR_DIVERGED;
+            break;
+        }
+        if (rel <= p->tol) {
+            outcome = FLD_OK;
+            break;
+        }
+        if (rel < best) {
+            best = rel;
+            since_best = 0;
+        } else {
+            ++since_best;
+        }
+        if (since_best >= kStallChecks && !(p->precision == FLD_PREC_MIXED && fam == FAM_F32)) {
+            // no new minimum for many checks: the residual has reached the
+            // floor of the arithmetic in use
+            stalled = true;
+            break;
+        }
+        if (p->precision == FLD_PREC_MIXED && fam == FAM_F32 && (rel <= sw || since_best >= 4)) {
+            // single precision has done what it can (Sec. 6.2: ~1e-4 is its
+            // practical limit): continue with float-float correction sweeps
+            if ((st = sync_family(g, FAM_FF)) != FLD_OK) return st;
+            fam = FAM_FF;
+            since_best = 0;
+            best = rel;
+        }
+    }
+    FLD_CK(cudaEventRecord(g->ev1, g->stream));
+    FLD_CK(cudaEventSynchronize(g->ev1));
+    float ms = 0.0f;
+    FLD_CK(cudaEventElapsedTime(&ms, g->ev0, g->ev1));
+    res.status = outcome;
+    res.iterations = it;
+    res.rel_residual = rel;
+    res.ms = ms;
+    if (r) *r = res;
+    if (outcome == FLD_ERR_DIVERGED) g_last_error = "residual became NaN or infinite";
+    if (outcome == FLD_ERR_NOT_CONVERGED)
+        g_last_error = stalled ? "residual stalled above tol (floor of the arithmetic)" : "max_iters reached before tol";
+    return outcome;
+}
+
+}  // extern "C"

@@ -1,0 +1,85 @@
+// fld_internal.h -- launchers shared by the kernels and the host driver of
+// the GB300 FLD solver (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include "fld_device.cuh"
+
+namespace fld {
+
+// Arithmetic of one sweep family.
+enum Family : int { FAM_F32 = 0, FAM_FF = 1, FAM_F64 = 2 };
+
+struct PassParams {
+    int lim;
+    int local_iters;
+    double larsen_n;
+    double omega;
+    double inv2h;
+    double floor_;   // eps * jbar (or the no-emission floor)
+};
+
+// Device fields of one grid (padded layout unless noted).
+struct Fields {
+    // single-precision family
+    float *sp = nullptr, *ah2 = nullptr, *jh2 = nullptr;   // sigma', sigma_a' h^2, j h^2
+    float *phi = nullptr, *phlo = nullptr, *D = nullptr;   // phi (hi), phi (lo), D
+    float *Df = nullptr;                                   // scratch: fresh D for the residual
+    // double-precision family (allocated on first FP64 use)
+    double *sp64 = nullptr, *ah264 = nullptr, *jh264 = nullptr;
+    double *phi64 = nullptr, *D64 = nullptr, *Df64 = nullptr;
+    // inputs (unpadded, nx*ny*nz floats)
+    float *sigma_t = nullptr, *albedo = nullptr, *jsrc = nullptr;
+    // reduction scratch
+    double *partials = nullptr;   // 2 doubles per block
+    double *result = nullptr;     // 2 doubles
+    int partial_cap = 0;          // blocks the partials buffer holds
+};
+
+// Medium preparation (Algorithm 1: sigma floor; sigma_a', j scaled by h^2).
+cudaError_t launch_prep_f(const Layout &L, const Fields &f, float sigma_eps, float h2, cudaStream_t s);
+cudaError_t launch_prep_d(const Layout &L, const Fields &f, double sigma_eps, double h2, cudaStream_t s);
+
+// phi = phi0 / D = D0 on the unknowns, phi_b / D_b on the ghosts, 0 elsewhere.
+cudaError_t launch_init_f(const Layout &L, float *phi, float *phlo, float *D, double phi0, double D0,
+                          double phi_b, double D_b, cudaStream_t s);
+cudaError_t launch_init_d(const Layout &L, double *phi, double *D, double phi0, double D0, double phi_b,
+                          double D_b, cudaStream_t s);
+
+// Conversions between the packed (nx+2)(ny+2)(nz+2) double layout and the
+// device fields.  dst_lo may be null (single float); src_lo likewise.
+cudaError_t launch_unpack_to_f(const Layout &L, const double *src, float *dst_hi, float *dst_lo, cudaStream_t s);
+cudaError_t launch_unpack_to_d(const Layout &L, const double *src, double *dst, cudaStream_t s);
+cudaError_t launch_pack_from_f(const Layout &L, const float *hi, const float *lo, double *dst, cudaStream_t s);
+cudaError_t launch_pack_from_d(const Layout &L, const double *src, double *dst, cudaStream_t s);
+// Between families (float-float <-> double) in the device layout.
+cudaError_t launch_f_to_d(const Layout &L, const float *hi, const float *lo, double *dst, cudaStream_t s);
+cudaError_t launch_d_to_f(const Layout &L, const double *src, float *hi, float *lo, cudaStream_t s);
+
+// One colour pass of Algorithm 1 (colour 0 = red: i+j+k even).
+cudaError_t launch_pass(Family fam, const Layout &L, const Fields &f, const PassParams &p, int colour,
+                        cudaStream_t s);
+
+// Residual of Eq. 37 with fresh D: writes sum(R h^2)^2 over the margin set
+// to result[0] and sum (j h^2)^2 over all unknowns to result[1].
+cudaError_t launch_residual(Family fam, const Layout &L, const Fields &f, const PassParams &p, int margin,
+                            cudaStream_t s);
+
+// sum j^2 over the unknowns of the unpadded source -> result[0].
+cudaError_t launch_sumsq_source(const Layout &L, const Fields &f, cudaStream_t s);
+
+// Blocks the residual / reduction launches use (sizes the partials buffer).
+int reduction_blocks(const Layout &L);
+
+// Single-scatter source.
+cudaError_t launch_bake_scan_negz(const Layout &L, const Fields &f, float h, float radiance, int accumulate,
+                                  cudaStream_t s);
+cudaError_t launch_bake_march(const Layout &L, const Fields &f, float h, const double w[3], const double pos[3],
+                              int point, float value, float step, int accumulate, cudaStream_t s);
+
+// Validation of n input values (any pointer may be null): result[0] counts
+// NaN / negative / infinite sigma_t and j, result[1] albedo outside [0, 1].
+cudaError_t launch_validate(long long n, const Fields &f, const float *sigma_t, const float *albedo,
+                            const float *j, cudaStream_t s);
+
+}  // namespace fld

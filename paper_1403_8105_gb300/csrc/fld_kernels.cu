@@ -1,0 +1,766 @@
+// fld_kernels.cu -- CUDA kernels of the GB300 FLD solver (sm_103a).
+//
+// Koerner et al., "Flux-Limited Diffusion for Multiple Scattering in
+// Participating Media", CGF 33(2) 2014:
+//   * medium preparation and initialisation (Algorithm 1, first steps);
+//   * one colour pass of the red-black SOR relaxation (Algorithm 1) with the
+//     Knudsen number (Eq. 35), D update (Eq. 33), face coefficients
+//     D_ps = (D_p + D_s)/2, local update (Eq. 32) and SOR blend (Eq. 36);
+//   * the residual of Eq. 37 with D recomputed from phi, reduced on the
+//     device (warp shuffles, block tree, deterministic second pass);
+//   * the single-scatter source q_ri = L sigma_s T (Sec. 3 after Eq. 6) by
+//     a transmittance march (Eq. 3).
+//
+// The stencil is memory-bound: no tensor-core formulation applies.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "fld_device.cuh"
+#include "fld_internal.h"
+
+namespace fld {
+
+namespace {
+
+constexpr int kRedThreads = 256;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of v over the block; valid in thread 0.  blockDim <= 1024.
+__device__ __forceinline__ double block_sum(double v, double *sh) {
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+    v = warp_sum(v);
+    __syncthreads();
+    if ((tid & 31) == 0) sh[tid >> 5] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (tid < 32) {
+        r = (tid < (nthr + 31) / 32) ? sh[tid] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
+// Second pass: fixed-order sum of the per-block partial pairs.
+__global__ void __launch_bounds__(kRedThreads) k_finalize(const double *__restrict__ partials, int nblocks,
+                                                         double *__restrict__ result) {
+    __shared__ double sh[32];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
+        a += partials[2 * i];
+        b += partials[2 * i + 1];
+    }
+    a = block_sum(a, sh);
+    __syncthreads();
+    b = block_sum(b, sh);
+    if (threadIdx.x == 0) {
+        result[0] = a;
+        result[1] = b;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Preparation
+// ---------------------------------------------------------------------------
+__global__ void k_prep_f(Layout L, const float *__restrict__ st, const float *__restrict__ alb,
+                         const float *__restrict__ js, float *__restrict__ sp, float *__restrict__ ah2,
+                         float *__restrict__ jh2, float seps, float h2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= L.nx || j >= L.ny) return;
+    const long long v = ((long long)k * L.ny + j) * L.nx + i;
+    const long long q = L.at(i, j, k);
+    const float s = fmaxf(st[v], seps);                           // Algorithm 1: sigma floor
+    sp[q] = s;
+    ah2[q] = __fmul_rn(__fmul_rn(__fsub_rn(1.0f, alb[v]), s), h2);  // (1 - albedo) sigma' dl^2
+    jh2[q] = __fmul_rn(js[v], h2);
+}
+
+__global__ void k_prep_d(Layout L, const float *__restrict__ st, const float *__restrict__ alb,
+                         const float *__restrict__ js, double *__restrict__ sp, double *__restrict__ ah2,
+                         double *__restrict__ jh2, double seps, double h2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= L.nx || j >= L.ny) return;
+    const long long v = ((long long)k * L.ny + j) * L.nx + i;
+    const long long q = L.at(i, j, k);
+    const double s = fmax((double)st[v], seps);
+    sp[q] = s;
+    ah2[q] = __dmul_rn(__dmul_rn(1.0 - (double)alb[v], s), h2);
+    jh2[q] = __dmul_rn((double)js[v], h2);
+}
+
+// Every padded element: unknowns get (phi0, D0), the ghost layer (phi_b, D_b),
+// alignment slack 0.
+template <typename T>
+__global__ void k_init(Layout L, T *__restrict__ phi, float *__restrict__ phlo, T *__restrict__ D, T phi0, T D0,
+                       T phi_b, T D_b) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= L.total) return;
+    T p = T(0), d = T(0);
+    const long long r = e - kOx;
+    if (r >= 0 && r < L.plane * (L.nz + 2)) {
+        const int K = (int)(r / L.plane);
+        const long long w = r - (long long)K * L.plane;
+        const int J = (int)(w / L.px);
+        const int I = (int)(w - (long long)J * L.px);
+        if (I <= L.nx + 1) {
+            const bool ghost = I == 0 || J == 0 || K == 0 || I == L.nx + 1 || J == L.ny + 1 || K == L.nz + 1;
+            p = ghost ? phi_b : phi0;
+            d = ghost ? D_b : D0;
+        }
+    }
+    phi[e] = p;
+    D[e] = d;
+    if (phlo) phlo[e] = 0.0f;
+}
+
+// Packed (nx+2)(ny+2)(nz+2) <-> device layout.
+__global__ void k_unpack_to_f(Layout L, const double *__restrict__ src, float *__restrict__ hi,
+                              float *__restrict__ lo) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y;
+    const int K = blockIdx.z;
+    if (I > L.nx + 1) return;
+    const double x = src[((long long)K * (L.ny + 2) + J) * (L.nx + 2) + I];
+    const long long q = L.at(I - 1, J - 1, K - 1);
+    const float h = (float)x;
+    hi[q] = h;
+    if (lo) lo[q] = (float)(x - (double)h);
+}
+
+__global__ void k_unpack_to_d(Layout L, const double *__restrict__ src, double *__restrict__ dst) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y;
+    const int K = blockIdx.z;
+    if (I > L.nx + 1) return;
+    dst[L.at(I - 1, J - 1, K - 1)] = src[((long long)K * (L.ny + 2) + J) * (L.nx + 2) + I];
+}
+
+__global__ void k_pack_from_f(Layout L, const float *__restrict__ hi, const float *__restrict__ lo,
+                              double *__restrict__ dst) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y;
+    const int K = blockIdx.z;
+    if (I > L.nx + 1) return;
+    const long long q = L.at(I - 1, J - 1, K - 1);
+    dst[((long long)K * (L.ny + 2) + J) * (L.nx + 2) + I] = (double)hi[q] + (lo ? (double)lo[q] : 0.0);
+}
+
+__global__ void k_pack_from_d(Layout L, const double *__restrict__ src, double *__restrict__ dst) {
+    const int I = blockIdx.x * blockDim.x + threadIdx.x;
+    const int J = blockIdx.y;
+    const int K = blockIdx.z;
+    if (I > L.nx + 1) return;
+    dst[((long long)K * (L.ny + 2) + J) * (L.nx + 2) + I] = src[L.at(I - 1, J - 1, K - 1)];
+}
+
+__global__ void k_f_to_d(long long n, const float *__restrict__ hi, const float *__restrict__ lo,
+                         double *__restrict__ dst) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) dst[e] = (double)hi[e] + (lo ? (double)lo[e] : 0.0);
+}
+
+__global__ void k_d_to_f(long long n, const double *__restrict__ src, float *__restrict__ hi,
+                         float *__restrict__ lo) {
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const double x = src[e];
+    const float h = (float)x;
+    hi[e] = h;
+    if (lo) lo[e] = (float)(x - (double)h);
+}
+
+// ---------------------------------------------------------------------------
+// Red-black pass.
+//
+// Thread (t, j, k) updates voxel i = 2t + ((j + k + colour) & 1) of row (j, k)
+// if i < nx; all its neighbours have the other colour, so the pass is free of
+// races and its result does not depend on thread order.
+//
+// Update in residual form: with d_s = phi_s - phi_p and D_ps = (D_p + D_s)/2,
+//   S(D_p)   = j dl^2 - sigma_a' dl^2 phi_p + sum_s D_ps d_s
+//            = jh2 - ah2 phi_p + (D_p/2) sum_s d_s + (1/2) sum_s D_s d_s
+//   den(D_p) = ah2 + sum_s D_ps = ah2 + 3 D_p + (1/2) sum_s D_s
+// and Eq. 32 reads phi' = phi_p + S/den (num/den of the paper with num - phi_p
+// den = S).  Each local round recomputes D_p (Eq. 35, 33) at the current
+// point value phi_p + delta and sets delta = S(D_p)/den(D_p); the SOR blend
+// (Eq. 36) is phi_p + omega * delta.  One round is Algorithm 1 as printed.
+// ---------------------------------------------------------------------------
+
+// Terms of the residual-form update that do not depend on D_p, shared by the
+// sweep and the residual kernel so both evaluate the same discrete equation
+// bit for bit:  A = sum_s d_s,  B = sum_s D_s d_s  (float-float),
+// C = sum_s D_s,  base = jh2 - ah2 phi_p + B/2, and the central differences.
+struct FFTerms {
+    ff A, base;
+    float C, gx, gy, gz;
+};
+
+__device__ __forceinline__ FFTerms ff_terms(float p0, float p0lo, const float ps[6], const float ls[6],
+                                            const float Ds[6], float ah, float jj) {
+    FFTerms t;
+    t.gx = __fadd_rn(__fsub_rn(ps[1], ps[0]), __fsub_rn(ls[1], ls[0]));
+    t.gy = __fadd_rn(__fsub_rn(ps[3], ps[2]), __fsub_rn(ls[3], ls[2]));
+    t.gz = __fadd_rn(__fsub_rn(ps[5], ps[4]), __fsub_rn(ls[5], ls[4]));
+    const ff P = {p0, p0lo};
+    ff A = {0.0f, 0.0f}, B = {0.0f, 0.0f};
+    float C = 0.0f;
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        const ff d = ff_sub(ff{ps[s], ls[s]}, P);
+        A = ff_add(A, d);
+        B = ff_add(B, ff_mul_f(d, Ds[s]));
+        C = __fadd_rn(C, Ds[s]);
+    }
+    ff base = ff_add_f(ff_mul_f(P, -ah), jj);
+    t.base = ff_add(base, ff{0.5f * B.hi, 0.5f * B.lo});
+    t.A = A;
+    t.C = C;
+    return t;
+}
+
+// S(D_p) = base + (D_p / 2) A  and  den(D_p) = ah2 + 3 D_p + C / 2.
+__device__ __forceinline__ ff ff_S(const FFTerms &t, float Dp) { return ff_add(t.base, ff_mul_f(t.A, 0.5f * Dp)); }
+__device__ __forceinline__ float ff_den(const FFTerms &t, float ah, float Dp) {
+    return __fadd_rn(__fadd_rn(ah, 3.0f * Dp), 0.5f * t.C);
+}
+
+// FF = true keeps phi as a float-float pair and sums S exactly enough that
+// the update is accurate to the pair's precision; FF = false is plain FP32.
+template <bool FF>
+__global__ void __launch_bounds__(256) k_pass_f(Layout L, const float *__restrict__ sp,
+                                                const float *__restrict__ ah2, const float *__restrict__ jh2,
+                                                float *__restrict__ phi, float *__restrict__ phlo,
+                                                float *__restrict__ D, int colour, int lim, float larsen_n,
+                                                float omega, float inv2h, float floor_, int local_iters) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (j >= L.ny) return;
+    const int i = 2 * t + ((j + k + colour) & 1);
+    if (i >= L.nx) return;
+    const long long q = L.at(i, j, k);
+    const long long sy = L.px, sz = L.plane;
+    const long long nb[6] = {q - 1, q + 1, q - sy, q + sy, q - sz, q + sz};
+
+    const float p0 = phi[q];
+    float ps[6], Ds[6];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        ps[s] = phi[nb[s]];
+        Ds[s] = D[nb[s]];
+    }
+    const float s_ = sp[q], ah = ah2[q], jj = jh2[q];
+
+    float p0lo = 0.0f, ls[6] = {0, 0, 0, 0, 0, 0};
+    if (FF) {
+        p0lo = phlo[q];
+#pragma unroll
+        for (int s = 0; s < 6; ++s) ls[s] = phlo[nb[s]];
+    }
+    float delta = 0.0f, Dp = 0.0f;
+    if (FF) {
+        const FFTerms T = ff_terms(p0, p0lo, ps, ls, Ds, ah, jj);
+        for (int r = 0; r < local_iters; ++r) {
+            Dp = knudsen_D_f(T.gx, T.gy, T.gz, inv2h, s_, __fadd_rn(p0, delta), floor_, lim, larsen_n);
+            const ff S = ff_S(T, Dp);
+            delta = __fadd_rn(S.hi, S.lo) / ff_den(T, ah, Dp);
+        }
+        const ff nw = ff_add_f(ff{p0, p0lo}, __fmul_rn(omega, delta));
+        phi[q] = nw.hi;
+        phlo[q] = nw.lo;
+    } else {
+        // plain single precision (the bulk sweeps)
+        const float gx = __fsub_rn(ps[1], ps[0]), gy = __fsub_rn(ps[3], ps[2]), gz = __fsub_rn(ps[5], ps[4]);
+        float A = 0.0f, B = 0.0f, C = 0.0f;
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+            const float d = __fsub_rn(ps[s], p0);
+            A = __fadd_rn(A, d);
+            B = fmaf(Ds[s], d, B);
+            C = __fadd_rn(C, Ds[s]);
+        }
+        const float base = fmaf(0.5f, B, fmaf(-ah, p0, jj));
+        for (int r = 0; r < local_iters; ++r) {
+            Dp = knudsen_D_f(gx, gy, gz, inv2h, s_, __fadd_rn(p0, delta), floor_, lim, larsen_n);
+            const float S = fmaf(0.5f * Dp, A, base);
+            const float den = __fadd_rn(__fadd_rn(ah, 3.0f * Dp), 0.5f * C);
+            delta = S / den;
+        }
+        phi[q] = fmaf(omega, delta, p0);
+    }
+    D[q] = Dp;
+}
+
+__global__ void __launch_bounds__(256) k_pass_d(Layout L, const double *__restrict__ sp,
+                                                const double *__restrict__ ah2, const double *__restrict__ jh2,
+                                                double *__restrict__ phi, double *__restrict__ D, int colour,
+                                                int lim, double larsen_n, double omega, double inv2h,
+                                                double floor_, int local_iters) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (j >= L.ny) return;
+    const int i = 2 * t + ((j + k + colour) & 1);
+    if (i >= L.nx) return;
+    const long long q = L.at(i, j, k);
+    const long long sy = L.px, sz = L.plane;
+    const long long nb[6] = {q - 1, q + 1, q - sy, q + sy, q - sz, q + sz};
+    const double p0 = phi[q];
+    double ps[6], Ds[6];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        ps[s] = phi[nb[s]];
+        Ds[s] = D[nb[s]];
+    }
+    const double s_ = sp[q], ah = ah2[q], jj = jh2[q];
+    const double gx = ps[1] - ps[0], gy = ps[3] - ps[2], gz = ps[5] - ps[4];
+    double A = 0.0, B = 0.0, C = 0.0;
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        const double d = ps[s] - p0;
+        A += d;
+        B = fma(Ds[s], d, B);
+        C += Ds[s];
+    }
+    const double base = fma(0.5, B, fma(-ah, p0, jj));
+    double delta = 0.0, Dp = 0.0;
+    for (int r = 0; r < local_iters; ++r) {
+        Dp = knudsen_D_d(gx, gy, gz, inv2h, s_, p0 + delta, floor_, lim, larsen_n);
+        const double S = fma(0.5 * Dp, A, base);
+        const double den = (ah + 3.0 * Dp) + 0.5 * C;
+        delta = S / den;
+    }
+    phi[q] = fma(omega, delta, p0);
+    D[q] = Dp;
+}
+
+// ---------------------------------------------------------------------------
+// Residual (Eq. 37) with D recomputed from the current phi.
+// ---------------------------------------------------------------------------
+__global__ void k_fresh_D_f(Layout L, const float *__restrict__ sp, const float *__restrict__ phi,
+                            const float *__restrict__ phlo, float *__restrict__ Df, int lim, float larsen_n,
+                            float inv2h, float floor_) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= L.nx || j >= L.ny) return;
+    const long long q = L.at(i, j, k);
+    const long long sy = L.px, sz = L.plane;
+    float lxm = 0, lxp = 0, lym = 0, lyp = 0, lzm = 0, lzp = 0;
+    if (phlo) {
+        lxm = phlo[q - 1]; lxp = phlo[q + 1]; lym = phlo[q - sy]; lyp = phlo[q + sy];
+        lzm = phlo[q - sz]; lzp = phlo[q + sz];
+    }
+    const float gx = __fadd_rn(__fsub_rn(phi[q + 1], phi[q - 1]), __fsub_rn(lxp, lxm));
+    const float gy = __fadd_rn(__fsub_rn(phi[q + sy], phi[q - sy]), __fsub_rn(lyp, lym));
+    const float gz = __fadd_rn(__fsub_rn(phi[q + sz], phi[q - sz]), __fsub_rn(lzp, lzm));
+    Df[q] = knudsen_D_f(gx, gy, gz, inv2h, sp[q], phi[q], floor_, lim, larsen_n);
+}
+
+__global__ void k_fresh_D_d(Layout L, const double *__restrict__ sp, const double *__restrict__ phi,
+                            double *__restrict__ Df, int lim, double larsen_n, double inv2h, double floor_) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= L.nx || j >= L.ny) return;
+    const long long q = L.at(i, j, k);
+    const long long sy = L.px, sz = L.plane;
+    Df[q] = knudsen_D_d(phi[q + 1] - phi[q - 1], phi[q + sy] - phi[q - sy], phi[q + sz] - phi[q - sz], inv2h,
+                        sp[q], phi[q], floor_, lim, larsen_n);
+}
+
+// Per-voxel residual R_p dl^2 = jh2 - ah2 phi_p + sum_s D_ps (phi_s - phi_p)
+// in float-float; squares and the source squares summed in double.
+__global__ void __launch_bounds__(256) k_residual_f(Layout L, const float *__restrict__ ah2,
+                                                    const float *__restrict__ jh2, const float *__restrict__ phi,
+                                                    const float *__restrict__ phlo, const float *__restrict__ Df,
+                                                    const float *__restrict__ Dghost, int margin,
+                                                    double *__restrict__ partials) {
+    __shared__ double sh[32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    double r2 = 0.0, j2 = 0.0;
+    if (i < L.nx && j < L.ny) {
+        const long long q = L.at(i, j, k);
+        const long long sy = L.px, sz = L.plane;
+        const long long nb[6] = {q - 1, q + 1, q - sy, q + sy, q - sz, q + sz};
+        const bool onface[6] = {i == 0, i == L.nx - 1, j == 0, j == L.ny - 1, k == 0, k == L.nz - 1};
+        float ps[6], ls[6], Ds[6];
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+            ps[s] = phi[nb[s]];
+            ls[s] = phlo ? phlo[nb[s]] : 0.0f;
+            // ghost neighbours keep their Dirichlet D (never recomputed)
+            Ds[s] = onface[s] ? Dghost[nb[s]] : Df[nb[s]];
+        }
+        const float ah = ah2[q];
+        const FFTerms T = ff_terms(phi[q], phlo ? phlo[q] : 0.0f, ps, ls, Ds, ah, jh2[q]);
+        const ff S = ff_S(T, Df[q]);
+        const double Sd = ff_to_d(S);
+        const bool in = i >= margin && i < L.nx - margin && j >= margin && j < L.ny - margin && k >= margin &&
+                        k < L.nz - margin;
+        r2 = in ? Sd * Sd : 0.0;
+        const double jd = (double)jh2[q];
+        j2 = jd * jd;
+    }
+    r2 = block_sum(r2, sh);
+    __syncthreads();
+    j2 = block_sum(j2, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+        partials[2 * b] = r2;
+        partials[2 * b + 1] = j2;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_residual_d(Layout L, const double *__restrict__ ah2,
+                                                    const double *__restrict__ jh2, const double *__restrict__ phi,
+                                                    const double *__restrict__ Df, const double *__restrict__ Dghost,
+                                                    int margin, double *__restrict__ partials) {
+    __shared__ double sh[32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    double r2 = 0.0, j2 = 0.0;
+    if (i < L.nx && j < L.ny) {
+        const long long q = L.at(i, j, k);
+        const long long sy = L.px, sz = L.plane;
+        const long long nb[6] = {q - 1, q + 1, q - sy, q + sy, q - sz, q + sz};
+        const bool onface[6] = {i == 0, i == L.nx - 1, j == 0, j == L.ny - 1, k == 0, k == L.nz - 1};
+        const double p0 = phi[q], Dp = Df[q];
+        double A = 0.0, B = 0.0;
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+            const double Dn = onface[s] ? Dghost[nb[s]] : Df[nb[s]];
+            const double d = phi[nb[s]] - p0;
+            A += d;
+            B = fma(Dn, d, B);
+        }
+        const double S = fma(0.5 * Dp, A, fma(0.5, B, fma(-ah2[q], p0, jh2[q])));
+        const bool in = i >= margin && i < L.nx - margin && j >= margin && j < L.ny - margin && k >= margin &&
+                        k < L.nz - margin;
+        r2 = in ? S * S : 0.0;
+        j2 = jh2[q] * jh2[q];
+    }
+    r2 = block_sum(r2, sh);
+    __syncthreads();
+    j2 = block_sum(j2, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
+        partials[2 * b] = r2;
+        partials[2 * b + 1] = j2;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_sumsq(long long n, const float *__restrict__ x,
+                                               double *__restrict__ partials) {
+    __shared__ double sh[32];
+    double a = 0.0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const double v = (double)x[e];
+        a += v * v;
+    }
+    a = block_sum(a, sh);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = 0.0;
+    }
+}
+
+// Input validation counters: [0] bad sigma (NaN/neg/inf), [1] bad albedo, [2] bad j.
+__global__ void __launch_bounds__(256) k_validate(long long n, const float *__restrict__ st,
+                                                  const float *__restrict__ alb, const float *__restrict__ js,
+                                                  double *__restrict__ partials) {
+    __shared__ double sh[32];
+    double bs = 0.0, ba = 0.0;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        if (st) {
+            const float s = st[e];
+            bs += !(s >= 0.0f && s <= 3.0e38f) ? 1.0 : 0.0;
+        }
+        if (alb) {
+            const float a = alb[e];
+            ba += !(a >= 0.0f && a <= 1.0f) ? 1.0 : 0.0;
+        }
+        if (js) {
+            const float v = js[e];
+            bs += !(v >= 0.0f && v <= 3.0e38f) ? 1.0 : 0.0;
+        }
+    }
+    bs = block_sum(bs, sh);
+    __syncthreads();
+    ba = block_sum(ba, sh);
+    if (threadIdx.x == 0) {
+        partials[2 * blockIdx.x] = bs;
+        partials[2 * blockIdx.x + 1] = ba;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Single-scatter source.
+// ---------------------------------------------------------------------------
+
+// Light along -z with step h/2: the samples at quarter-voxel offsets blend the
+// two nearest centres 3:1 and 1:3, so the optical depth above voxel k is the
+// trapezoid sum over the centres above it plus half a voxel of the top
+// centre -- an exclusive scan down each column.
+__global__ void k_bake_scan_negz(Layout L, const float *__restrict__ st, const float *__restrict__ alb,
+                                 float *__restrict__ js, float h, float radiance, int accumulate) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= L.nx || j >= L.ny) return;
+    const long long col = (long long)j * L.nx + i;
+    const long long sk = (long long)L.nx * L.ny;
+    double tau = 0.0;
+    float above = 0.0f;
+    for (int k = L.nz - 1; k >= 0; --k) {
+        const long long v = col + (long long)k * sk;
+        const float s = st[v];
+        tau += (k == L.nz - 1) ? 0.5 * (double)h * (double)s : 0.5 * (double)h * ((double)s + (double)above);
+        above = s;
+        const float q = radiance * (alb[v] * s) * expf(-(float)tau);
+        js[v] = accumulate ? js[v] + q : q;
+    }
+}
+
+__device__ __forceinline__ float sigma_trilinear(const Layout &L, const float *__restrict__ st, float h, float x,
+                                                 float y, float z) {
+    float u[3] = {x / h - 0.5f, y / h - 0.5f, z / h - 0.5f};
+    const int n[3] = {L.nx, L.ny, L.nz};
+    int i0[3];
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float w = fminf(fmaxf(u[a], 0.0f), (float)(n[a] - 1));
+        int b = (int)floorf(w);
+        b = min(max(b, 0), max(n[a] - 2, 0));
+        i0[a] = b;
+        f[a] = (n[a] == 1) ? 0.0f : w - (float)b;
+    }
+    const int i1 = min(i0[0] + 1, L.nx - 1), j1 = min(i0[1] + 1, L.ny - 1), k1 = min(i0[2] + 1, L.nz - 1);
+    const long long sy = L.nx, sz = (long long)L.nx * L.ny;
+    const long long b00 = i0[2] * sz + i0[1] * sy, b01 = i0[2] * sz + j1 * sy;
+    const long long b10 = k1 * sz + i0[1] * sy, b11 = k1 * sz + j1 * sy;
+    const float c00 = __ldg(st + b00 + i0[0]) * (1.0f - f[0]) + __ldg(st + b00 + i1) * f[0];
+    const float c01 = __ldg(st + b01 + i0[0]) * (1.0f - f[0]) + __ldg(st + b01 + i1) * f[0];
+    const float c10 = __ldg(st + b10 + i0[0]) * (1.0f - f[0]) + __ldg(st + b10 + i1) * f[0];
+    const float c11 = __ldg(st + b11 + i0[0]) * (1.0f - f[0]) + __ldg(st + b11 + i1) * f[0];
+    const float c0 = c00 * (1.0f - f[1]) + c01 * f[1];
+    const float c1 = c10 * (1.0f - f[1]) + c11 * f[1];
+    return c0 * (1.0f - f[2]) + c1 * f[2];
+}
+
+// General march: from the voxel centre towards the light, samples at the
+// midpoints of steps of length `step`, the last step shortened to end at the
+// grid boundary (or at a point light inside the grid).
+__global__ void __launch_bounds__(256) k_bake_march(Layout L, const float *__restrict__ st,
+                                                    const float *__restrict__ alb, float *__restrict__ js, float h,
+                                                    float wx, float wy, float wz, float px, float py, float pz,
+                                                    int point, float value, float step, int accumulate) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= L.nx || j >= L.ny) return;
+    const long long v = ((long long)k * L.ny + j) * L.nx + i;
+    const float x[3] = {(i + 0.5f) * h, (j + 0.5f) * h, (k + 0.5f) * h};
+    float w[3] = {wx, wy, wz};
+    float r = 0.0f;
+    if (point) {
+        const float d[3] = {px - x[0], py - x[1], pz - x[2]};
+        r = sqrtf(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        if (r > 0.0f) {
+            w[0] = d[0] / r; w[1] = d[1] / r; w[2] = d[2] / r;
+        }
+    }
+    const float ext[3] = {L.nx * h, L.ny * h, L.nz * h};
+    float len = INFINITY;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (w[a] > 0.0f) len = fminf(len, (ext[a] - x[a]) / w[a]);
+        else if (w[a] < 0.0f) len = fminf(len, (0.0f - x[a]) / w[a]);
+    }
+    if (point) len = (r > 0.0f) ? fminf(len, r) : 0.0f;
+    double tau = 0.0;
+    const int m_full = (int)floorf(len / step);
+    for (int m = 0; m < m_full; ++m) {
+        const float t = ((float)m + 0.5f) * step;
+        tau += (double)(sigma_trilinear(L, st, h, x[0] + t * w[0], x[1] + t * w[1], x[2] + t * w[2]) * step);
+    }
+    const float rem = len - (float)m_full * step;
+    if (rem > 1e-6f * step) {
+        const float t = (float)m_full * step + 0.5f * rem;
+        tau += (double)(sigma_trilinear(L, st, h, x[0] + t * w[0], x[1] + t * w[1], x[2] + t * w[2]) * rem);
+    }
+    float q = value * (alb[v] * st[v]) * expf(-(float)tau);
+    if (point) {
+        const float rr = fmaxf(r, 0.5f * h);
+        q = q / (4.0f * 3.14159265358979f * rr * rr);
+    }
+    js[v] = accumulate ? js[v] + q : q;
+}
+
+inline dim3 pass_grid(const Layout &L, dim3 blk) {
+    const int half = (L.nx + 1) / 2;
+    return dim3((half + blk.x - 1) / blk.x, (L.ny + blk.y - 1) / blk.y, L.nz);
+}
+
+inline dim3 vox_block() { return dim3(32, 8, 1); }
+inline dim3 vox_grid(const Layout &L) {
+    return dim3((L.nx + 31) / 32, (L.ny + 7) / 8, L.nz);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+cudaError_t launch_prep_f(const Layout &L, const Fields &f, float sigma_eps, float h2, cudaStream_t s) {
+    k_prep_f<<<vox_grid(L), vox_block(), 0, s>>>(L, f.sigma_t, f.albedo, f.jsrc, f.sp, f.ah2, f.jh2, sigma_eps, h2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_d(const Layout &L, const Fields &f, double sigma_eps, double h2, cudaStream_t s) {
+    k_prep_d<<<vox_grid(L), vox_block(), 0, s>>>(L, f.sigma_t, f.albedo, f.jsrc, f.sp64, f.ah264, f.jh264,
+                                                  sigma_eps, h2);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_f(const Layout &L, float *phi, float *phlo, float *D, double phi0, double D0, double phi_b,
+                          double D_b, cudaStream_t s) {
+    const int blk = 256;
+    const long long nb = (L.total + blk - 1) / blk;
+    k_init<float><<<(unsigned)nb, blk, 0, s>>>(L, phi, phlo, D, (float)phi0, (float)D0, (float)phi_b, (float)D_b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_d(const Layout &L, double *phi, double *D, double phi0, double D0, double phi_b, double D_b,
+                          cudaStream_t s) {
+    const int blk = 256;
+    const long long nb = (L.total + blk - 1) / blk;
+    k_init<double><<<(unsigned)nb, blk, 0, s>>>(L, phi, nullptr, D, phi0, D0, phi_b, D_b);
+    return cudaGetLastError();
+}
+
+static dim3 packed_grid(const Layout &L) { return dim3((L.nx + 2 + 127) / 128, L.ny + 2, L.nz + 2); }
+
+cudaError_t launch_unpack_to_f(const Layout &L, const double *src, float *hi, float *lo, cudaStream_t s) {
+    k_unpack_to_f<<<packed_grid(L), 128, 0, s>>>(L, src, hi, lo);
+    return cudaGetLastError();
+}
+cudaError_t launch_unpack_to_d(const Layout &L, const double *src, double *dst, cudaStream_t s) {
+    k_unpack_to_d<<<packed_grid(L), 128, 0, s>>>(L, src, dst);
+    return cudaGetLastError();
+}
+cudaError_t launch_pack_from_f(const Layout &L, const float *hi, const float *lo, double *dst, cudaStream_t s) {
+    k_pack_from_f<<<packed_grid(L), 128, 0, s>>>(L, hi, lo, dst);
+    return cudaGetLastError();
+}
+cudaError_t launch_pack_from_d(const Layout &L, const double *src, double *dst, cudaStream_t s) {
+    k_pack_from_d<<<packed_grid(L), 128, 0, s>>>(L, src, dst);
+    return cudaGetLastError();
+}
+cudaError_t launch_f_to_d(const Layout &L, const float *hi, const float *lo, double *dst, cudaStream_t s) {
+    k_f_to_d<<<(unsigned)((L.total + 255) / 256), 256, 0, s>>>(L.total, hi, lo, dst);
+    return cudaGetLastError();
+}
+cudaError_t launch_d_to_f(const Layout &L, const double *src, float *hi, float *lo, cudaStream_t s) {
+    k_d_to_f<<<(unsigned)((L.total + 255) / 256), 256, 0, s>>>(L.total, src, hi, lo);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pass(Family fam, const Layout &L, const Fields &f, const PassParams &p, int colour,
+                        cudaStream_t s) {
+    const dim3 blk(32, 8, 1);
+    const dim3 grd = pass_grid(L, blk);
+    switch (fam) {
+    case FAM_F32:
+        k_pass_f<false><<<grd, blk, 0, s>>>(L, f.sp, f.ah2, f.jh2, f.phi, nullptr, f.D, colour, p.lim,
+                                           (float)p.larsen_n, (float)p.omega, (float)p.inv2h, (float)p.floor_,
+                                           p.local_iters);
+        break;
+    case FAM_FF:
+        k_pass_f<true><<<grd, blk, 0, s>>>(L, f.sp, f.ah2, f.jh2, f.phi, f.phlo, f.D, colour, p.lim,
+                                          (float)p.larsen_n, (float)p.omega, (float)p.inv2h, (float)p.floor_,
+                                          p.local_iters);
+        break;
+    case FAM_F64:
+        k_pass_d<<<grd, blk, 0, s>>>(L, f.sp64, f.ah264, f.jh264, f.phi64, f.D64, colour, p.lim, p.larsen_n,
+                                    p.omega, p.inv2h, p.floor_, p.local_iters);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+int reduction_blocks(const Layout &L) {
+    const dim3 g = vox_grid(L);
+    const long long n = (long long)g.x * g.y * g.z;
+    return (int)(n > 4096 ? n : 4096);
+}
+
+cudaError_t launch_residual(Family fam, const Layout &L, const Fields &f, const PassParams &p, int margin,
+                            cudaStream_t s) {
+    const dim3 grd = vox_grid(L), blk = vox_block();
+    const int nblocks = (int)(grd.x * grd.y * grd.z);
+    if (nblocks > f.partial_cap) return cudaErrorInvalidValue;
+    if (fam == FAM_F64) {
+        k_fresh_D_d<<<grd, blk, 0, s>>>(L, f.sp64, f.phi64, f.Df64, p.lim, p.larsen_n, p.inv2h, p.floor_);
+        k_residual_d<<<grd, blk, 0, s>>>(L, f.ah264, f.jh264, f.phi64, f.Df64, f.D64, margin, f.partials);
+    } else {
+        const float *lo = fam == FAM_FF ? f.phlo : nullptr;
+        k_fresh_D_f<<<grd, blk, 0, s>>>(L, f.sp, f.phi, lo, f.Df, p.lim, (float)p.larsen_n, (float)p.inv2h,
+                                        (float)p.floor_);
+        k_residual_f<<<grd, blk, 0, s>>>(L, f.ah2, f.jh2, f.phi, lo, f.Df, f.D, margin, f.partials);
+    }
+    k_finalize<<<1, kRedThreads, 0, s>>>(f.partials, nblocks, f.result);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sumsq_source(const Layout &L, const Fields &f, cudaStream_t s) {
+    const long long n = (long long)L.nx * L.ny * L.nz;
+    int nb = (int)((n + 255) / 256);
+    if (nb > 1024) nb = 1024;
+    if (nb > f.partial_cap) nb = f.partial_cap;
+    k_sumsq<<<nb, 256, 0, s>>>(n, f.jsrc, f.partials);
+    k_finalize<<<1, kRedThreads, 0, s>>>(f.partials, nb, f.result);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_validate(long long n, const Fields &f, const float *st, const float *alb, const float *js,
+                            cudaStream_t s) {
+    int nb = (int)((n + 255) / 256);
+    if (nb > 1024) nb = 1024;
+    if (nb > f.partial_cap) nb = f.partial_cap;
+    if (nb < 1) nb = 1;
+    k_validate<<<nb, 256, 0, s>>>(n, st, alb, js, f.partials);
+    k_finalize<<<1, kRedThreads, 0, s>>>(f.partials, nb, f.result);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bake_scan_negz(const Layout &L, const Fields &f, float h, float radiance, int accumulate,
+                                  cudaStream_t s) {
+    const dim3 blk(32, 4, 1);
+    const dim3 grd((L.nx + 31) / 32, (L.ny + 3) / 4, 1);
+    k_bake_scan_negz<<<grd, blk, 0, s>>>(L, f.sigma_t, f.albedo, f.jsrc, h, radiance, accumulate);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bake_march(const Layout &L, const Fields &f, float h, const double w[3], const double pos[3],
+                              int point, float value, float step, int accumulate, cudaStream_t s) {
+    k_bake_march<<<vox_grid(L), vox_block(), 0, s>>>(L, f.sigma_t, f.albedo, f.jsrc, h, (float)w[0], (float)w[1],
+                                                     (float)w[2], (float)pos[0], (float)pos[1], (float)pos[2], point,
+                                                     value, step, accumulate);
+    return cudaGetLastError();
+}
+
+}  // namespace fld

@@ -1,0 +1,273 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle.
+
+* one red-black iteration from the same state: FP64 kernels to ~1e-12,
+  single-precision and float-float kernels to their arithmetic;
+* the residual of Eq. 37 on the same state;
+* the single-scatter source (column scan and general march, point light);
+* solved fixed points on heterogeneous clouds, ragged and degenerate sizes;
+* error codes for invalid inputs.
+"""
+import numpy as np
+import pytest
+
+import fld_inputs
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+fld = pytest.importorskip("paper_1403_8105_gb300")
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+INNER = (slice(1, -1),) * 3
+
+
+def random_case(shape, seed, vacuum_frac=0.2):
+    rng = np.random.default_rng(seed)
+    sig = rng.uniform(0.5, 40.0, shape).astype(np.float32)
+    sig[rng.uniform(size=shape) < vacuum_frac] = 0.0
+    alb = rng.uniform(0.3, 0.99, shape).astype(np.float32)
+    j = rng.uniform(0.0, 5.0, shape).astype(np.float32)
+    j[sig == 0] = 0.0
+    return sig, alb, j, 1.0 / max(shape)
+
+
+def oracle_problem(sig, alb, j, h, **kw):
+    p = oracle.make_problem(sig, alb, j.astype(np.float64), h, **kw)
+    return p
+
+
+def gpu_grid(sig, alb, j, h):
+    nz, ny, nx = sig.shape
+    g = fld.Grid(nx, ny, nz, h)
+    g.set_medium(sig, alb)
+    g.set_source(j)
+    return g
+
+
+def rel_max(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+# ---------------------------------------------------------------------------
+# one iteration from the same state
+# ---------------------------------------------------------------------------
+
+LIMS = ["lp", "kershaw", "larsen", "sum", "max", "cda"]
+
+
+@pytest.mark.parametrize("limiter", LIMS)
+@pytest.mark.parametrize("local", [1, 2])
+def test_one_iteration_fp64_matches_oracle(limiter, local):
+    sig, alb, j, h = random_case((9, 11, 13), 3)
+    ref = oracle_problem(sig, alb, j, h, limiter=limiter, omega=1.4, local_iters=local, nthreads=1)
+    oracle.init_state(ref)
+    oracle.rb_iteration(ref, 3)                 # a non-trivial state
+    phi0, D0 = ref.phi.copy(), ref.D.copy()
+    oracle.rb_iteration(ref, 1)
+    with gpu_grid(sig, alb, j, h) as g:
+        g.set_state(phi0, D0)
+        p = fld.params(limiter=limiter, precision="fp64", omega=1.4, local_iters=local, warm_start=1)
+        g.iterate(p, 1)
+        phi, D = g.get_state()
+    assert rel_max(phi, ref.phi) <= 1e-12
+    assert rel_max(D, ref.D) <= 1e-12
+
+
+@pytest.mark.parametrize("precision,tol", [("fp32", 3e-6), ("mixed", 3e-6)])
+@pytest.mark.parametrize("limiter", ["lp", "kershaw", "larsen"])
+def test_one_iteration_single_matches_oracle(precision, tol, limiter):
+    sig, alb, j, h = random_case((16, 12, 20), 5)
+    ref = oracle_problem(sig, alb, j, h, limiter=limiter, omega=1.5, local_iters=2, nthreads=1)
+    oracle.init_state(ref)
+    oracle.rb_iteration(ref, 4)
+    if precision == "fp32":
+        ref.phi[...] = ref.phi.astype(np.float32)       # the FP32 family stores phi in float
+    ref.D[...] = ref.D.astype(np.float32)
+    phi0, D0 = ref.phi.copy(), ref.D.copy()
+    oracle.rb_iteration(ref, 1)
+    with gpu_grid(sig, alb, j, h) as g:
+        g.set_state(phi0, D0)
+        p = fld.params(limiter=limiter, precision=precision, omega=1.5, local_iters=2, warm_start=1)
+        g.iterate(p, 1)
+        phi, D = g.get_state()
+    assert rel_max(phi, ref.phi) <= tol
+    assert rel_max(D, ref.D) <= 3e-5
+
+
+# ---------------------------------------------------------------------------
+# residual
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("margin", [0, 2])
+def test_residual_matches_oracle(margin):
+    sig, alb, j, h = random_case((14, 15, 16), 8)
+    ref = oracle_problem(sig, alb, j, h, limiter="lp", omega=1.5, local_iters=2, nthreads=1)
+    oracle.init_state(ref)
+    oracle.rb_iteration(ref, 30)
+    want, _, _ = oracle.residual(ref, margin=margin)
+    with gpu_grid(sig, alb, j, h) as g:
+        g.set_state(ref.phi, ref.D)
+        got64 = g.residual(fld.params(precision="fp64", residual_margin=margin))
+        gotff = g.residual(fld.params(precision="mixed", residual_margin=margin))
+    assert abs(got64 - want) <= 1e-11 * want
+    assert abs(gotff - want) <= 2e-5 * want
+
+
+# ---------------------------------------------------------------------------
+# single-scatter source
+# ---------------------------------------------------------------------------
+
+def test_bake_column_scan_matches_oracle():
+    case = fld_inputs.cloud_case(40, seed=2, albedo=0.95)
+    want = oracle.bake_directional(case.sigma_t, case.alb, case.h, (0, 0, -1), 1.0)
+    with fld.Grid(40, 40, 40, case.h) as g:
+        g.set_medium(case.sigma_t, case.alb)
+        g.bake_directional((0, 0, -1), 1.0)
+        got = g.get_source()
+    assert np.abs(got - want).max() <= 2e-6 * np.abs(want).max()
+
+
+@pytest.mark.parametrize("direction", [(0.3, -0.2, -1.0), (1.0, 0.0, 0.0), (-0.5, 0.7, 0.2)])
+def test_bake_march_matches_oracle(direction):
+    sig, alb = fld_inputs.cloud_medium(24, seed=4, albedo=0.9)
+    h = 1.0 / 24
+    want = oracle.bake_directional(sig, alb, h, direction, 2.0)
+    with fld.Grid(24, 24, 24, h) as g:
+        g.set_medium(sig, alb)
+        g.bake_directional(direction, 2.0)
+        got = g.get_source()
+    assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
+
+
+def test_bake_point_and_accumulate_match_oracle():
+    sig, alb = fld_inputs.cloud_medium(20, seed=6, albedo=0.85)
+    h = 1.0 / 20
+    pos = (0.3, 0.6, 1.2)
+    want = oracle.bake_point(sig, alb, h, pos, 3.0) + oracle.bake_directional(sig, alb, h, (0, 0, -1), 1.0)
+    with fld.Grid(20, 20, 20, h) as g:
+        g.set_medium(sig, alb)
+        g.bake_point(pos, 3.0)
+        g.bake_directional((0, 0, -1), 1.0, accumulate=1)
+        got = g.get_source()
+    assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
+
+
+# ---------------------------------------------------------------------------
+# fixed points
+# ---------------------------------------------------------------------------
+
+def _oracle_fixed_point(sig, alb, j, h, limiter="lp", omega=1.7, tol=1e-11):
+    ref = oracle_problem(sig, alb, j, h, limiter=limiter, omega=omega, local_iters=2)
+    oracle.init_state(ref)
+    it, rel, _ = oracle.solve(ref, tol=tol, max_iters=400000, check_every=20)
+    assert rel <= tol
+    return ref
+
+
+@pytest.mark.parametrize("shape", [(24, 24, 24), (23, 17, 29)])
+def test_cloud_fixed_point_mixed_and_fp64(shape):
+    nz, ny, nx = shape
+    sig, alb = fld_inputs.cloud_medium(nx, seed=11, albedo=0.95, ny=ny, nz=nz)
+    h = 1.0 / max(shape)
+    q = oracle.bake_directional(sig, alb, h, (0, 0, -1), 1.0).astype(np.float32)
+    ref = _oracle_fixed_point(sig, alb, q, h)
+    for precision, tol, bound in (("mixed", 1e-7, 1e-5), ("fp64", 1e-10, 1e-8)):
+        with gpu_grid(sig, alb, q, h) as g:
+            p = fld.params(limiter="lp", precision=precision, tol=tol, omega=1.7, local_iters=2,
+                           check_every=32, max_iters=400000)
+            r = g.solve(p)
+            assert r.status == fld.FLD_OK, r.as_dict()
+            phi, _ = g.get_state()
+        err = np.linalg.norm(phi[INNER] - ref.phi[INNER]) / np.linalg.norm(ref.phi[INNER])
+        assert err <= bound, (precision, err)
+
+
+def test_point_source_fp64_c1_setup():
+    # 32^3, sigma_t = 10, sigma_s = 9, unit point source at (16,16,16),
+    # phi = 0 ghosts, phi0 = 1e-6, LP, FP64 to 1e-10.
+    ps = fld_inputs.point_source_medium(32, 10.0, 9.0, centre=(16, 16, 16))
+    ref = oracle_problem(ps.sigma_t, ps.albedo, ps.j, ps.h, limiter="lp", omega=1.7, local_iters=2)
+    oracle.init_state(ref, phi0=1e-6, phi_b=0.0)
+    it, rel, _ = oracle.solve(ref, tol=1e-10, max_iters=100000, check_every=10)
+    with gpu_grid(ps.sigma_t, ps.albedo, ps.j, ps.h) as g:
+        p = fld.params(limiter="lp", precision="fp64", tol=1e-10, omega=1.7, local_iters=2, check_every=10,
+                       phi0=1e-6, phi_b=0.0, max_iters=100000)
+        r = g.solve(p)
+        assert r.status == fld.FLD_OK
+        phi, _ = g.get_state()
+    err = np.linalg.norm(phi[INNER] - ref.phi[INNER]) / np.linalg.norm(ref.phi[INNER])
+    assert err <= 1e-8, err
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (7, 1, 1), (1, 5, 3), (9, 33, 17)])
+def test_degenerate_and_ragged_sizes(shape):
+    sig, alb, j, h = random_case(shape, 13, vacuum_frac=0.0)
+    ref = _oracle_fixed_point(sig, alb, j, h, omega=1.5, tol=1e-12)
+    with gpu_grid(sig, alb, j, h) as g:
+        r = g.solve(fld.params(precision="mixed", tol=1e-7, omega=1.5, check_every=8, max_iters=100000))
+        assert r.status == fld.FLD_OK, r.as_dict()
+        phi, _ = g.get_state()
+    assert rel_max(phi[INNER], ref.phi[INNER]) <= 1e-6
+
+
+def test_no_emission_stays_zero():
+    shape = (6, 7, 8)
+    sig = np.full(shape, 3.0, np.float32)
+    alb = np.full(shape, 0.5, np.float32)
+    with gpu_grid(sig, alb, np.zeros(shape, np.float32), 1.0 / 8) as g:
+        r = g.solve(fld.params(precision="mixed", max_iters=64, check_every=16))
+        phi, D = g.get_state()
+    assert r.status == fld.FLD_OK
+    assert np.all(phi == 0.0) and np.all(np.isfinite(D))
+
+
+# ---------------------------------------------------------------------------
+# errors
+# ---------------------------------------------------------------------------
+
+def test_invalid_inputs_are_rejected():
+    shape = (4, 4, 4)
+    ok_sig = np.ones(shape, np.float32)
+    ok_alb = np.full(shape, 0.5, np.float32)
+    with fld.Grid(4, 4, 4, 0.25) as g:
+        with pytest.raises(fld.FldError) as e:
+            g.solve(fld.params())
+        assert e.value.status == fld.FLD_ERR_STATE
+        for bad_sig, bad_alb in ((-ok_sig, ok_alb), (ok_sig * np.nan, ok_alb), (ok_sig, ok_alb + 1.0)):
+            with pytest.raises(fld.FldError) as e:
+                g.set_medium(bad_sig.astype(np.float32), bad_alb.astype(np.float32))
+            assert e.value.status == fld.FLD_ERR_INVALID_ARG
+        g.set_medium(ok_sig, ok_alb)
+        with pytest.raises(fld.FldError) as e:
+            g.set_source(-np.ones(shape, np.float32))
+        assert e.value.status == fld.FLD_ERR_INVALID_ARG
+        for bad in (dict(omega=2.5), dict(limiter=9), dict(precision=7), dict(local_iters=100)):
+            with pytest.raises(fld.FldError) as e:
+                g.solve(fld.params(**bad))
+            assert e.value.status == fld.FLD_ERR_INVALID_ARG
+        g.set_source(np.ones(shape, np.float32))
+        r = g.solve(fld.params(max_iters=8, check_every=4, tol=0.0))
+        assert r.status == fld.FLD_ERR_NOT_CONVERGED and r.iterations == 8
+        # no emission at all: phi = 0 is the exact solution from the start
+        g.set_source(np.zeros(shape, np.float32))
+        r = g.solve(fld.params(max_iters=8, check_every=4, tol=0.0))
+        assert r.status == fld.FLD_OK and r.iterations == 0
+
+
+def test_device_pointers_through_torch():
+    sig, alb, j, h = random_case((12, 10, 14), 21)
+    ref = _oracle_fixed_point(sig, alb, j, h, omega=1.5, tol=1e-11)
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        g = fld.Grid(14, 10, 12, h, stream=stream.cuda_stream)
+        g.set_medium(torch.from_numpy(sig).to(dev), torch.from_numpy(alb).to(dev))
+        g.set_source(torch.from_numpy(j).to(dev))
+        g.solve(fld.params(precision="mixed", tol=1e-7, omega=1.5, check_every=16, max_iters=100000))
+        phi = torch.empty((14, 12, 16), dtype=torch.float64, device=dev)
+        fld.fld_get_state(g.handle, phi, None)
+        stream.synchronize()
+        g.close()
+    assert rel_max(phi.cpu().numpy()[INNER], ref.phi[INNER]) <= 1e-6
