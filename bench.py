@@ -1,0 +1,456 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 FLD solver.
+
+Workload (one step = the whole hot path on one synthetic volume):
+  128^3 fBm sphere cloud (seed 0, 5 octaves, base frequency 4,
+  sigma_t = 200 max(0, fbm - 0.35)^1.5, vacuum outside r = 0.45), albedo
+  0.95, unit directional light along -z baked by the transmittance march
+  (step h/2), Levermore-Pomraning limiter, solved with red-black SOR to a
+  relative residual of 1e-6 (single-precision sweeps, float-float correction
+  sweeps once single precision stalls).  Per step: set_medium from
+  device-resident arrays, bake, solve.
+
+Metric: voxel-updates/s (one update = one phi_p update; one red-black
+iteration = nx*ny*nz updates) over the timed solves, plus time to the
+residual.  `--gpus N` under torchrun runs N independent replicas (one GPU
+per rank, per-rank seed); the value is the sum of all ranks' updates over
+the slowest rank's time.
+
+`--impl reference` times the FP64 CPU oracle on the same workload (bounded
+samples of its iterations) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "FLD voxel-updates/s & time to rel. residual 1e-6 (% HBM peak); p50/p99 solve latency"
+UNIT = "voxel-updates/s"
+# algorithmic bytes per voxel update of one sweep (D stored, as in Algorithm 1):
+# reads phi, D, sigma', sigma_a' dl^2, j dl^2 and writes phi, D (4 bytes each);
+# the float-float correction sweep also reads and writes the low word of phi.
+BYTES_PER_UPDATE = {"fp32": 28, "ff": 36}
+KERNEL_NAME = {"fp32": "k_pass_f<false> (single-precision red/black pass)",
+               "ff": "k_pass_f<true> (float-float correction pass)"}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--n", type=int, default=128)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--omega", type=float, default=0.0, help="SOR factor (0 = library default)")
+    ap.add_argument("--check-every", type=int, default=256)
+    ap.add_argument("--max-iters", type=int, default=600000)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample length")
+    ap.add_argument("--no-extras", action="store_true", help="skip cpu baseline / 256^3 roofline / e2e")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# ranks
+# ---------------------------------------------------------------------------
+
+class Ranks:
+    def __init__(self, use_cuda: bool):
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+        self.device = None
+        if self.world > 1:
+            import torch
+            import torch.distributed as dist
+            backend = "nccl" if use_cuda else "gloo"
+            if use_cuda:
+                torch.cuda.set_device(self.local)
+                self.device = torch.device("cuda", self.local)
+            dist.init_process_group(backend=backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist:
+            self.dist.barrier()
+
+    def reduce(self, value: float, op: str) -> float:
+        if not self.dist:
+            return value
+        import torch
+        t = torch.tensor([value], dtype=torch.float64, device=self.device or "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX if op == "max" else self.dist.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.dist:
+            self.dist.destroy_process_group()
+
+
+class _OneRank:
+    rank, world, local = 0, 1, 0
+
+
+def reduce_ranks(values, world_max_time):
+    """Whole-job throughput: all ranks' updates over the slowest rank's time."""
+    return sum(values) / world_max_time if world_max_time > 0 else 0.0
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, local_index: int):
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+        ids = [x.strip() for x in vis.split(",")] if vis else []
+        self.gpu = ids[local_index] if local_index < len(ids) else str(local_index)
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="fld_clocks_", suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except OSError:
+            return None
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
+
+
+def traffic_record(kernel_key: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, valid only while
+    the kernel source is unchanged since the capture (source hash recorded)."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
+    src = os.path.join(ROOT, "paper_1403_8105_gb300", "csrc", "fld_kernels.cu")
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        for line in open(path):
+            f = dict(kv.split("=", 1) for kv in line.split() if "=" in kv)
+            if f.get("kernel") == kernel_key and f.get("workload") == workload and f.get("src") == digest:
+                return float(f["bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+
+def workload_inputs(n: int, seed: int):
+    import fld_inputs
+    sig, alb = fld_inputs.cloud_medium(n, seed=seed, albedo=0.95)
+    return sig, alb
+
+
+def workload_config(args, ranks):
+    return {
+        "workload": f"C2 heterogeneous fBm sphere cloud {args.n}^3 (unit cube, h=1/{args.n}), albedo 0.95, "
+                    f"unit directional light along -z (march step h/2), Levermore-Pomraning, "
+                    f"rel. residual {args.tol:g}",
+        "grid": [args.n, args.n, args.n],
+        "seed": "0 + rank",
+        "precision": "mixed: fp32 sweeps, float-float correction sweeps after the fp32 stall",
+        "scheme": "red-black SOR (Algorithm 1), self-consistent point update (local_iters=2)",
+        "limiter": "levermore-pomraning",
+        "tol": args.tol,
+        "l2": "flushed (256 MB write) before every timed step; the 128^3 working set (~70 MB) is L2-resident "
+              "within a solve",
+        "parallelism": f"replicas x{ranks.world}" if ranks.world > 1 else "1 GPU",
+    }
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    import paper_1403_8105_gb300 as fld
+
+    ranks = Ranks(use_cuda=True)
+    torch.cuda.set_device(ranks.local)
+    dev = torch.device("cuda", ranks.local)
+    fld.load(build_if_missing=True)
+    n = args.n
+    h = 1.0 / n
+    nvox = n ** 3
+    sig_np, alb_np = workload_inputs(n, seed=ranks.rank)
+    sig = torch.from_numpy(sig_np).to(dev)
+    alb = torch.from_numpy(alb_np).to(dev)
+    torch.cuda.synchronize()          # inputs resident before the grid's stream reads them
+    stream = torch.cuda.Stream(device=dev)
+    g = fld.Grid(n, n, n, h, stream=stream.cuda_stream)
+    p = fld.params(limiter="lp", precision="mixed", tol=args.tol, omega=args.omega, local_iters=2,
+                   check_every=args.check_every, max_iters=args.max_iters)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
+
+    def step():
+        g.set_medium(sig, alb)
+        g.bake_directional((0.0, 0.0, -1.0), 1.0)
+        return g.solve(p)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+        stream.synchronize()
+
+        sampler = ClockSampler(ranks.local)
+        ranks.barrier()
+        torch.cuda.synchronize()
+        sampler.start()
+        results, step_ms = [], []
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            stream.synchronize()
+            e0.record(stream)
+            results.append(step())
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+        torch.cuda.synchronize()
+        ranks.barrier()
+        clocks = sampler.stop()
+
+    total_ms = sum(step_ms)
+    updates = sum(r.iterations for r in results) * nvox
+    max_ms = ranks.reduce(total_ms, "max")
+    all_updates = ranks.reduce(float(updates), "sum")
+    value = all_updates / (max_ms / 1e3)
+    launches = sum(int(r.kernels) + 3 for r in results)   # + set_medium validation (2) + bake (1)
+
+    # sweep kernel timing inside the timed solves (graph blocks hold only passes)
+    fam_ms = {"fp32": sum(r.ms_sweep_fp32 for r in results), "ff": sum(r.ms_sweep_corr for r in results)}
+    fam_it = {"fp32": sum(r.iterations_fp32 for r in results), "ff": sum(r.iterations_corr for r in results)}
+    dom = max(fam_ms, key=lambda k: fam_ms[k])
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    peak_src = "measured (MEASURED_PEAKS.json hbm_gbs)" if peaks else "fallback 6.8 TB/s"
+
+    def roof(fam, ms_total, iters, nv, workload, l2_resident):
+        if iters == 0 or ms_total <= 0:
+            return None
+        launch_s = ms_total / 1e3 / (2 * iters)
+        alg = BYTES_PER_UPDATE[fam] * nv / 2           # one launch updates one colour
+        ach = alg / launch_s / 1e9
+        return {"bound": "hbm", "kernel": KERNEL_NAME[fam], "achieved": round(ach, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4), "traffic": traffic_record(fam, workload),
+                "algorithmic_bytes_per_launch": alg, "launch_us": round(launch_s * 1e6, 3),
+                "launches_measured": 2 * iters, "peak_source": peak_src, "l2_resident": l2_resident}
+
+    roofline = roof(dom, fam_ms[dom], fam_it[dom], nvox, f"cloud{n}", True)
+    other = "ff" if dom == "fp32" else "fp32"
+    roof_other = roof(other, fam_ms[other], fam_it[other], nvox, f"cloud{n}", True)
+
+    extras = {}
+    if ranks.rank == 0 and not args.no_extras:
+        extras["roofline_hbm_resident"] = roofline_256(fld, torch, dev, sig_np, alb_np, roof)
+        extras["e2e"] = e2e_measure(fld, g, sig_np, alb_np, p, n, args)
+        extras["cpu_baseline"] = cpu_baseline(sig_np, alb_np, n, args.cpu_seconds)
+    g.close()
+
+    times_s = [ms / 1e3 for ms in step_ms]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ranks.world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": max_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (float-float correction sweeps)", "data": "synthetic",
+        "config": workload_config(args, ranks),
+        "time_to_residual_s": {"p50": statistics.median(times_s), "max": max(times_s)},
+        "iterations_per_solve": [r.iterations for r in results],
+        "iterations_fp32_per_solve": [r.iterations_fp32 for r in results],
+        "rel_residual": [r.rel_residual for r in results],
+        "status": [fld.fld_status_string(r.status) for r in results],
+        "roofline": roofline, "roofline_other_pass": roof_other,
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    line.update(extras)
+    if "e2e" not in line:
+        line["e2e"] = None
+    ranks.barrier()
+    if ranks.rank == 0:
+        print(json.dumps(line), flush=True)
+    ranks.close()
+
+
+def roofline_256(fld, torch, dev, sig_np, alb_np, roof):
+    """The same sweeps on a 256^3 volume (the 128^3 medium tiled 2x2x2), whose
+    ~0.5 GB working set cannot stay in L2: the pass then streams from HBM."""
+    import numpy as np
+    n = 2 * sig_np.shape[0]
+    sig = torch.from_numpy(np.tile(sig_np, (2, 2, 2))).to(dev)
+    alb = torch.from_numpy(np.tile(alb_np, (2, 2, 2))).to(dev)
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream(device=dev)
+    out = {}
+    g = fld.Grid(n, n, n, 1.0 / n, stream=stream.cuda_stream)
+    try:
+        g.set_medium(sig, alb)
+        g.bake_directional((0.0, 0.0, -1.0), 1.0)
+        for fam, prec in (("fp32", "fp32"), ("ff", "mixed")):
+            p = fld.params(limiter="lp", precision=prec, tol=0.0, local_iters=2, check_every=64, max_iters=64,
+                           fp32_switch=1e30)
+            g.solve(p, check=False)            # warm-up (and graph capture)
+            p.warm_start = 1
+            r = g.solve(p, check=False)
+            ms = r.ms_sweep_fp32 if fam == "fp32" else r.ms_sweep_corr
+            it = r.iterations_fp32 if fam == "fp32" else r.iterations_corr
+            out[fam] = roof(fam, ms, it, n ** 3, f"cloud{n}", False)
+    finally:
+        g.close()
+    return out
+
+
+def e2e_measure(fld, g, sig_np, alb_np, p, n, args):
+    """The same steps through the public API with host buffers: the medium is
+    copied host->device inside the step and phi is read back to the host."""
+    import numpy as np
+    import torch
+    phi = np.empty((n + 2, n + 2, n + 2), np.float64)
+    times, updates, checks = [], 0, 0
+    for _ in range(max(1, args.e2e_steps)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.set_medium(sig_np, alb_np)
+        g.bake_directional((0.0, 0.0, -1.0), 1.0)
+        r = g.solve(p)
+        fld.fld_get_state(g.handle, phi, None)
+        times.append(time.perf_counter() - t0)
+        updates += r.iterations * n ** 3
+        checks += r.checks
+    steps = max(1, args.e2e_steps)
+    return {"value": updates / sum(times), "unit": UNIT, "steps": steps,
+            "h2d_bytes_per_step": int(sig_np.nbytes + alb_np.nbytes),
+            "d2h_bytes_per_step": int(phi.nbytes + 16 * checks / steps)}
+
+
+def cpu_baseline(sig_np, alb_np, n, seconds):
+    """The FP64 oracle as it stands, on the host cores: iterations of
+    Algorithm 1 on the same 128^3 cloud, for about `seconds`."""
+    import oracle
+    q = oracle.bake_directional(sig_np, alb_np, 1.0 / n, (0, 0, -1), 1.0)
+    prob = oracle.make_problem(sig_np, alb_np, q, 1.0 / n, limiter="lp", local_iters=2,
+                               omega=oracle.omega_default(n, n, n))
+    oracle.init_state(prob)
+    it, t0 = 0, time.perf_counter()
+    chunk = 2
+    while True:
+        oracle.rb_iteration(prob, chunk)
+        it += chunk
+        el = time.perf_counter() - t0
+        if el >= seconds or it >= 100000:
+            break
+    return {"value": it * n ** 3 / el, "unit": UNIT, "cores": prob.nthreads, "kind": "oracle",
+            "sample": f"{it} iterations of Algorithm 1 (FP64, local_iters=2) on the {n}^3 cloud from the paper's "
+                      f"initial state, {el:.1f} s; a full solve to 1e-6 needs ~2e5 iterations"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    n = args.n
+    sig_np, alb_np = workload_inputs(n, seed=0)
+    q = oracle.bake_directional(sig_np, alb_np, 1.0 / n, (0, 0, -1), 1.0)
+    prob = oracle.make_problem(sig_np, alb_np, q, 1.0 / n, limiter="lp", local_iters=2,
+                               omega=oracle.omega_default(n, n, n))
+    oracle.init_state(prob)
+    per_step = 8     # iterations per step: a bounded sample of the solve
+    for _ in range(args.warmup):
+        oracle.rb_iteration(prob, per_step)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.rb_iteration(prob, per_step)
+    el = time.perf_counter() - t0
+    value = args.steps * per_step * n ** 3 / el
+    cfg = workload_config(args, _OneRank())
+    cfg["parallelism"] = "host cores"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el * 1e3 / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": cfg,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": prob.nthreads, "kind": "oracle",
+                         "sample": f"each step = {per_step} iterations of Algorithm 1 (FP64) on the {n}^3 cloud"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -125,6 +125,9 @@ typedef struct {
     double jbar;           /* RMS emission over the unknowns                        */
     double omega;          /* SOR factor used                                       */
     double ms;             /* device time of the solve, CUDA events                 */
+    double ms_sweep_fp32;  /* device time inside blocks of single-precision sweeps  */
+    double ms_sweep_corr;  /* device time inside blocks of float-float / FP64 sweeps */
+    long long kernels;     /* kernel launches the solve issued (incl. graph nodes)  */
 } fld_solve_result;
 
 /* Fill *p with the defaults: LP limiter, Larsen n = 2, omega auto,

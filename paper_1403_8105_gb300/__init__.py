@@ -55,6 +55,7 @@ class SolveResult(ctypes.Structure):
         ("status", ctypes.c_int), ("iterations", ctypes.c_int), ("iterations_fp32", ctypes.c_int),
         ("iterations_corr", ctypes.c_int), ("checks", ctypes.c_int), ("rel_residual", ctypes.c_double),
         ("jbar", ctypes.c_double), ("omega", ctypes.c_double), ("ms", ctypes.c_double),
+        ("ms_sweep_fp32", ctypes.c_double), ("ms_sweep_corr", ctypes.c_double), ("kernels", ctypes.c_longlong),
     ]
 
     def as_dict(self):

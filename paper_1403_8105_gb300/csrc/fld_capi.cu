@@ -73,7 +73,8 @@ struct fld_grid_s {
     bool valid_float = false, valid_d = false;   // which family holds the state
     bool lo_live = false;                        // phlo may be non-zero
     GraphEntry graphs[3];
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, evb0 = nullptr, evb1 = nullptr;
+    long long kernels = 0;                       // kernel launches issued so far
 };
 
 namespace {
@@ -125,6 +126,7 @@ fld_status read_result(fld_grid_s *g, double out[2]) {
 fld_status update_jbar(fld_grid_s *g) {
     if (g->jbar_version == g->version) return FLD_OK;
     FLD_CK(launch_sumsq_source(g->L, g->f, g->stream));
+    g->kernels += 2;
     double r[2];
     fld_status st = read_result(g, r);
     if (st != FLD_OK) return st;
@@ -144,12 +146,14 @@ fld_status prepare(fld_grid_s *g, const fld_solve_params *p, Family fam) {
         if (st != FLD_OK) return st;
         if (g->prepared_d != g->version || g->prepared_seps_d != seps) {
             FLD_CK(launch_prep_d(g->L, g->f, seps, h2, g->stream));
+            g->kernels += 1;
             g->prepared_d = g->version;
             g->prepared_seps_d = seps;
         }
     } else {
         if (g->prepared_f != g->version || g->prepared_seps_f != seps) {
             FLD_CK(launch_prep_f(g->L, g->f, (float)seps, (float)h2, g->stream));
+            g->kernels += 1;
             g->prepared_f = g->version;
             g->prepared_seps_f = seps;
         }
@@ -179,10 +183,12 @@ fld_status init_state(fld_grid_s *g, const fld_solve_params *p, Family fam) {
     const double D_b = p->D_b >= 0.0 ? p->D_b : D_def;
     if (fam == FAM_F64) {
         FLD_CK(launch_init_d(g->L, g->f.phi64, g->f.D64, phi0, D0, phi_b, D_b, g->stream));
+        g->kernels += 1;
         g->valid_d = true;
         g->valid_float = false;
     } else {
         FLD_CK(launch_init_f(g->L, g->f.phi, g->f.phlo, g->f.D, phi0, D0, phi_b, D_b, g->stream));
+        g->kernels += 1;
         g->valid_float = true;
         g->valid_d = false;
         g->lo_live = false;
@@ -199,6 +205,7 @@ fld_status sync_family(fld_grid_s *g, Family fam) {
             if (!g->valid_float) return fail(FLD_ERR_STATE, "no state to continue from");
             FLD_CK(launch_f_to_d(g->L, g->f.phi, g->lo_live ? g->f.phlo : nullptr, g->f.phi64, g->stream));
             FLD_CK(launch_f_to_d(g->L, g->f.D, nullptr, g->f.D64, g->stream));
+            g->kernels += 2;
             g->valid_d = true;
         }
         g->valid_float = false;
@@ -207,6 +214,7 @@ fld_status sync_family(fld_grid_s *g, Family fam) {
             if (!g->valid_d) return fail(FLD_ERR_STATE, "no state to continue from");
             FLD_CK(launch_d_to_f(g->L, g->f.phi64, g->f.phi, g->f.phlo, g->stream));
             FLD_CK(launch_d_to_f(g->L, g->f.D64, g->f.D, nullptr, g->stream));
+            g->kernels += 2;
             g->valid_float = true;
             g->lo_live = true;
         }
@@ -255,11 +263,13 @@ fld_status run_block(fld_grid_s *g, Family fam, const PassParams &pp, int iters)
         e.p = pp;
     }
     FLD_CK(cudaGraphLaunch(e.exec, g->stream));
+    g->kernels += 2LL * iters;
     return FLD_OK;
 }
 
 fld_status residual_now(fld_grid_s *g, Family fam, const PassParams &pp, int margin, double *rel) {
     FLD_CK(launch_residual(fam, g->L, g->f, pp, margin, g->stream));
+    g->kernels += 3;
     double r[2];
     fld_status st = read_result(g, r);
     if (st != FLD_OK) return st;
@@ -400,7 +410,8 @@ fld_status fld_create_grid(int nx, int ny, int nz, double h, void *stream, fld_g
     if (st == FLD_OK && cudaMalloc((void **)&g->f.partials, sizeof(double) * 2 * (size_t)g->f.partial_cap) != cudaSuccess)
         st = FLD_ERR_OOM;
     if (st == FLD_OK && cudaMalloc((void **)&g->f.result, sizeof(double) * 2) != cudaSuccess) st = FLD_ERR_OOM;
-    if (st == FLD_OK && (cudaEventCreate(&g->ev0) != cudaSuccess || cudaEventCreate(&g->ev1) != cudaSuccess))
+    if (st == FLD_OK && (cudaEventCreate(&g->ev0) != cudaSuccess || cudaEventCreate(&g->ev1) != cudaSuccess ||
+                         cudaEventCreate(&g->evb0) != cudaSuccess || cudaEventCreate(&g->evb1) != cudaSuccess))
         st = FLD_ERR_CUDA;
     if (st == FLD_OK) {
         for (float **p : pf)
@@ -430,6 +441,8 @@ void fld_destroy(fld_grid g) {
         if (p) cudaFree(p);
     if (g->ev0) cudaEventDestroy(g->ev0);
     if (g->ev1) cudaEventDestroy(g->ev1);
+    if (g->evb0) cudaEventDestroy(g->evb0);
+    if (g->evb1) cudaEventDestroy(g->evb1);
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
     delete g;
 }
@@ -625,6 +638,7 @@ fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r)
     if (p->max_iters < 0 || p->check_every < 1) return fail(FLD_ERR_INVALID_ARG, "bad max_iters / check_every");
     fld_solve_result res;
     memset(&res, 0, sizeof(res));
+    const long long kernels0 = g->kernels;
     Family fam = p->precision == FLD_PREC_FP64 ? FAM_F64 : FAM_F32;
     if ((st = prepare(g, p, fam)) != FLD_OK) return st;
     if (p->precision == FLD_PREC_MIXED && (st = prepare(g, p, FAM_FF)) != FLD_OK) return st;
@@ -650,12 +664,18 @@ fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r)
     while (outcome == FLD_ERR_NOT_CONVERGED && it < p->max_iters) {
         int k = p->check_every;
         if (k > p->max_iters - it) k = p->max_iters - it;
+        FLD_CK(cudaEventRecord(g->evb0, g->stream));
         if ((st = run_block(g, fam, pp, k)) != FLD_OK) return st;
+        FLD_CK(cudaEventRecord(g->evb1, g->stream));
         it += k;
-        if (fam == FAM_FF) res.iterations_corr += k;
-        else if (fam == FAM_F32) res.iterations_fp32 += k;
+        if (fam == FAM_F32) res.iterations_fp32 += k;
+        else res.iterations_corr += k;
         if ((st = residual_now(g, fam, pp, p->residual_margin, &rel)) != FLD_OK) return st;
         ++res.checks;
+        float bms = 0.0f;   // the residual read above synchronised the stream
+        FLD_CK(cudaEventElapsedTime(&bms, g->evb0, g->evb1));
+        if (fam == FAM_F32) res.ms_sweep_fp32 += bms;
+        else res.ms_sweep_corr += bms;
         if (!isfinite(rel)) {
             outcome = FLD_ERR_DIVERGED;
             break;
@@ -693,6 +713,7 @@ fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r)
     res.iterations = it;
     res.rel_residual = rel;
     res.ms = ms;
+    res.kernels = g->kernels - kernels0;
     if (r) *r = res;
     if (outcome == FLD_ERR_DIVERGED) g_last_error = "residual became NaN or infinite";
     if (outcome == FLD_ERR_NOT_CONVERGED)

@@ -61,7 +61,7 @@ def test_struct_layout_matches_header():
             decl = decl.strip()
             if not decl:
                 continue
-            names = decl.split(None, 1)[1]
+            names = re.match(r"^(?:\w+\s+)+?(\w+(?:\s*,\s*\w+)*)$", decl).group(1)
             fields += [x.strip() for x in names.split(",")]
         assert [f for f, _ in py._fields_] == fields, cname
 
