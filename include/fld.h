@@ -194,6 +194,40 @@ fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r)
  * the arithmetic of p->precision with an accurate sum.  Synchronises. */
 fld_status fld_residual(fld_grid g, const fld_solve_params *p, double *rel);
 
+/* Allocation-free residual.  The paper has no counterpart: this entry point
+ * exists for callers that cannot allocate device memory when they need the
+ * residual -- e.g. a renderer that runs the solver inside its frame loop,
+ * where cudaMalloc/cudaFree are banned after start-up because they
+ * synchronise the device, or a host application that owns all device memory
+ * through its own pool and only lends the library its buffers.
+ *
+ * Computes the same quantity as fld_residual with FLD_PREC_FP64 (Rbar/jbar of
+ * Eq. 37, D recomputed from phi, RMS over the unknowns beyond
+ * p->residual_margin; p->limiter, larsen_n, sigma_eps, eps also apply) from
+ * caller-owned DEVICE buffers: sigma_t, albedo, j unpadded floats; phi and D
+ * padded doubles (only the ghost layer of D is read).  *rel is a host
+ * double.  All work is enqueued on `stream` (a cudaStream_t, NULL = legacy
+ * default stream), which the call then synchronises.
+ *
+ * Scratch: a fixed array of 2*FLD_NOALLOC_MAX_BLOCKS + 8 doubles (1 MiB + 64
+ * bytes) in the library's device memory image, present on every GPU that
+ * loads the library until the process exits.  The call launches one block
+ * per 32x8 tile of an x-y plane, so grids with
+ * ceil(nx/32)*ceil(ny/8)*nz > FLD_NOALLOC_MAX_BLOCKS (and nz > 65535) are
+ * rejected with FLD_ERR_INVALID_ARG; 256^3 fits exactly.  No cudaMalloc,
+ * cudaFree or other allocating routine is called.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU (other streams, other threads) race and must be
+ * serialised by the caller.  Each call writes every slot it reads, so no
+ * state carries over between calls. */
+#define FLD_NOALLOC_MAX_BLOCKS 65536
+fld_status fld_residual_noalloc(int nx, int ny, int nz, double h, const fld_solve_params *p,
+                                const float *sigma_t, const float *albedo, const float *j,
+                                const double *phi, const double *D, double *rel, void *stream);
+
 /* Free the grid and everything it owns (NULL is ignored). */
 void fld_destroy(fld_grid g);
 

@@ -26,8 +26,8 @@ __all__ = [
     "LIMITERS", "PRECISIONS", "FldError", "SolveParams", "SolveResult",
     "load", "library_path", "fld_default_params", "fld_create_grid", "fld_set_medium", "fld_set_source",
     "fld_get_source", "fld_bake_directional", "fld_bake_point", "fld_set_state", "fld_get_state",
-    "fld_iterate", "fld_solve", "fld_residual", "fld_destroy", "fld_status_string", "fld_last_error",
-    "Grid", "params",
+    "fld_iterate", "fld_solve", "fld_residual", "fld_residual_noalloc", "fld_destroy", "fld_status_string",
+    "fld_last_error", "Grid", "params",
 ]
 
 FLD_OK, FLD_ERR_INVALID_ARG, FLD_ERR_OOM, FLD_ERR_CUDA, FLD_ERR_STATE = 0, 1, 2, 3, 4
@@ -108,6 +108,8 @@ def load(build_if_missing: bool = True):
             "fld_iterate": (c_int, [_vp, P, c_int]),
             "fld_solve": (c_int, [_vp, P, R]),
             "fld_residual": (c_int, [_vp, P, ctypes.POINTER(c_double)]),
+            "fld_residual_noalloc": (c_int, [c_int, c_int, c_int, c_double, P, _vp, _vp, _vp, _vp, _vp,
+                                             ctypes.POINTER(c_double), _vp]),
             "fld_destroy": (None, [_vp]),
             "fld_status_string": (ctypes.c_char_p, [c_int]),
             "fld_last_error": (ctypes.c_char_p, []),
@@ -235,6 +237,24 @@ def fld_solve(g, p: SolveParams, check: bool = True) -> SolveResult:
 def fld_residual(g, p: SolveParams) -> float:
     rel = ctypes.c_double(0.0)
     _check(load().fld_residual(g, ctypes.byref(p), ctypes.byref(rel)), "fld_residual")
+    return rel.value
+
+
+def fld_residual_noalloc(nx: int, ny: int, nz: int, h: float, p: SolveParams, sigma_t, albedo, j, phi, D,
+                         stream=None) -> float:
+    """Allocation-free FP64 residual from caller-owned CUDA tensors (float32
+    sigma_t, albedo, j of shape (nz, ny, nx); float64 phi, D padded)."""
+    args = []
+    for a, dt in ((sigma_t, np.float32), (albedo, np.float32), (j, np.float32), (phi, np.float64),
+                  (D, np.float64)):
+        ptr, where, keep = _ptr(a, dt)
+        if where != FLD_MEM_DEVICE:
+            raise TypeError("fld_residual_noalloc takes device buffers (CUDA tensors)")
+        args.append(ptr)
+    rel = ctypes.c_double(0.0)
+    s = None if stream is None else _vp(int(stream))
+    _check(load().fld_residual_noalloc(int(nx), int(ny), int(nz), float(h), ctypes.byref(p), *args,
+                                       ctypes.byref(rel), s), "fld_residual_noalloc")
     return rel.value
 
 

@@ -56,6 +56,8 @@ bool same_params(const PassParams &a, const PassParams &b) {
 
 }  // namespace
 
+void fld::set_error_text(const char *msg) { g_last_error = msg ? msg : ""; }
+
 struct fld_grid_s {
     int device = 0;
     cudaStream_t stream = nullptr;

@@ -82,4 +82,7 @@ cudaError_t launch_bake_march(const Layout &L, const Fields &f, float h, const d
 cudaError_t launch_validate(long long n, const Fields &f, const float *sigma_t, const float *albedo,
                             const float *j, cudaStream_t s);
 
+// Sets the thread-local text that fld_last_error() returns.
+void set_error_text(const char *msg);
+
 }  // namespace fld
