@@ -42,8 +42,8 @@ UNIT = "voxel-updates/s"
 # reads phi, D, sigma', sigma_a' dl^2, j dl^2 and writes phi, D (4 bytes each);
 # the float-float correction sweep also reads and writes the low word of phi.
 BYTES_PER_UPDATE = {"fp32": 28, "ff": 36}
-KERNEL_NAME = {"fp32": "k_pass_f<false> (single-precision red/black pass)",
-               "ff": "k_pass_f<true> (float-float correction pass)"}
+KERNEL_NAME = {"fp32": "k_pass_f32 (single-precision red/black pass)",
+               "ff": "k_pass_ff (float-float correction pass)"}
 
 
 def parse_args():
@@ -57,6 +57,8 @@ def parse_args():
     ap.add_argument("--omega", type=float, default=0.0, help="SOR factor (0 = library default)")
     ap.add_argument("--check-every", type=int, default=256)
     ap.add_argument("--max-iters", type=int, default=600000)
+    ap.add_argument("--fp32-switch", type=float, default=0.0,
+                    help="residual at which the float-float sweeps take over (0 = library default)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample length")
     ap.add_argument("--no-extras", action="store_true", help="skip cpu baseline / 256^3 roofline / e2e")
@@ -242,7 +244,7 @@ def run_gpu(args):
     stream = torch.cuda.Stream(device=dev)
     g = fld.Grid(n, n, n, h, stream=stream.cuda_stream)
     p = fld.params(limiter="lp", precision="mixed", tol=args.tol, omega=args.omega, local_iters=2,
-                   check_every=args.check_every, max_iters=args.max_iters)
+                   check_every=args.check_every, max_iters=args.max_iters, fp32_switch=args.fp32_switch)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
 
     def step():

@@ -387,7 +387,10 @@ fld_status fld_create_grid(int nx, int ny, int nz, double h, void *stream, fld_g
         return cuda_fail(e, "cudaGetDevice");
     }
     g->nx = nx; g->ny = ny; g->nz = nz; g->h = h;
-    g->L = make_layout(nx, ny, nz);
+    if (!make_layout(nx, ny, nz, &g->L)) {
+        delete g;
+        return fail(FLD_ERR_INVALID_ARG, "grid too large: a padded field must stay below 2e9 elements");
+    }
     if (stream) {
         g->stream = (cudaStream_t)stream;
     } else {

@@ -9,35 +9,56 @@
 namespace fld {
 
 // ---------------------------------------------------------------------------
-// Layout of padded device fields.
+// Layout of padded device fields: red-black (colour-split) storage.
 //
-// Unknown (i, j, k) lives at element  base + ((k+1)*py + (j+1))*px + (i+1)
-// where base = kOx.  The ghost layer sits at i = -1 / nx etc.  kOx = 3 puts
-// the first unknown of every row on a 16-byte boundary when px is a multiple
-// of 4, so rows can be moved with 128-bit accesses.
+// Padded coordinates I = i+1, J = j+1, K = k+1 run over [0, n+1] per axis
+// (0 and n+1 are the Dirichlet ghost layer).  A cell's colour is
+// c = (I + J + K + 1) & 1, so c = 0 ("red") holds the unknowns with i+j+k
+// even, which Algorithm 1 updates first.  Each colour has its own array of
+// half rows: cell (I, J, K) of colour c lives at
+//     c * cs + (K * py + J) * hpx + kXoff + ((I + 1) >> 1).
+// In every half row the first unknown (I = 1 or 2) sits at position
+// kXoff + 1 = 32, so with hpx a multiple of 32 a warp of 32 consecutive
+// unknowns reads one aligned 128-byte line per field.  A colour pass streams
+// its own colour for the point's fields and the other colour for the six
+// neighbours: the x-neighbours are the adjacent elements (I >> 1) and
+// (I >> 1) + 1 of the other colour's row, the y/z-neighbours the same
+// position one row/plane away.  All offsets fit in 32 bits (checked at grid
+// creation).
 // ---------------------------------------------------------------------------
-constexpr int kOx = 3;
+constexpr int kXoff = 31;
 
 struct Layout {
     int nx, ny, nz;     // unknowns per axis
-    int px, py;         // row pitch (elements) and rows per plane (ny + 2)
-    long long plane;    // px * py
-    long long total;    // elements per padded field (incl. alignment slack)
+    int hpx;            // half-row pitch (elements), a multiple of 32
+    int py;             // rows per plane (ny + 2)
+    int cs;             // elements per colour array
+    int total;          // elements per padded field (both colours)
 
-    __host__ __device__ __forceinline__ long long at(int i, int j, int k) const {
+    __host__ __device__ __forceinline__ int at(int i, int j, int k) const {
         // i, j, k in [-1, n]: -1 and n are the ghost layer
-        return kOx + ((long long)(k + 1) * py + (j + 1)) * px + (i + 1);
+        const int I = i + 1, J = j + 1, K = k + 1;
+        const int c = (I + J + K + 1) & 1;
+        return c * cs + (K * py + J) * hpx + kXoff + ((I + 1) >> 1);
     }
+    // offset of the half-row (J, K) inside a colour array (incl. kXoff)
+    __host__ __device__ __forceinline__ int row(int J, int K) const { return (K * py + J) * hpx + kXoff; }
 };
 
-inline Layout make_layout(int nx, int ny, int nz) {
+// Largest padded grid whose fields the 32-bit offsets address.
+constexpr long long kMaxLayoutElems = 2000000000LL;
+
+inline bool make_layout(int nx, int ny, int nz, Layout *out) {
     Layout L;
     L.nx = nx; L.ny = ny; L.nz = nz;
-    L.px = ((kOx + nx + 2) + 3) & ~3;
+    L.hpx = (kXoff + (nx + 2) / 2 + 1 + 31) & ~31;
     L.py = ny + 2;
-    L.plane = (long long)L.px * L.py;
-    L.total = L.plane * (nz + 2) + 4;
-    return L;
+    const long long cs = (long long)L.hpx * L.py * (nz + 2);
+    if (2 * cs + 8 > kMaxLayoutElems) return false;
+    L.cs = (int)cs;
+    L.total = (int)(2 * cs);
+    *out = L;
+    return true;
 }
 
 enum Limiter : int { LIM_CDA = 0, LIM_SUM = 1, LIM_MAX = 2, LIM_KERSHAW = 3, LIM_LARSEN = 4, LIM_LP = 5 };
@@ -93,8 +114,11 @@ __device__ __forceinline__ float limiter_f(int kind, float larsen_n, float R) {
     }
     default: {  // LIM_LP
         if (R < 1.0f) return lp_series_f(R);
-        const float e = expf(-2.0f * R);
-        return ((1.0f - 1.0f / R) + 2.0f * e / (1.0f - e)) / R;
+        // F = r ((1 - r) + 2/(e^{2R} - 1)), r = 1/R; the last term is below
+        // 3.4e-8 of the first once R > 9 and is dropped there
+        const float r = 1.0f / R;
+        const float tail = R < 9.0f ? 2.0f / (expf(2.0f * R) - 1.0f) : 0.0f;
+        return r * ((1.0f - r) + tail);
     }
     }
 }
@@ -174,13 +198,23 @@ __device__ __forceinline__ double ff_to_d(ff a) { return (double)a.hi + (double)
 // ---------------------------------------------------------------------------
 // Knudsen number (Eq. 35) and D (Eq. 33) from the central gradient (Eq. 34).
 // g_x etc. are the already formed central differences phi(i+1) - phi(i-1).
+// The single-precision path is split so a point update can reuse |grad phi|
+// across its local rounds; grad_floor_f followed by D_of_f is the one D
+// function shared, bit for bit, by the correction sweep and the residual.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float knudsen_D_f(float gx, float gy, float gz, float inv2h, float sp,
-                                             float phi_p, float floor_, int lim, float larsen_n) {
+__device__ __forceinline__ float grad_floor_f(float gx, float gy, float gz, float inv2h, float floor_) {
     gx *= inv2h; gy *= inv2h; gz *= inv2h;
-    const float g = sqrtf(fmaf(gx, gx, fmaf(gy, gy, gz * gz)));
-    const float R = fmaxf(g, floor_) / fmaxf(sp * phi_p, floor_);
+    return fmaxf(sqrtf(fmaf(gx, gx, fmaf(gy, gy, gz * gz))), floor_);
+}
+
+__device__ __forceinline__ float D_of_f(float gmax, float sp, float phi_p, float floor_, int lim, float larsen_n) {
+    const float R = gmax / fmaxf(sp * phi_p, floor_);
     return limiter_f(lim, larsen_n, R) / sp;
+}
+
+__device__ __forceinline__ float knudsen_D_f(float gx, float gy, float gz, float inv2h, float sp, float phi_p,
+                                             float floor_, int lim, float larsen_n) {
+    return D_of_f(grad_floor_f(gx, gy, gz, inv2h, floor_), sp, phi_p, floor_, lim, larsen_n);
 }
 
 __device__ __forceinline__ double knudsen_D_d(double gx, double gy, double gz, double inv2h, double sp,

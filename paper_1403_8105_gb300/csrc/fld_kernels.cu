@@ -76,7 +76,7 @@ __global__ void k_prep_f(Layout L, const float *__restrict__ st, const float *__
     const int k = blockIdx.z;
     if (i >= L.nx || j >= L.ny) return;
     const long long v = ((long long)k * L.ny + j) * L.nx + i;
-    const long long q = L.at(i, j, k);
+    const int q = L.at(i, j, k);
     const float s = fmaxf(st[v], seps);                           // Algorithm 1: sigma floor
     sp[q] = s;
     ah2[q] = __fmul_rn(__fmul_rn(__fsub_rn(1.0f, alb[v]), s), h2);  // (1 - albedo) sigma' dl^2
@@ -91,32 +91,33 @@ __global__ void k_prep_d(Layout L, const float *__restrict__ st, const float *__
     const int k = blockIdx.z;
     if (i >= L.nx || j >= L.ny) return;
     const long long v = ((long long)k * L.ny + j) * L.nx + i;
-    const long long q = L.at(i, j, k);
+    const int q = L.at(i, j, k);
     const double s = fmax((double)st[v], seps);
     sp[q] = s;
     ah2[q] = __dmul_rn(__dmul_rn(1.0 - (double)alb[v], s), h2);
     jh2[q] = __dmul_rn((double)js[v], h2);
 }
 
-// Every padded element: unknowns get (phi0, D0), the ghost layer (phi_b, D_b),
-// alignment slack 0.
+// Every element of both colour arrays: unknowns get (phi0, D0), the ghost
+// layer (phi_b, D_b), the alignment slack of each half row 0.
 template <typename T>
 __global__ void k_init(Layout L, T *__restrict__ phi, float *__restrict__ phlo, T *__restrict__ D, T phi0, T D0,
                        T phi_b, T D_b) {
-    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= L.total) return;
+    const int c = e >= L.cs ? 1 : 0;
+    const int r = e - c * L.cs;
+    const int K = r / (L.hpx * L.py);
+    const int w = r - K * (L.hpx * L.py);
+    const int J = w / L.hpx;
+    const int pos = w - J * L.hpx - kXoff;            // = (I + 1) >> 1 for a cell
+    const int par = (J + K + 1 + c) & 1;               // I & 1 of this row's cells
+    const int I = par ? 2 * pos - 1 : 2 * pos;
     T p = T(0), d = T(0);
-    const long long r = e - kOx;
-    if (r >= 0 && r < L.plane * (L.nz + 2)) {
-        const int K = (int)(r / L.plane);
-        const long long w = r - (long long)K * L.plane;
-        const int J = (int)(w / L.px);
-        const int I = (int)(w - (long long)J * L.px);
-        if (I <= L.nx + 1) {
-            const bool ghost = I == 0 || J == 0 || K == 0 || I == L.nx + 1 || J == L.ny + 1 || K == L.nz + 1;
-            p = ghost ? phi_b : phi0;
-            d = ghost ? D_b : D0;
-        }
+    if (pos >= 0 && I >= 0 && I <= L.nx + 1) {
+        const bool ghost = I == 0 || J == 0 || K == 0 || I == L.nx + 1 || J == L.ny + 1 || K == L.nz + 1;
+        p = ghost ? phi_b : phi0;
+        d = ghost ? D_b : D0;
     }
     phi[e] = p;
     D[e] = d;
@@ -131,7 +132,7 @@ __global__ void k_unpack_to_f(Layout L, const double *__restrict__ src, float *_
     const int K = blockIdx.z;
     if (I > L.nx + 1) return;
     const double x = src[((long long)K * (L.ny + 2) + J) * (L.nx + 2) + I];
-    const long long q = L.at(I - 1, J - 1, K - 1);
+    const int q = L.at(I - 1, J - 1, K - 1);
     const float h = (float)x;
     hi[q] = h;
     if (lo) lo[q] = (float)(x - (double)h);
@@ -151,7 +152,7 @@ __global__ void k_pack_from_f(Layout L, const float *__restrict__ hi, const floa
     const int J = blockIdx.y;
     const int K = blockIdx.z;
     if (I > L.nx + 1) return;
-    const long long q = L.at(I - 1, J - 1, K - 1);
+    const int q = L.at(I - 1, J - 1, K - 1);
     dst[((long long)K * (L.ny + 2) + J) * (L.nx + 2) + I] = (double)hi[q] + (lo ? (double)lo[q] : 0.0);
 }
 
@@ -182,9 +183,10 @@ __global__ void k_d_to_f(long long n, const double *__restrict__ src, float *__r
 // ---------------------------------------------------------------------------
 // Red-black pass.
 //
-// Thread (t, j, k) updates voxel i = 2t + ((j + k + colour) & 1) of row (j, k)
-// if i < nx; all its neighbours have the other colour, so the pass is free of
-// races and its result does not depend on thread order.
+// Thread (t, J, K) of colour c updates the t-th unknown of colour c in row
+// (J, K) (padded I = 2t + 2 - ((J + K + 1 + c) & 1)) if the row has one.  All six neighbours have the other colour, so a pass is
+// free of races and its result does not depend on thread order.  Within a
+// warp every access is a run of consecutive elements of one colour array.
 //
 // Update in residual form: with d_s = phi_s - phi_p and D_ps = (D_p + D_s)/2,
 //   S(D_p)   = j dl^2 - sigma_a' dl^2 phi_p + sum_s D_ps d_s
@@ -196,10 +198,63 @@ __global__ void k_d_to_f(long long n, const double *__restrict__ src, float *__r
 // (Eq. 36) is phi_p + omega * delta.  One round is Algorithm 1 as printed.
 // ---------------------------------------------------------------------------
 
+struct Nbrs {
+    int own, nb[6];
+};
+
+// Offsets of the t-th unknown of colour c in row (J, K) and of its
+// neighbours (x-, x+, y-, y+, z-, z+); false if the row has fewer unknowns
+// of that colour.  The row's unknowns of colour c are I = 2t + 2 - par,
+// par = (J + K + 1 + c) & 1, i.e. every other I starting at 1 or 2.
+__device__ __forceinline__ bool pass_cell(const Layout &L, int c, int t, int J, int K, Nbrs &o) {
+    const int par = (J + K + 1 + c) & 1;
+    const int I = 2 * t + 2 - par;
+    if (I > L.nx) return false;
+    const int row = L.row(J, K);
+    const int ob = (1 - c) * L.cs;
+    const int h = I >> 1;
+    const int pos = (I + 1) >> 1;
+    o.own = c * L.cs + row + pos;
+    o.nb[0] = ob + row + h;
+    o.nb[1] = ob + row + h + 1;
+    o.nb[2] = ob + row - L.hpx + pos;
+    o.nb[3] = ob + row + L.hpx + pos;
+    o.nb[4] = ob + row - L.hpx * L.py + pos;
+    o.nb[5] = ob + row + L.hpx * L.py + pos;
+    return true;
+}
+
+// Limiter (Table 2) with approximate reciprocals, for the bulk
+// single-precision sweeps, whose accuracy is bounded by phi stored in float;
+// the correction sweeps and the residual use the correctly rounded forms.
+__device__ __forceinline__ float limiter_fast(int kind, float larsen_n, float R) {
+    switch (kind) {
+    case LIM_CDA: return 1.0f / 3.0f;
+    case LIM_SUM: return __fdividef(1.0f, 3.0f + R);
+    case LIM_MAX: return __fdividef(1.0f, fmaxf(3.0f, R));
+    case LIM_KERSHAW: return __fdividef(2.0f, 3.0f + hypotf(3.0f, 2.0f * R));
+    case LIM_LARSEN: {
+        const float m = fmaxf(3.0f, R), s = fminf(3.0f, R);
+        return __fdividef(1.0f, m * __powf(1.0f + __powf(__fdividef(s, m), larsen_n), __fdividef(1.0f, larsen_n)));
+    }
+    default: {
+        if (R < 1.0f) return lp_series_f(R);
+        const float r = __fdividef(1.0f, R);
+        // 2e/(1-e), e = exp(-2R), is below 3.4e-8 of (1 - 1/R) once R > 9
+        const float tail = R < 9.0f ? __fdividef(2.0f, __expf(2.0f * R) - 1.0f) : 0.0f;
+        return r * ((1.0f - r) + tail);
+    }
+    }
+}
+
 // Terms of the residual-form update that do not depend on D_p, shared by the
 // sweep and the residual kernel so both evaluate the same discrete equation
-// bit for bit:  A = sum_s d_s,  B = sum_s D_s d_s  (float-float),
-// C = sum_s D_s,  base = jh2 - ah2 phi_p + B/2, and the central differences.
+// bit for bit:  A = sum_s d_s,  B = sum_s D_s d_s,  C = sum_s D_s,
+// base = jh2 - ah2 phi_p + B/2, and the central differences.  A and B are
+// compensated sums (Ogita-Rump-Oishi style): each difference d_s =
+// phi_s - phi_p is formed exactly as a pair (TwoSum of the high words plus
+// the low words), each product D_s d_s exactly by TwoProd, and the running
+// sums carry their rounding errors in a separate low word.
 struct FFTerms {
     ff A, base;
     float C, gx, gy, gz;
@@ -211,19 +266,25 @@ __device__ __forceinline__ FFTerms ff_terms(float p0, float p0lo, const float ps
     t.gx = __fadd_rn(__fsub_rn(ps[1], ps[0]), __fsub_rn(ls[1], ls[0]));
     t.gy = __fadd_rn(__fsub_rn(ps[3], ps[2]), __fsub_rn(ls[3], ls[2]));
     t.gz = __fadd_rn(__fsub_rn(ps[5], ps[4]), __fsub_rn(ls[5], ls[4]));
-    const ff P = {p0, p0lo};
-    ff A = {0.0f, 0.0f}, B = {0.0f, 0.0f};
-    float C = 0.0f;
+    float Ah = 0.0f, Al = 0.0f, Bh = 0.0f, Bl = 0.0f, C = 0.0f;
 #pragma unroll
     for (int s = 0; s < 6; ++s) {
-        const ff d = ff_sub(ff{ps[s], ls[s]}, P);
-        A = ff_add(A, d);
-        B = ff_add(B, ff_mul_f(d, Ds[s]));
+        const ff dh = two_sum(ps[s], -p0);                                  // exact high part
+        const float dl = __fadd_rn(__fsub_rn(ls[s], p0lo), dh.lo);          // low part
+        const ff a = two_sum(Ah, dh.hi);
+        Ah = a.hi;
+        Al = __fadd_rn(Al, __fadd_rn(dl, a.lo));
+        const ff pr = two_prod(Ds[s], dh.hi);
+        const float pe = fmaf(Ds[s], dl, pr.lo);
+        const ff b = two_sum(Bh, pr.hi);
+        Bh = b.hi;
+        Bl = __fadd_rn(Bl, __fadd_rn(pe, b.lo));
         C = __fadd_rn(C, Ds[s]);
     }
-    ff base = ff_add_f(ff_mul_f(P, -ah), jj);
+    const ff B = fast_two_sum(Bh, Bl);
+    ff base = ff_add_f(ff_mul_f(ff{p0, p0lo}, -ah), jj);
     t.base = ff_add(base, ff{0.5f * B.hi, 0.5f * B.lo});
-    t.A = A;
+    t.A = fast_two_sum(Ah, Al);
     t.C = C;
     return t;
 }
@@ -234,71 +295,97 @@ __device__ __forceinline__ float ff_den(const FFTerms &t, float ah, float Dp) {
     return __fadd_rn(__fadd_rn(ah, 3.0f * Dp), 0.5f * t.C);
 }
 
-// FF = true keeps phi as a float-float pair and sums S exactly enough that
-// the update is accurate to the pair's precision; FF = false is plain FP32.
-template <bool FF>
-__global__ void __launch_bounds__(256) k_pass_f(Layout L, const float *__restrict__ sp,
-                                                const float *__restrict__ ah2, const float *__restrict__ jh2,
-                                                float *__restrict__ phi, float *__restrict__ phlo,
-                                                float *__restrict__ D, int colour, int lim, float larsen_n,
-                                                float omega, float inv2h, float floor_, int local_iters) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
-    if (j >= L.ny) return;
-    const int i = 2 * t + ((j + k + colour) & 1);
-    if (i >= L.nx) return;
-    const long long q = L.at(i, j, k);
-    const long long sy = L.px, sz = L.plane;
-    const long long nb[6] = {q - 1, q + 1, q - sy, q + sy, q - sz, q + sz};
-
-    const float p0 = phi[q];
+// Plain single-precision pass (the bulk sweeps).  LIM < 0 and ROUNDS = 0
+// select the limiter and the number of local rounds at run time; the common
+// cases are compiled with both fixed.
+template <int LIM, int ROUNDS>
+__global__ void __launch_bounds__(256) k_pass_f32(Layout L, const float *__restrict__ sp,
+                                                  const float *__restrict__ ah2, const float *__restrict__ jh2,
+                                                  float *__restrict__ phi, float *__restrict__ D, int colour,
+                                                  int lim_rt, float larsen_n, float omega, float inv2h, float floor_,
+                                                  int rounds_rt) {
+    const int lim = LIM >= 0 ? LIM : lim_rt;
+    const int local_iters = ROUNDS > 0 ? ROUNDS : rounds_rt;
+    Nbrs o;
+    if (!pass_cell(L, colour, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y + 1,
+                   blockIdx.z + 1, o) ||
+        blockIdx.y * blockDim.y + threadIdx.y >= L.ny)
+        return;
+    const float p0 = phi[o.own];
     float ps[6], Ds[6];
 #pragma unroll
     for (int s = 0; s < 6; ++s) {
-        ps[s] = phi[nb[s]];
-        Ds[s] = D[nb[s]];
+        ps[s] = phi[o.nb[s]];
+        Ds[s] = D[o.nb[s]];
     }
-    const float s_ = sp[q], ah = ah2[q], jj = jh2[q];
-
-    float p0lo = 0.0f, ls[6] = {0, 0, 0, 0, 0, 0};
-    if (FF) {
-        p0lo = phlo[q];
+    const float s_ = sp[o.own], ah = ah2[o.own], jj = jh2[o.own];
+    const float gx = ps[1] - ps[0], gy = ps[3] - ps[2], gz = ps[5] - ps[4];
+    const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+    const float g = g2 > 0.0f ? g2 * rsqrtf(g2) * inv2h : 0.0f;     // |grad phi| (Eq. 34)
+    const float gmax = fmaxf(g, floor_);
+    const float inv_sp = __fdividef(1.0f, s_);
+    float A = 0.0f, B = 0.0f, C = 0.0f;
 #pragma unroll
-        for (int s = 0; s < 6; ++s) ls[s] = phlo[nb[s]];
+    for (int s = 0; s < 6; ++s) {
+        const float d = ps[s] - p0;
+        A += d;
+        B = fmaf(Ds[s], d, B);
+        C += Ds[s];
     }
+    const float base = fmaf(0.5f, B, fmaf(-ah, p0, jj));
+    const float den0 = fmaf(0.5f, C, ah);
     float delta = 0.0f, Dp = 0.0f;
-    if (FF) {
-        const FFTerms T = ff_terms(p0, p0lo, ps, ls, Ds, ah, jj);
-        for (int r = 0; r < local_iters; ++r) {
-            Dp = knudsen_D_f(T.gx, T.gy, T.gz, inv2h, s_, __fadd_rn(p0, delta), floor_, lim, larsen_n);
-            const ff S = ff_S(T, Dp);
-            delta = __fadd_rn(S.hi, S.lo) / ff_den(T, ah, Dp);
-        }
-        const ff nw = ff_add_f(ff{p0, p0lo}, __fmul_rn(omega, delta));
-        phi[q] = nw.hi;
-        phlo[q] = nw.lo;
-    } else {
-        // plain single precision (the bulk sweeps)
-        const float gx = __fsub_rn(ps[1], ps[0]), gy = __fsub_rn(ps[3], ps[2]), gz = __fsub_rn(ps[5], ps[4]);
-        float A = 0.0f, B = 0.0f, C = 0.0f;
 #pragma unroll
-        for (int s = 0; s < 6; ++s) {
-            const float d = __fsub_rn(ps[s], p0);
-            A = __fadd_rn(A, d);
-            B = fmaf(Ds[s], d, B);
-            C = __fadd_rn(C, Ds[s]);
-        }
-        const float base = fmaf(0.5f, B, fmaf(-ah, p0, jj));
-        for (int r = 0; r < local_iters; ++r) {
-            Dp = knudsen_D_f(gx, gy, gz, inv2h, s_, __fadd_rn(p0, delta), floor_, lim, larsen_n);
-            const float S = fmaf(0.5f * Dp, A, base);
-            const float den = __fadd_rn(__fadd_rn(ah, 3.0f * Dp), 0.5f * C);
-            delta = S / den;
-        }
-        phi[q] = fmaf(omega, delta, p0);
+    for (int r = 0; r < (ROUNDS > 0 ? ROUNDS : 64); ++r) {
+        if (ROUNDS == 0 && r >= local_iters) break;
+        const float R = __fdividef(gmax, fmaxf(s_ * (p0 + delta), floor_));     // Eq. 35
+        Dp = limiter_fast(lim, larsen_n, R) * inv_sp;                          // Eq. 33
+        delta = __fdividef(fmaf(0.5f * Dp, A, base), fmaf(3.0f, Dp, den0));   // Eq. 32
     }
-    D[q] = Dp;
+    phi[o.own] = fmaf(omega, delta, p0);                                       // Eq. 36
+    D[o.own] = Dp;
+}
+
+// Float-float correction pass: phi kept as a hi/lo pair, S summed so the
+// update is accurate to the pair's precision; correctly rounded D (the same
+// function the residual kernel evaluates).
+template <int LIM, int ROUNDS>
+__global__ void __launch_bounds__(256) k_pass_ff(Layout L, const float *__restrict__ sp,
+                                                 const float *__restrict__ ah2, const float *__restrict__ jh2,
+                                                 float *__restrict__ phi, float *__restrict__ phlo,
+                                                 float *__restrict__ D, int colour, int lim_rt, float larsen_n,
+                                                 float omega, float inv2h, float floor_, int rounds_rt) {
+    const int lim = LIM >= 0 ? LIM : lim_rt;
+    const int local_iters = ROUNDS > 0 ? ROUNDS : rounds_rt;
+    Nbrs o;
+    if (!pass_cell(L, colour, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y + 1,
+                   blockIdx.z + 1, o) ||
+        blockIdx.y * blockDim.y + threadIdx.y >= L.ny)
+        return;
+    const float p0 = phi[o.own], p0lo = phlo[o.own];
+    float ps[6], ls[6], Ds[6];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        ps[s] = phi[o.nb[s]];
+        ls[s] = phlo[o.nb[s]];
+        Ds[s] = D[o.nb[s]];
+    }
+    const float s_ = sp[o.own], ah = ah2[o.own], jj = jh2[o.own];
+    const FFTerms T = ff_terms(p0, p0lo, ps, ls, Ds, ah, jj);
+    const float gmax = grad_floor_f(T.gx, T.gy, T.gz, inv2h, floor_);
+    float delta = 0.0f, Dp = 0.0f;
+#pragma unroll
+    for (int r = 0; r < (ROUNDS > 0 ? ROUNDS : 64); ++r) {
+        if (ROUNDS == 0 && r >= local_iters) break;
+        Dp = D_of_f(gmax, s_, __fadd_rn(p0, delta), floor_, lim, larsen_n);
+        const ff S = ff_S(T, Dp);
+        // delta is a correction: its rounding does not move the fixed point
+        delta = __fdividef(__fadd_rn(S.hi, S.lo), ff_den(T, ah, Dp));
+    }
+    const ff nw = ff_add_f(ff{p0, p0lo}, __fmul_rn(omega, delta));
+    phi[o.own] = nw.hi;
+    phlo[o.own] = nw.lo;
+    D[o.own] = Dp;
 }
 
 __global__ void __launch_bounds__(256) k_pass_d(Layout L, const double *__restrict__ sp,
@@ -306,23 +393,19 @@ __global__ void __launch_bounds__(256) k_pass_d(Layout L, const double *__restri
                                                 double *__restrict__ phi, double *__restrict__ D, int colour,
                                                 int lim, double larsen_n, double omega, double inv2h,
                                                 double floor_, int local_iters) {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
-    if (j >= L.ny) return;
-    const int i = 2 * t + ((j + k + colour) & 1);
-    if (i >= L.nx) return;
-    const long long q = L.at(i, j, k);
-    const long long sy = L.px, sz = L.plane;
-    const long long nb[6] = {q - 1, q + 1, q - sy, q + sy, q - sz, q + sz};
-    const double p0 = phi[q];
+    Nbrs o;
+    if (!pass_cell(L, colour, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y + 1,
+                   blockIdx.z + 1, o) ||
+        blockIdx.y * blockDim.y + threadIdx.y >= L.ny)
+        return;
+    const double p0 = phi[o.own];
     double ps[6], Ds[6];
 #pragma unroll
     for (int s = 0; s < 6; ++s) {
-        ps[s] = phi[nb[s]];
-        Ds[s] = D[nb[s]];
+        ps[s] = phi[o.nb[s]];
+        Ds[s] = D[o.nb[s]];
     }
-    const double s_ = sp[q], ah = ah2[q], jj = jh2[q];
+    const double s_ = sp[o.own], ah = ah2[o.own], jj = jh2[o.own];
     const double gx = ps[1] - ps[0], gy = ps[3] - ps[2], gz = ps[5] - ps[4];
     double A = 0.0, B = 0.0, C = 0.0;
 #pragma unroll
@@ -340,8 +423,8 @@ __global__ void __launch_bounds__(256) k_pass_d(Layout L, const double *__restri
         const double den = (ah + 3.0 * Dp) + 0.5 * C;
         delta = S / den;
     }
-    phi[q] = fma(omega, delta, p0);
-    D[q] = Dp;
+    phi[o.own] = fma(omega, delta, p0);
+    D[o.own] = Dp;
 }
 
 // ---------------------------------------------------------------------------
@@ -354,16 +437,17 @@ __global__ void k_fresh_D_f(Layout L, const float *__restrict__ sp, const float 
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
     if (i >= L.nx || j >= L.ny) return;
-    const long long q = L.at(i, j, k);
-    const long long sy = L.px, sz = L.plane;
+    const int q = L.at(i, j, k);
+    const int xm = L.at(i - 1, j, k), xp = L.at(i + 1, j, k), ym = L.at(i, j - 1, k), yp = L.at(i, j + 1, k);
+    const int zm = L.at(i, j, k - 1), zp = L.at(i, j, k + 1);
     float lxm = 0, lxp = 0, lym = 0, lyp = 0, lzm = 0, lzp = 0;
     if (phlo) {
-        lxm = phlo[q - 1]; lxp = phlo[q + 1]; lym = phlo[q - sy]; lyp = phlo[q + sy];
-        lzm = phlo[q - sz]; lzp = phlo[q + sz];
+        lxm = phlo[xm]; lxp = phlo[xp]; lym = phlo[ym]; lyp = phlo[yp];
+        lzm = phlo[zm]; lzp = phlo[zp];
     }
-    const float gx = __fadd_rn(__fsub_rn(phi[q + 1], phi[q - 1]), __fsub_rn(lxp, lxm));
-    const float gy = __fadd_rn(__fsub_rn(phi[q + sy], phi[q - sy]), __fsub_rn(lyp, lym));
-    const float gz = __fadd_rn(__fsub_rn(phi[q + sz], phi[q - sz]), __fsub_rn(lzp, lzm));
+    const float gx = __fadd_rn(__fsub_rn(phi[xp], phi[xm]), __fsub_rn(lxp, lxm));
+    const float gy = __fadd_rn(__fsub_rn(phi[yp], phi[ym]), __fsub_rn(lyp, lym));
+    const float gz = __fadd_rn(__fsub_rn(phi[zp], phi[zm]), __fsub_rn(lzp, lzm));
     Df[q] = knudsen_D_f(gx, gy, gz, inv2h, sp[q], phi[q], floor_, lim, larsen_n);
 }
 
@@ -373,10 +457,10 @@ __global__ void k_fresh_D_d(Layout L, const double *__restrict__ sp, const doubl
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
     if (i >= L.nx || j >= L.ny) return;
-    const long long q = L.at(i, j, k);
-    const long long sy = L.px, sz = L.plane;
-    Df[q] = knudsen_D_d(phi[q + 1] - phi[q - 1], phi[q + sy] - phi[q - sy], phi[q + sz] - phi[q - sz], inv2h,
-                        sp[q], phi[q], floor_, lim, larsen_n);
+    const int q = L.at(i, j, k);
+    Df[q] = knudsen_D_d(phi[L.at(i + 1, j, k)] - phi[L.at(i - 1, j, k)],
+                        phi[L.at(i, j + 1, k)] - phi[L.at(i, j - 1, k)],
+                        phi[L.at(i, j, k + 1)] - phi[L.at(i, j, k - 1)], inv2h, sp[q], phi[q], floor_, lim, larsen_n);
 }
 
 // Per-voxel residual R_p dl^2 = jh2 - ah2 phi_p + sum_s D_ps (phi_s - phi_p)
@@ -392,9 +476,9 @@ __global__ void __launch_bounds__(256) k_residual_f(Layout L, const float *__res
     const int k = blockIdx.z;
     double r2 = 0.0, j2 = 0.0;
     if (i < L.nx && j < L.ny) {
-        const long long q = L.at(i, j, k);
-        const long long sy = L.px, sz = L.plane;
-        const long long nb[6] = {q - 1, q + 1, q - sy, q + sy, q - sz, q + sz};
+        const int q = L.at(i, j, k);
+        const int nb[6] = {L.at(i - 1, j, k), L.at(i + 1, j, k), L.at(i, j - 1, k),
+                           L.at(i, j + 1, k), L.at(i, j, k - 1), L.at(i, j, k + 1)};
         const bool onface[6] = {i == 0, i == L.nx - 1, j == 0, j == L.ny - 1, k == 0, k == L.nz - 1};
         float ps[6], ls[6], Ds[6];
 #pragma unroll
@@ -434,9 +518,9 @@ __global__ void __launch_bounds__(256) k_residual_d(Layout L, const double *__re
     const int k = blockIdx.z;
     double r2 = 0.0, j2 = 0.0;
     if (i < L.nx && j < L.ny) {
-        const long long q = L.at(i, j, k);
-        const long long sy = L.px, sz = L.plane;
-        const long long nb[6] = {q - 1, q + 1, q - sy, q + sy, q - sz, q + sz};
+        const int q = L.at(i, j, k);
+        const int nb[6] = {L.at(i - 1, j, k), L.at(i + 1, j, k), L.at(i, j - 1, k),
+                           L.at(i, j + 1, k), L.at(i, j, k - 1), L.at(i, j, k + 1)};
         const bool onface[6] = {i == 0, i == L.nx - 1, j == 0, j == L.ny - 1, k == 0, k == L.nz - 1};
         const double p0 = phi[q], Dp = Df[q];
         double A = 0.0, B = 0.0;
@@ -610,6 +694,8 @@ __global__ void __launch_bounds__(256) k_bake_march(Layout L, const float *__res
     js[v] = accumulate ? js[v] + q : q;
 }
 
+// One thread per unknown of the colour in a row (ceil(nx/2) of them), one
+// y-row per thread row, one z-plane per block z.
 inline dim3 pass_grid(const Layout &L, dim3 blk) {
     const int half = (L.nx + 1) / 2;
     return dim3((half + blk.x - 1) / blk.x, (L.ny + blk.y - 1) / blk.y, L.nz);
@@ -639,16 +725,16 @@ cudaError_t launch_prep_d(const Layout &L, const Fields &f, double sigma_eps, do
 cudaError_t launch_init_f(const Layout &L, float *phi, float *phlo, float *D, double phi0, double D0, double phi_b,
                           double D_b, cudaStream_t s) {
     const int blk = 256;
-    const long long nb = (L.total + blk - 1) / blk;
-    k_init<float><<<(unsigned)nb, blk, 0, s>>>(L, phi, phlo, D, (float)phi0, (float)D0, (float)phi_b, (float)D_b);
+    const int nb = (L.total + blk - 1) / blk;
+    k_init<float><<<nb, blk, 0, s>>>(L, phi, phlo, D, (float)phi0, (float)D0, (float)phi_b, (float)D_b);
     return cudaGetLastError();
 }
 
 cudaError_t launch_init_d(const Layout &L, double *phi, double *D, double phi0, double D0, double phi_b, double D_b,
                           cudaStream_t s) {
     const int blk = 256;
-    const long long nb = (L.total + blk - 1) / blk;
-    k_init<double><<<(unsigned)nb, blk, 0, s>>>(L, phi, nullptr, D, phi0, D0, phi_b, D_b);
+    const int nb = (L.total + blk - 1) / blk;
+    k_init<double><<<nb, blk, 0, s>>>(L, phi, nullptr, D, phi0, D0, phi_b, D_b);
     return cudaGetLastError();
 }
 
@@ -671,11 +757,11 @@ cudaError_t launch_pack_from_d(const Layout &L, const double *src, double *dst, 
     return cudaGetLastError();
 }
 cudaError_t launch_f_to_d(const Layout &L, const float *hi, const float *lo, double *dst, cudaStream_t s) {
-    k_f_to_d<<<(unsigned)((L.total + 255) / 256), 256, 0, s>>>(L.total, hi, lo, dst);
+    k_f_to_d<<<(L.total + 255) / 256, 256, 0, s>>>(L.total, hi, lo, dst);
     return cudaGetLastError();
 }
 cudaError_t launch_d_to_f(const Layout &L, const double *src, float *hi, float *lo, cudaStream_t s) {
-    k_d_to_f<<<(unsigned)((L.total + 255) / 256), 256, 0, s>>>(L.total, src, hi, lo);
+    k_d_to_f<<<(L.total + 255) / 256, 256, 0, s>>>(L.total, src, hi, lo);
     return cudaGetLastError();
 }
 
@@ -684,16 +770,24 @@ cudaError_t launch_pass(Family fam, const Layout &L, const Fields &f, const Pass
     const dim3 blk(32, 8, 1);
     const dim3 grd = pass_grid(L, blk);
     switch (fam) {
-    case FAM_F32:
-        k_pass_f<false><<<grd, blk, 0, s>>>(L, f.sp, f.ah2, f.jh2, f.phi, nullptr, f.D, colour, p.lim,
-                                           (float)p.larsen_n, (float)p.omega, (float)p.inv2h, (float)p.floor_,
-                                           p.local_iters);
+    case FAM_F32: {
+        auto k = k_pass_f32<-1, 0>;
+        if (p.local_iters == 2 && p.lim == LIM_LP) k = k_pass_f32<LIM_LP, 2>;
+        else if (p.local_iters == 2 && p.lim == LIM_KERSHAW) k = k_pass_f32<LIM_KERSHAW, 2>;
+        else if (p.local_iters == 2 && p.lim == LIM_LARSEN) k = k_pass_f32<LIM_LARSEN, 2>;
+        k<<<grd, blk, 0, s>>>(L, f.sp, f.ah2, f.jh2, f.phi, f.D, colour, p.lim, (float)p.larsen_n, (float)p.omega,
+                              (float)p.inv2h, (float)p.floor_, p.local_iters);
         break;
-    case FAM_FF:
-        k_pass_f<true><<<grd, blk, 0, s>>>(L, f.sp, f.ah2, f.jh2, f.phi, f.phlo, f.D, colour, p.lim,
-                                          (float)p.larsen_n, (float)p.omega, (float)p.inv2h, (float)p.floor_,
-                                          p.local_iters);
+    }
+    case FAM_FF: {
+        auto k = k_pass_ff<-1, 0>;
+        if (p.local_iters == 2 && p.lim == LIM_LP) k = k_pass_ff<LIM_LP, 2>;
+        else if (p.local_iters == 2 && p.lim == LIM_KERSHAW) k = k_pass_ff<LIM_KERSHAW, 2>;
+        else if (p.local_iters == 2 && p.lim == LIM_LARSEN) k = k_pass_ff<LIM_LARSEN, 2>;
+        k<<<grd, blk, 0, s>>>(L, f.sp, f.ah2, f.jh2, f.phi, f.phlo, f.D, colour, p.lim, (float)p.larsen_n,
+                              (float)p.omega, (float)p.inv2h, (float)p.floor_, p.local_iters);
         break;
+    }
     case FAM_F64:
         k_pass_d<<<grd, blk, 0, s>>>(L, f.sp64, f.ah264, f.jh264, f.phi64, f.D64, colour, p.lim, p.larsen_n,
                                     p.omega, p.inv2h, p.floor_, p.local_iters);
