@@ -62,6 +62,11 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample length")
     ap.add_argument("--no-extras", action="store_true", help="skip cpu baseline / 256^3 roofline / e2e")
+    ap.add_argument("--workload", choices=["cloud", "batch"], default="cloud",
+                    help="cloud: the 128^3 solve (default); batch: independent solves of uneven size, "
+                         "batched in shared launches vs one after another")
+    ap.add_argument("--count", type=int, default=16, help="batch workload: number of solves")
+    ap.add_argument("--sizes", default="32,48,64,96", help="batch workload: edge lengths drawn from")
     return ap.parse_args()
 
 
@@ -446,10 +451,88 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_batch(args):
+    """Independent solves of uneven size (edges drawn from --sizes, per-solve
+    fBm seed, albedo U[0.8, 0.99], point or oblique directional light), solved
+    to the residual one after another with fld_solve and together with
+    fld_solve_batch; both timed with CUDA events on one stream."""
+    import numpy as np
+    import torch
+
+    import fld_inputs
+    import paper_1403_8105_gb300 as fld
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sizes = tuple(int(x) for x in args.sizes.split(","))
+    specs = fld_inputs.batch_cases(args.count, seed=1234, sizes=sizes)
+    stream = torch.cuda.Stream(device=dev)
+    media = []
+    for sp in specs:
+        sig, alb = fld_inputs.cloud_medium(sp["n"], seed=sp["seed"] % 100000, albedo=sp["albedo"])
+        media.append((torch.from_numpy(sig).to(dev), torch.from_numpy(alb).to(dev), sp))
+    torch.cuda.synchronize()
+    p = fld.params(limiter="lp", precision="mixed", tol=args.tol, check_every=args.check_every,
+                   max_iters=args.max_iters)
+
+    def setup():
+        grids = []
+        for sig, alb, sp in media:
+            n = sp["n"]
+            g = fld.Grid(n, n, n, 1.0 / n, stream=stream.cuda_stream)
+            g.set_medium(sig, alb)
+            lt = sp["light"]
+            if lt.kind == "point":
+                g.bake_point(lt.pos, lt.power)
+            else:
+                g.bake_directional(lt.dir, lt.radiance)
+            grids.append(g)
+        stream.synchronize()
+        return grids
+
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {}
+    for mode in ("sequential", "batched"):
+        grids = setup()
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            if mode == "sequential":
+                rs = [g.solve(p) for g in grids]
+            else:
+                st, rs = fld.fld_solve_batch(grids, p)
+            e1.record(stream)
+            e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        upd = sum(r.iterations * g.shape[0] * g.shape[1] * g.shape[2] for r, g in zip(rs, grids))
+        lat = sorted(r.ms for r in rs) if mode == "batched" else None
+        out[mode] = {"ms": ms, "updates": upd, "value": upd / (ms / 1e3),
+                     "converged": sum(r.status == fld.FLD_OK for r in rs),
+                     "per_solve": [[g.shape[0], fld.fld_status_string(r.status), r.iterations,
+                                    float("%.3g" % r.rel_residual)] for r, g in zip(rs, grids)]}
+        if lat:
+            out[mode]["latency_ms_p50"] = float(np.percentile(lat, 50))
+            out[mode]["latency_ms_p99"] = float(np.percentile(lat, 99))
+        for g in grids:
+            g.close()
+    line = {
+        "metric": METRIC, "value": out["batched"]["value"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": out["batched"]["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (float-float correction sweeps)", "data": "synthetic",
+        "config": {"workload": f"batch of {args.count} independent solves, edges from {sizes}, per-solve fBm "
+                               f"seed, albedo U[0.8,0.99], point or oblique light, LP, rel. residual {args.tol:g}",
+                   "sizes": [sp["n"] for sp in specs]},
+        "batched": out["batched"], "sequential": out["sequential"],
+        "speedup_vs_sequential": out["sequential"]["ms"] / out["batched"]["ms"],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_gpu(args)
 

@@ -89,8 +89,11 @@ typedef struct {
     int limiter;          /* fld_limiter                                             */
     double larsen_n;      /* n of Larsen-n, > 0 (default 2)                          */
     double omega;         /* SOR factor of Eq. 36, 0 < omega < 2; <= 0 selects
-                             2/(1 + sin(pi/(n+1))) clamped to [1, 1.9], n the
-                             largest extent                                          */
+                             2/(1 + sin(pi/(n+1))) clamped to [1, 1.93], n the
+                             largest extent.  fld_solve keeps the state with the
+                             best residual and, if the residual turns non-finite
+                             or grows 1000-fold, returns to it with omega - 1
+                             reduced by 3 % (at most 8 times)                        */
     int local_iters;      /* rounds of Knudsen -> D_p -> phi' per point before the
                              SOR blend, >= 1.  1 is Algorithm 1 as printed; 2 makes
                              each point's update self-consistent in its own D_p,
@@ -128,6 +131,8 @@ typedef struct {
     double ms_sweep_fp32;  /* device time inside blocks of single-precision sweeps  */
     double ms_sweep_corr;  /* device time inside blocks of float-float / FP64 sweeps */
     long long kernels;     /* kernel launches the solve issued (incl. graph nodes)  */
+    int omega_backoffs;    /* times the solve returned to its best state and
+                              reduced omega after the residual diverged         */
 } fld_solve_result;
 
 /* Fill *p with the defaults: LP limiter, Larsen n = 2, omega auto,
@@ -138,7 +143,8 @@ void fld_default_params(fld_solve_params *p);
 /* Create a grid of nx*ny*nz unknowns (each >= 1) of edge h > 0 on the
  * current CUDA device.  stream: cudaStream_t or NULL.  *out receives the
  * handle.  Allocates the solver fields on the device (about 40 bytes per
- * voxel; FP64 fields are added on first FP64 use). */
+ * voxel; the FP64 fields are added on first FP64 use and the solve's
+ * snapshot of its best state on the first fld_solve). */
 fld_status fld_create_grid(int nx, int ny, int nz, double h, void *stream, fld_grid *out);
 
 /* Medium: extinction sigma_t >= 0 and albedo in [0, 1] (unpadded, float).
@@ -188,6 +194,25 @@ fld_status fld_iterate(fld_grid g, const fld_solve_params *p, int iterations);
  * outcome.  Returns FLD_OK, FLD_ERR_NOT_CONVERGED or FLD_ERR_DIVERGED (r
  * filled in every case), or an error. */
 fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r);
+
+/* Solve `count` independent grids together (not a paper item; the batched
+ * form of fld_solve).  Grids are taken in order of size and packed into groups
+ * whose per-iteration working set (24 bytes per voxel) fits in 3/4 of the
+ * GPU's L2; groups run one after another.  Within a group every colour pass of
+ * every still-active grid runs in one launch, blocks of p->check_every
+ * iterations are replayed from one CUDA graph, the residuals of all grids are
+ * reduced in one pass per check (per-grid slots), and grids leave the launch
+ * as they converge.  Each grid follows
+ * exactly the decisions fld_solve would take for it alone (same omega, check
+ * schedule, precision switch and safeguard), so its result equals its solo
+ * solve.  Precision FP32 or MIXED (FP64: FLD_ERR_INVALID_ARG).  All grids must
+ * live on one device and be distinct; the batch runs on grids[0]'s stream after
+ * every grid's prior work finished.  results (may be NULL) receives count
+ * entries; there `ms` is the time from the start of the batch to the check at
+ * which that grid finished and `kernels` counts the launches of the whole
+ * batch.  Returns FLD_OK if every grid converged, else FLD_ERR_DIVERGED if one
+ * diverged, else FLD_ERR_NOT_CONVERGED. */
+fld_status fld_solve_batch(fld_grid *grids, int count, const fld_solve_params *p, fld_solve_result *results);
 
 /* Relative residual Rbar/jbar of the current phi (Eq. 37 with D recomputed
  * from phi, RMS over the unknowns beyond p->residual_margin), evaluated in

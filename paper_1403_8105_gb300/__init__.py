@@ -26,7 +26,8 @@ __all__ = [
     "LIMITERS", "PRECISIONS", "FldError", "SolveParams", "SolveResult",
     "load", "library_path", "fld_default_params", "fld_create_grid", "fld_set_medium", "fld_set_source",
     "fld_get_source", "fld_bake_directional", "fld_bake_point", "fld_set_state", "fld_get_state",
-    "fld_iterate", "fld_solve", "fld_residual", "fld_residual_noalloc", "fld_destroy", "fld_status_string",
+    "fld_iterate", "fld_solve", "fld_solve_batch", "fld_residual", "fld_residual_noalloc", "fld_destroy",
+    "fld_status_string",
     "fld_last_error", "Grid", "params",
 ]
 
@@ -56,6 +57,7 @@ class SolveResult(ctypes.Structure):
         ("iterations_corr", ctypes.c_int), ("checks", ctypes.c_int), ("rel_residual", ctypes.c_double),
         ("jbar", ctypes.c_double), ("omega", ctypes.c_double), ("ms", ctypes.c_double),
         ("ms_sweep_fp32", ctypes.c_double), ("ms_sweep_corr", ctypes.c_double), ("kernels", ctypes.c_longlong),
+        ("omega_backoffs", ctypes.c_int),
     ]
 
     def as_dict(self):
@@ -107,6 +109,7 @@ def load(build_if_missing: bool = True):
             "fld_get_state": (c_int, [_vp, _vp, _vp, c_int]),
             "fld_iterate": (c_int, [_vp, P, c_int]),
             "fld_solve": (c_int, [_vp, P, R]),
+            "fld_solve_batch": (c_int, [ctypes.POINTER(_vp), c_int, P, R]),
             "fld_residual": (c_int, [_vp, P, ctypes.POINTER(c_double)]),
             "fld_residual_noalloc": (c_int, [c_int, c_int, c_int, c_double, P, _vp, _vp, _vp, _vp, _vp,
                                              ctypes.POINTER(c_double), _vp]),
@@ -232,6 +235,17 @@ def fld_solve(g, p: SolveParams, check: bool = True) -> SolveResult:
         _check(st, "fld_solve", allow=(FLD_OK, FLD_ERR_NOT_CONVERGED, FLD_ERR_DIVERGED))
     r.status = st
     return r
+
+
+def fld_solve_batch(grids, p: SolveParams, check: bool = True):
+    """Solve several grids together; returns (status, [SolveResult per grid])."""
+    n = len(grids)
+    arr = (_vp * n)(*[g.handle if isinstance(g, Grid) else g for g in grids])
+    out = (SolveResult * n)()
+    st = load().fld_solve_batch(arr, n, ctypes.byref(p), out)
+    if check:
+        _check(st, "fld_solve_batch", allow=(FLD_OK, FLD_ERR_NOT_CONVERGED, FLD_ERR_DIVERGED))
+    return st, list(out)
 
 
 def fld_residual(g, p: SolveParams) -> float:

@@ -10,8 +10,11 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
+#include <chrono>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "../../include/fld.h"
 #include "fld_device.cuh"
@@ -41,6 +44,10 @@ fld_status cuda_fail(cudaError_t e, const char *where) {
 
 constexpr double kFloorNoEmission = 1e-30;   // floor of Eq. 35 when jbar = 0
 constexpr int kStallChecks = 48;              // checks without a new minimum before giving up
+constexpr int kSwitchChecks = 24;             // ... before single precision hands over (MIXED)
+constexpr double kGuardGrowth = 1e3;          // residual growth (vs the best) read as divergence
+constexpr int kMaxBackoffs = 8;               // omega reductions before reporting divergence
+constexpr double kOmegaMax = 1.93;            // upper clamp of the automatic omega
 
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
@@ -77,6 +84,9 @@ struct fld_grid_s {
     GraphEntry graphs[3];
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evb0 = nullptr, evb1 = nullptr;
     long long kernels = 0;                       // kernel launches issued so far
+    // last good state of a solve (float family: phi, lo, D; FP64: phi, D)
+    float *snap_phi = nullptr, *snap_lo = nullptr, *snap_D = nullptr;
+    double *snap_phi64 = nullptr, *snap_D64 = nullptr;
 };
 
 namespace {
@@ -114,7 +124,7 @@ double omega_of(const fld_grid_s *g, const fld_solve_params *p) {
     if (g->nz > n) n = g->nz;
     double w = 2.0 / (1.0 + sin(M_PI / (n + 1.0)));
     if (w < 1.0) w = 1.0;
-    if (w > 1.9) w = 1.9;
+    if (w > kOmegaMax) w = kOmegaMax;
     return w;
 }
 
@@ -322,6 +332,92 @@ fld_status validate_inputs(fld_grid_s *g, const float *st, const float *alb, con
     return FLD_OK;
 }
 
+// Copy the family's state into (save) or out of (restore) the snapshot.
+fld_status snapshot(fld_grid_s *g, Family fam, bool save) {
+    const size_t nf = sizeof(float) * (size_t)g->L.total, nd = sizeof(double) * (size_t)g->L.total;
+    if (fam == FAM_F64) {
+        if (!g->snap_phi64) {
+            if (cudaMalloc((void **)&g->snap_phi64, nd) != cudaSuccess ||
+                cudaMalloc((void **)&g->snap_D64, nd) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return fail(FLD_ERR_OOM, "cudaMalloc of the solve snapshot failed");
+            }
+        }
+        double *a[2] = {g->f.phi64, g->f.D64}, *b[2] = {g->snap_phi64, g->snap_D64};
+        for (int i = 0; i < 2; ++i)
+            FLD_CK(cudaMemcpyAsync(save ? b[i] : a[i], save ? a[i] : b[i], nd, cudaMemcpyDeviceToDevice, g->stream));
+    } else {
+        if (!g->snap_phi) {
+            if (cudaMalloc((void **)&g->snap_phi, nf) != cudaSuccess ||
+                cudaMalloc((void **)&g->snap_lo, nf) != cudaSuccess ||
+                cudaMalloc((void **)&g->snap_D, nf) != cudaSuccess) {
+                (void)cudaGetLastError();
+                return fail(FLD_ERR_OOM, "cudaMalloc of the solve snapshot failed");
+            }
+        }
+        float *a[3] = {g->f.phi, g->f.phlo, g->f.D}, *b[3] = {g->snap_phi, g->snap_lo, g->snap_D};
+        for (int i = 0; i < 3; ++i)
+            FLD_CK(cudaMemcpyAsync(save ? b[i] : a[i], save ? a[i] : b[i], nf, cudaMemcpyDeviceToDevice, g->stream));
+    }
+    return FLD_OK;
+}
+
+// Decisions of one solve after each residual check (shared by fld_solve and
+// fld_solve_batch, so a grid takes the same path alone and in a batch).
+enum Action { ACT_CONTINUE, ACT_SAVE, ACT_RESTORE, ACT_SWITCH, ACT_CONVERGED, ACT_DIVERGED, ACT_STALLED };
+
+struct Controller {
+    int precision = FLD_PREC_MIXED;
+    double tol = 1e-6, sw = 2e-5;
+    Family fam = FAM_F32;
+    double best = INFINITY;   // best residual after at least one block
+    int since_best = 0;       // checks without a new minimum
+    int backoffs = 0;
+
+    void begin_phase() { since_best = 0; }
+    // First check (before any iteration): the state is kept as the fallback of
+    // the safeguard, but progress is measured from the first block onwards
+    // (SOR's early transient may sit above the initial residual for a while).
+    Action first(double rel) const {
+        if (rel <= tol) return ACT_CONVERGED;
+        if (!isfinite(rel)) return ACT_DIVERGED;
+        return ACT_SAVE;
+    }
+    // After a block of iterations.
+    Action next(double rel, double omega) {
+        const bool diverging = !isfinite(rel) || rel > kGuardGrowth * best || (since_best >= 16 && rel > 2.0 * best);
+        if (diverging) {
+            if (backoffs >= kMaxBackoffs || omega <= 1.0) return ACT_DIVERGED;
+            ++backoffs;
+            since_best = 0;
+            return ACT_RESTORE;
+        }
+        if (rel <= tol) return ACT_CONVERGED;
+        Action a = ACT_CONTINUE;
+        if (rel < best) {
+            best = rel;
+            since_best = 0;
+            a = ACT_SAVE;
+        } else {
+            ++since_best;
+        }
+        // single precision has done what it can (Sec. 6.2: ~1e-4 is its limit)
+        if (precision == FLD_PREC_MIXED && fam == FAM_F32 && (rel <= sw || since_best >= kSwitchChecks))
+            return ACT_SWITCH;
+        // The float-float and FP64 sweeps reach residuals near 1e-7; stalling
+        // far above the tolerance there means over-relaxation is cycling, not
+        // that the arithmetic is exhausted: back off omega.
+        if (fam != FAM_F32 && tol > 0.0 && since_best >= kSwitchChecks && best > 100.0 * tol) {
+            if (backoffs >= kMaxBackoffs || omega <= 1.0) return ACT_STALLED;
+            ++backoffs;
+            since_best = 0;
+            return ACT_RESTORE;
+        }
+        if (since_best >= kStallChecks && !(precision == FLD_PREC_MIXED && fam == FAM_F32)) return ACT_STALLED;
+        return a;
+    }
+};
+
 }  // namespace
 
 // ===========================================================================
@@ -448,6 +544,9 @@ void fld_destroy(fld_grid g) {
     if (g->ev1) cudaEventDestroy(g->ev1);
     if (g->evb0) cudaEventDestroy(g->evb0);
     if (g->evb1) cudaEventDestroy(g->evb1);
+    void *snaps[] = {g->snap_phi, g->snap_lo, g->snap_D, g->snap_phi64, g->snap_D64};
+    for (void *p : snaps)
+        if (p) cudaFree(p);
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
     delete g;
 }
@@ -653,19 +752,38 @@ fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r)
         fam = FAM_FF;   // continue a correction phase
     }
     if ((st = sync_family(g, fam)) != FLD_OK) return st;
-    const PassParams pp = pass_params(g, p);
+    PassParams pp = pass_params(g, p);
     const double sw = p->fp32_switch > 0.0 ? p->fp32_switch : 2e-5;
     res.jbar = g->jbar;
     res.omega = pp.omega;
     FLD_CK(cudaEventRecord(g->ev0, g->stream));
-    double rel = INFINITY, best = INFINITY;
-    int since_best = 0;
+    Controller ctl;
+    ctl.precision = p->precision;
+    ctl.tol = p->tol;
+    ctl.sw = sw;
+    ctl.fam = fam;
+    double rel = INFINITY;
     int it = 0;
     bool stalled = false;
     fld_status outcome = FLD_ERR_NOT_CONVERGED;
+    // Safeguarded over-relaxation: the state with the best residual so far is
+    // kept; if the residual turns non-finite, grows kGuardGrowth-fold, or
+    // makes no new minimum for 16 checks while above twice the best, the solve
+    // returns to it and continues with omega - 1 reduced by 3 %.
+    Family snap_fam = fam;
+    bool snap_lo_live = g->lo_live;
+    auto save = [&]() -> fld_status {
+        fld_status s2 = snapshot(g, fam, true);
+        snap_fam = fam;
+        snap_lo_live = g->lo_live;
+        return s2;
+    };
     if ((st = residual_now(g, fam, pp, p->residual_margin, &rel)) != FLD_OK) return st;
     ++res.checks;
-    if (rel <= p->tol) outcome = FLD_OK;
+    Action a = ctl.first(rel);
+    if (a == ACT_CONVERGED) outcome = FLD_OK;
+    else if (a == ACT_DIVERGED) outcome = FLD_ERR_DIVERGED;
+    else if ((st = save()) != FLD_OK) return st;
     while (outcome == FLD_ERR_NOT_CONVERGED && it < p->max_iters) {
         int k = p->check_every;
         if (k > p->max_iters - it) k = p->max_iters - it;
@@ -681,35 +799,33 @@ fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r)
         FLD_CK(cudaEventElapsedTime(&bms, g->evb0, g->evb1));
         if (fam == FAM_F32) res.ms_sweep_fp32 += bms;
         else res.ms_sweep_corr += bms;
-        if (!isfinite(rel)) {
-            outcome = FLD_ERR_DIVERGED;
+        a = ctl.next(rel, pp.omega);
+        switch (a) {
+        case ACT_CONVERGED: outcome = FLD_OK; break;
+        case ACT_DIVERGED: outcome = FLD_ERR_DIVERGED; break;
+        case ACT_STALLED: stalled = true; break;
+        case ACT_SAVE:
+            if ((st = save()) != FLD_OK) return st;
             break;
-        }
-        if (rel <= p->tol) {
-            outcome = FLD_OK;
+        case ACT_RESTORE:
+            if ((st = snapshot(g, snap_fam, false)) != FLD_OK) return st;
+            fam = snap_fam;
+            ctl.fam = fam;
+            g->lo_live = snap_lo_live;
+            pp.omega = 1.0 + 0.97 * (pp.omega - 1.0);
+            rel = ctl.best;
             break;
-        }
-        if (rel < best) {
-            best = rel;
-            since_best = 0;
-        } else {
-            ++since_best;
-        }
-        if (since_best >= kStallChecks && !(p->precision == FLD_PREC_MIXED && fam == FAM_F32)) {
-            // no new minimum for many checks: the residual has reached the
-            // floor of the arithmetic in use
-            stalled = true;
-            break;
-        }
-        if (p->precision == FLD_PREC_MIXED && fam == FAM_F32 && (rel <= sw || since_best >= 4)) {
-            // single precision has done what it can (Sec. 6.2: ~1e-4 is its
-            // practical limit): continue with float-float correction sweeps
+        case ACT_SWITCH:
             if ((st = sync_family(g, FAM_FF)) != FLD_OK) return st;
             fam = FAM_FF;
-            since_best = 0;
-            best = rel;
+            ctl.fam = fam;
+            ctl.begin_phase();
+            break;
+        case ACT_CONTINUE: break;
         }
+        if (stalled) break;
     }
+    res.omega_backoffs = ctl.backoffs;
     FLD_CK(cudaEventRecord(g->ev1, g->stream));
     FLD_CK(cudaEventSynchronize(g->ev1));
     float ms = 0.0f;
@@ -718,12 +834,396 @@ fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r)
     res.iterations = it;
     res.rel_residual = rel;
     res.ms = ms;
+    res.omega = pp.omega;
     res.kernels = g->kernels - kernels0;
     if (r) *r = res;
     if (outcome == FLD_ERR_DIVERGED) g_last_error = "residual became NaN or infinite";
     if (outcome == FLD_ERR_NOT_CONVERGED)
         g_last_error = stalled ? "residual stalled above tol (floor of the arithmetic)" : "max_iters reached before tol";
     return outcome;
+}
+
+
+// Solve one group of grids in shared launches (see fld_solve_batch).
+static fld_status solve_group(fld_grid *grids, int count, const fld_solve_params *p, fld_solve_result *results,
+                              double t_offset_ms) {
+    fld_status st = FLD_OK;
+    // Prepare and initialise every grid on its own stream first.
+    std::vector<Family> fam(count, FAM_F32);
+    for (int a = 0; a < count; ++a) {
+        fld_grid_s *g = grids[a];
+        FLD_CK(cudaStreamSynchronize(g->stream));
+        if ((st = prepare(g, p, FAM_F32)) != FLD_OK) return st;
+        if (!p->warm_start) {
+            if ((st = init_state(g, p, FAM_F32)) != FLD_OK) return st;
+        } else if (p->precision == FLD_PREC_MIXED && !g->valid_d && g->lo_live) {
+            fam[a] = FAM_FF;
+        }
+        if ((st = sync_family(g, fam[a])) != FLD_OK) return st;
+        FLD_CK(cudaStreamSynchronize(g->stream));
+    }
+    // From here on all work of the batch is ordered on the first grid's stream.
+    cudaStream_t bs = grids[0]->stream;
+    std::vector<cudaStream_t> own(count);
+    for (int a = 0; a < count; ++a) {
+        own[a] = grids[a]->stream;
+        grids[a]->stream = bs;
+    }
+    struct Restore {
+        fld_grid *g;
+        std::vector<cudaStream_t> *s;
+        ~Restore() {
+            for (size_t a = 0; a < s->size(); ++a) g[a]->stream = (*s)[a];
+        }
+    } restore{grids, &own};
+
+    const double sw = p->fp32_switch > 0.0 ? p->fp32_switch : 2e-5;
+    std::vector<BatchDesc> hd(count);
+    std::vector<int> res_count(count);
+    int total_res = 0;
+    const int rounds = p->local_iters < 1 ? 1 : p->local_iters;
+    for (int a = 0; a < count; ++a) {
+        fld_grid_s *g = grids[a];
+        const PassParams pp = pass_params(g, p);
+        BatchDesc &d = hd[a];
+        d.L = g->L;
+        d.sp = g->f.sp; d.ah2 = g->f.ah2; d.jh2 = g->f.jh2; d.phi = g->f.phi; d.phlo = g->f.phlo;
+        d.D = g->f.D; d.Df = g->f.Df;
+        d.omega = (float)pp.omega; d.inv2h = (float)pp.inv2h; d.floor_ = (float)pp.floor_;
+        d.larsen_n = (float)pp.larsen_n; d.lim = pp.lim; d.rounds = rounds;
+        d.mode = fam[a] == FAM_FF ? 1 : 0;
+        d.active = 1;
+        pass_dims(g->L, &d.pass_bx, &d.pass_by);
+        residual_dims(g->L, &d.res_bx, &d.res_by);
+        res_count[a] = d.res_bx * d.res_by * g->nz;
+        d.res_slot = total_res;
+        total_res += res_count[a];
+    }
+    // CTA table of the batched residual (rebuilt over the active grids as
+    // grids finish).
+    std::vector<int> res_tab;
+    auto build_tables = [&]() {
+        res_tab.clear();
+        for (int a = 0; a < count; ++a) {
+            if (!hd[a].active) continue;
+            hd[a].res_first = (int)res_tab.size();
+            res_tab.insert(res_tab.end(), (size_t)res_count[a], a);
+        }
+    };
+    build_tables();
+
+    // Device workspace of this call.
+    BatchDesc *d_desc = nullptr;
+    int *d_res = nullptr, *d_count = nullptr;
+    double *d_part = nullptr, *d_out = nullptr;
+    struct Free {
+        void *p[5];
+        ~Free() {
+            for (void *q : p)
+                if (q) cudaFree(q);
+        }
+    } fr{{nullptr, nullptr, nullptr, nullptr, nullptr}};
+    if (cudaMalloc((void **)&d_desc, sizeof(BatchDesc) * count) != cudaSuccess ||
+        cudaMalloc((void **)&d_res, sizeof(int) * (size_t)total_res) != cudaSuccess ||
+        cudaMalloc((void **)&d_count, sizeof(int) * count) != cudaSuccess ||
+        cudaMalloc((void **)&d_part, sizeof(double) * 2 * (size_t)total_res) != cudaSuccess ||
+        cudaMalloc((void **)&d_out, sizeof(double) * 2 * count) != cudaSuccess) {
+        (void)cudaGetLastError();
+        fr.p[0] = d_desc; fr.p[1] = d_res; fr.p[2] = d_count; fr.p[3] = d_part; fr.p[4] = d_out;
+        return fail(FLD_ERR_OOM, "cudaMalloc of the batch workspace failed");
+    }
+    fr.p[0] = d_desc; fr.p[1] = d_res; fr.p[2] = d_count; fr.p[3] = d_part; fr.p[4] = d_out;
+    FLD_CK(cudaMemcpyAsync(d_count, res_count.data(), sizeof(int) * count, cudaMemcpyHostToDevice, bs));
+    auto upload = [&](bool tables) -> fld_status {
+        FLD_CK(cudaMemcpyAsync(d_desc, hd.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, bs));
+        if (tables) {
+            if (!res_tab.empty())
+                FLD_CK(cudaMemcpyAsync(d_res, res_tab.data(), sizeof(int) * res_tab.size(), cudaMemcpyHostToDevice, bs));
+        }
+        return FLD_OK;
+    };
+    if ((st = upload(true)) != FLD_OK) return st;
+
+    std::vector<fld_solve_result> res(count);
+    std::vector<Controller> ctl(count);
+    std::vector<PassParams> ppv(count);
+    for (int a = 0; a < count; ++a) ppv[a] = pass_params(grids[a], p);
+    std::vector<Family> snap_fam(count);
+    std::vector<bool> snap_lo(count);
+    std::vector<double> host_out(2 * count);
+    long long launches = 0;
+    for (int a = 0; a < count; ++a) {
+        memset(&res[a], 0, sizeof(fld_solve_result));
+        res[a].status = FLD_ERR_NOT_CONVERGED;
+        res[a].jbar = grids[a]->jbar;
+        res[a].omega = hd[a].omega;
+        ctl[a].precision = p->precision;
+        ctl[a].tol = p->tol;
+        ctl[a].sw = sw;
+        ctl[a].fam = fam[a];
+    }
+    const auto t0 = std::chrono::steady_clock::now();
+    auto elapsed_ms = [&]() {
+        return t_offset_ms + std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    };
+    auto residuals = [&]() -> fld_status {
+        FLD_CK(launch_residual_batch(d_desc, d_res, (int)res_tab.size(), count, d_count, d_part, d_out, p->limiter,
+                                     p->residual_margin, bs));
+        launches += 3;
+        FLD_CK(cudaMemcpyAsync(host_out.data(), d_out, sizeof(double) * 2 * count, cudaMemcpyDeviceToHost, bs));
+        FLD_CK(cudaStreamSynchronize(bs));
+        return FLD_OK;
+    };
+    auto rel_of = [&](int a) {
+        fld_grid_s *g = grids[a];
+        const int m = p->residual_margin;
+        const long long ex = g->nx - 2LL * m, ey = g->ny - 2LL * m, ez = g->nz - 2LL * m;
+        const long long cnt = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
+        const double rb = cnt > 0 ? sqrt(host_out[2 * a] / (double)cnt) : 0.0;
+        const double jb = sqrt(host_out[2 * a + 1] / (double)nvox(g));
+        return jb > 0.0 ? rb / jb : rb / (g->h * g->h);
+    };
+    auto finish = [&](int a, fld_status s2, double rel) {
+        hd[a].active = 0;
+        res[a].status = s2;
+        res[a].rel_residual = rel;
+        res[a].ms = elapsed_ms();
+    };
+    // first check
+    if ((st = residuals()) != FLD_OK) return st;
+    int active = 0;
+    for (int a = 0; a < count; ++a) {
+        const double rel = rel_of(a);
+        res[a].rel_residual = rel;
+        ++res[a].checks;
+        const Action act = ctl[a].first(rel);
+        if (act == ACT_CONVERGED) finish(a, FLD_OK, rel);
+        else if (act == ACT_DIVERGED) finish(a, FLD_ERR_DIVERGED, rel);
+        else {
+            if ((st = snapshot(grids[a], fam[a], true)) != FLD_OK) return st;
+            snap_fam[a] = fam[a];
+            snap_lo[a] = grids[a]->lo_live;
+            ++active;
+        }
+    }
+    if ((st = upload(false)) != FLD_OK) return st;
+
+    // The sweeps of the active grids are one CUDA graph: each grid's chain of
+    // solo pass kernels is captured on one stream of a small pool, forked from
+    // and joined back to the batch stream, so independent grids run
+    // concurrently and each runs exactly the kernels of its solo solve.  The
+    // graph covers up to kGraphIters iterations and is replayed per check; it
+    // is captured again when the active set, a grid's precision or its omega
+    // changes.
+    constexpr int kGraphIters = 64;
+    const int nside = count < 16 ? count : 16;
+    std::vector<cudaStream_t> side(nside, nullptr);
+    std::vector<cudaEvent_t> join(nside, nullptr);
+    cudaEvent_t fork = nullptr;
+    struct SideFree {
+        std::vector<cudaStream_t> *s;
+        std::vector<cudaEvent_t> *j;
+        cudaEvent_t *f;
+        ~SideFree() {
+            for (auto x : *s)
+                if (x) cudaStreamDestroy(x);
+            for (auto x : *j)
+                if (x) cudaEventDestroy(x);
+            if (*f) cudaEventDestroy(*f);
+        }
+    } sf{&side, &join, &fork};
+    FLD_CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    for (int i = 0; i < nside; ++i) {
+        FLD_CK(cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking));
+        FLD_CK(cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming));
+    }
+    cudaGraphExec_t exec = nullptr;
+    int graph_k = -1;
+    bool dirty = true;
+    struct GraphFree {
+        cudaGraphExec_t *e;
+        ~GraphFree() {
+            if (*e) cudaGraphExecDestroy(*e);
+        }
+    } gf{&exec};
+    auto capture = [&](int kg) -> fld_status {
+        if (exec) {
+            cudaGraphExecDestroy(exec);
+            exec = nullptr;
+        }
+        cudaGraph_t graph = nullptr;
+        FLD_CK(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
+        cudaError_t ce = cudaEventRecord(fork, bs);
+        for (int i = 0; i < nside && ce == cudaSuccess; ++i) ce = cudaStreamWaitEvent(side[i], fork, 0);
+        int slot = 0;
+        for (int a = 0; a < count && ce == cudaSuccess; ++a) {
+            if (!hd[a].active) continue;
+            cudaStream_t ss = side[slot++ % nside];
+            for (int i = 0; i < kg && ce == cudaSuccess; ++i)
+                for (int c = 0; c < 2 && ce == cudaSuccess; ++c)
+                    ce = launch_pass(fam[a], grids[a]->L, grids[a]->f, ppv[a], c, ss);
+        }
+        for (int i = 0; i < nside && ce == cudaSuccess; ++i) {
+            ce = cudaEventRecord(join[i], side[i]);
+            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(bs, join[i], 0);
+        }
+        cudaError_t ce2 = cudaStreamEndCapture(bs, &graph);
+        if (ce != cudaSuccess || ce2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(ce != cudaSuccess ? ce : ce2, "batched graph capture");
+        }
+        ce = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ce != cudaSuccess) {
+            exec = nullptr;
+            return cuda_fail(ce, "cudaGraphInstantiate (batch)");
+        }
+        graph_k = kg;
+        dirty = false;
+        return FLD_OK;
+    };
+    int it = 0;
+    while (active > 0 && it < p->max_iters) {
+        int k = p->check_every;
+        if (k > p->max_iters - it) k = p->max_iters - it;
+        // k iterations as reps replays of a kg-iteration graph
+        int kg = k < kGraphIters ? k : kGraphIters;
+        while (k % kg) --kg;
+        if (!exec || dirty || graph_k != kg)
+            if ((st = capture(kg)) != FLD_OK) return st;
+        for (int rep = 0; rep < k / kg; ++rep) FLD_CK(cudaGraphLaunch(exec, bs));
+        launches += 2LL * k * active;
+        it += k;
+        for (int a = 0; a < count; ++a) {
+            if (!hd[a].active) continue;
+            res[a].iterations += k;
+            if (hd[a].mode == 0) res[a].iterations_fp32 += k;
+            else res[a].iterations_corr += k;
+        }
+        if ((st = residuals()) != FLD_OK) return st;
+        bool changed = false;
+        for (int a = 0; a < count; ++a) {
+            if (!hd[a].active) continue;
+            fld_grid_s *g = grids[a];
+            const double rel = rel_of(a);
+            res[a].rel_residual = rel;
+            ++res[a].checks;
+            const Action act = ctl[a].next(rel, ppv[a].omega);
+            switch (act) {
+            case ACT_CONVERGED: finish(a, FLD_OK, rel); --active; changed = dirty = true; break;
+            case ACT_DIVERGED: finish(a, FLD_ERR_DIVERGED, rel); --active; changed = dirty = true; break;
+            case ACT_STALLED: finish(a, FLD_ERR_NOT_CONVERGED, rel); --active; changed = dirty = true; break;
+            case ACT_SAVE:
+                if ((st = snapshot(g, fam[a], true)) != FLD_OK) return st;
+                snap_fam[a] = fam[a];
+                snap_lo[a] = g->lo_live;
+                break;
+            case ACT_RESTORE:
+                if ((st = snapshot(g, snap_fam[a], false)) != FLD_OK) return st;
+                fam[a] = snap_fam[a];
+                ctl[a].fam = fam[a];
+                g->lo_live = snap_lo[a];
+                hd[a].mode = fam[a] == FAM_FF ? 1 : 0;
+                ppv[a].omega = 1.0 + 0.97 * (ppv[a].omega - 1.0);
+                hd[a].omega = (float)ppv[a].omega;
+                changed = dirty = true;
+                break;
+            case ACT_SWITCH:
+                if ((st = sync_family(g, FAM_FF)) != FLD_OK) return st;
+                fam[a] = FAM_FF;
+                ctl[a].fam = FAM_FF;
+                ctl[a].begin_phase();
+                hd[a].mode = 1;
+                changed = dirty = true;
+                break;
+            case ACT_CONTINUE: break;
+            }
+        }
+        if (changed) {
+            long long live = 0;
+            for (int a = 0; a < count; ++a)
+                if (hd[a].active) live += res_count[a];
+            const bool compact = active > 0 && live < (long long)(0.7 * (double)res_tab.size());
+            if (compact) build_tables();
+            if ((st = upload(compact)) != FLD_OK) return st;
+        }
+    }
+    fld_status worst = FLD_OK;
+    for (int a = 0; a < count; ++a) {
+        if (hd[a].active) finish(a, FLD_ERR_NOT_CONVERGED, res[a].rel_residual);
+        fld_grid_s *g = grids[a];
+        g->valid_float = true;
+        g->valid_d = false;
+        res[a].omega = ppv[a].omega;
+        res[a].omega_backoffs = ctl[a].backoffs;
+        res[a].kernels = launches;
+        if (res[a].status == FLD_ERR_DIVERGED) worst = FLD_ERR_DIVERGED;
+        else if (res[a].status != FLD_OK && worst == FLD_OK) worst = FLD_ERR_NOT_CONVERGED;
+        if (results) results[a] = res[a];
+    }
+    FLD_CK(cudaStreamSynchronize(bs));
+    if (worst != FLD_OK) g_last_error = "not every solve of the batch converged (see the per-grid results)";
+    return worst;
+}
+
+fld_status fld_solve_batch(fld_grid *grids, int count, const fld_solve_params *p, fld_solve_result *results) {
+    if (!grids || count < 1) return fail(FLD_ERR_INVALID_ARG, "grids must hold count >= 1 handles");
+    for (int a = 0; a < count; ++a) {
+        if (!grids[a]) return fail(FLD_ERR_INVALID_ARG, "a grid handle is NULL");
+        for (int b = 0; b < a; ++b)
+            if (grids[a] == grids[b]) return fail(FLD_ERR_INVALID_ARG, "a grid appears twice in the batch");
+        if (grids[a]->device != grids[0]->device) return fail(FLD_ERR_INVALID_ARG, "grids live on different devices");
+    }
+    fld_status st = enter(grids[0]);
+    if (st != FLD_OK) return st;
+    if ((st = check_params(grids[0], p)) != FLD_OK) return st;
+    if (p->precision == FLD_PREC_FP64)
+        return fail(FLD_ERR_INVALID_ARG, "batched solves run the FP32 / MIXED sweeps; use fld_solve for FP64");
+    if (!(p->tol >= 0.0)) return fail(FLD_ERR_INVALID_ARG, "tol must be >= 0");
+    if (p->max_iters < 0 || p->check_every < 1) return fail(FLD_ERR_INVALID_ARG, "bad max_iters / check_every");
+    // Grids of one shared launch should keep their per-iteration working set
+    // (24 bytes per voxel: sigma', sigma_a', j, phi hi/lo, D) within L2: a
+    // group larger than L2 streams from HBM on every pass, while each grid
+    // alone would not.  Grids are taken in order of size and packed greedily
+    // into groups of at most 3/4 of the L2 capacity; groups run one after
+    // another, small grids share launches, large grids run alone.
+    int l2 = 0;
+    if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, grids[0]->device) != cudaSuccess || l2 <= 0) {
+        (void)cudaGetLastError();
+        l2 = 64 << 20;
+    }
+    const double budget = 0.75 * (double)l2;
+    std::vector<int> order(count);
+    for (int a = 0; a < count; ++a) order[a] = a;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return nvox(grids[x]) < nvox(grids[y]); });
+    std::vector<fld_solve_result> res(count);
+    fld_status worst = FLD_OK;
+    const auto t0 = std::chrono::steady_clock::now();
+    size_t a = 0;
+    while (a < order.size()) {
+        std::vector<fld_grid> group;
+        std::vector<int> idx;
+        double ws = 0.0;
+        while (a < order.size()) {
+            const double w = 24.0 * (double)nvox(grids[order[a]]);
+            if (!group.empty() && ws + w > budget) break;
+            group.push_back(grids[order[a]]);
+            idx.push_back(order[a]);
+            ws += w;
+            ++a;
+        }
+        std::vector<fld_solve_result> gr(group.size());
+        const double off = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        st = solve_group(group.data(), (int)group.size(), p, gr.data(), off);
+        if (st != FLD_OK && st != FLD_ERR_NOT_CONVERGED && st != FLD_ERR_DIVERGED) return st;
+        for (size_t b = 0; b < group.size(); ++b) res[idx[b]] = gr[b];
+        if (st == FLD_ERR_DIVERGED) worst = FLD_ERR_DIVERGED;
+        else if (st == FLD_ERR_NOT_CONVERGED && worst == FLD_OK) worst = FLD_ERR_NOT_CONVERGED;
+    }
+    if (results)
+        for (int b = 0; b < count; ++b) results[b] = res[b];
+    if (worst != FLD_OK) g_last_error = "not every solve of the batch converged (see the per-grid results)";
+    return worst;
 }
 
 }  // extern "C"

@@ -82,6 +82,31 @@ cudaError_t launch_bake_march(const Layout &L, const Fields &f, float h, const d
 cudaError_t launch_validate(long long n, const Fields &f, const float *sigma_t, const float *albedo,
                             const float *j, cudaStream_t s);
 
+// One grid of a batched solve, read by the batched residual kernels at run
+// time (so grids can converge or change phase between checks).
+struct alignas(16) BatchDesc {
+    Layout L;
+    float *sp, *ah2, *jh2, *phi, *phlo, *D, *Df;
+    float omega, inv2h, floor_, larsen_n;
+    int lim, rounds;
+    int mode;            // 0: single-precision sweeps, 1: float-float correction sweeps
+    int active;          // 0: converged / stopped, its CTAs return at once
+    int pass_first, pass_bx, pass_by;   // (unused by the residual) pass grid dims
+    int res_first, res_bx, res_by;      // same for the residual table
+    int res_slot;                       // first partial-sum slot of this grid
+    int pad_[3];
+};
+static_assert(sizeof(BatchDesc) % 16 == 0, "BatchDesc is read with 16-byte loads");
+
+// Batched residual: per grid g, result[2g] = sum (R h^2)^2, result[2g+1] = sum (j h^2)^2,
+// summed in the same order as launch_residual.
+cudaError_t launch_residual_batch(const BatchDesc *descs, const int *cta_grid, int nctas, int ngrids,
+                                  const int *res_count, double *partials, double *result, int lim, int margin,
+                                  cudaStream_t s);
+// Pass / residual grid dimensions of a layout (CTAs = x * y * nz).
+void pass_dims(const Layout &L, int *bx, int *by);
+void residual_dims(const Layout &L, int *bx, int *by);
+
 // Sets the thread-local text that fld_last_error() returns.
 void set_error_text(const char *msg);
 

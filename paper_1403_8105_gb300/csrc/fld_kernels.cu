@@ -295,22 +295,19 @@ __device__ __forceinline__ float ff_den(const FFTerms &t, float ah, float Dp) {
     return __fadd_rn(__fadd_rn(ah, 3.0f * Dp), 0.5f * t.C);
 }
 
-// Plain single-precision pass (the bulk sweeps).  LIM < 0 and ROUNDS = 0
-// select the limiter and the number of local rounds at run time; the common
-// cases are compiled with both fixed.
+// Plain single-precision pass (the bulk sweeps), for the cell of thread
+// (t, J, K).  LIM < 0 and ROUNDS = 0 select the limiter and the number of
+// local rounds at run time; the common cases are compiled with both fixed.
 template <int LIM, int ROUNDS>
-__global__ void __launch_bounds__(256) k_pass_f32(Layout L, const float *__restrict__ sp,
-                                                  const float *__restrict__ ah2, const float *__restrict__ jh2,
-                                                  float *__restrict__ phi, float *__restrict__ D, int colour,
-                                                  int lim_rt, float larsen_n, float omega, float inv2h, float floor_,
-                                                  int rounds_rt) {
+__device__ __forceinline__ void pass_f32_body(const Layout &L, const float *__restrict__ sp,
+                                              const float *__restrict__ ah2, const float *__restrict__ jh2,
+                                              float *__restrict__ phi, float *__restrict__ D, int colour, int t,
+                                              int J, int K, int lim_rt, float larsen_n, float omega, float inv2h,
+                                              float floor_, int rounds_rt) {
     const int lim = LIM >= 0 ? LIM : lim_rt;
     const int local_iters = ROUNDS > 0 ? ROUNDS : rounds_rt;
     Nbrs o;
-    if (!pass_cell(L, colour, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y + 1,
-                   blockIdx.z + 1, o) ||
-        blockIdx.y * blockDim.y + threadIdx.y >= L.ny)
-        return;
+    if (J > L.ny || !pass_cell(L, colour, t, J, K, o)) return;
     const float p0 = phi[o.own];
     float ps[6], Ds[6];
 #pragma unroll
@@ -346,22 +343,31 @@ __global__ void __launch_bounds__(256) k_pass_f32(Layout L, const float *__restr
     D[o.own] = Dp;
 }
 
+template <int LIM, int ROUNDS>
+__global__ void __launch_bounds__(256) k_pass_f32(Layout L, const float *__restrict__ sp,
+                                                  const float *__restrict__ ah2, const float *__restrict__ jh2,
+                                                  float *__restrict__ phi, float *__restrict__ D, int colour,
+                                                  int lim_rt, float larsen_n, float omega, float inv2h, float floor_,
+                                                  int rounds_rt) {
+    pass_f32_body<LIM, ROUNDS>(L, sp, ah2, jh2, phi, D, colour, blockIdx.x * blockDim.x + threadIdx.x,
+                               blockIdx.y * blockDim.y + threadIdx.y + 1, blockIdx.z + 1, lim_rt, larsen_n, omega,
+                               inv2h, floor_, rounds_rt);
+}
+
 // Float-float correction pass: phi kept as a hi/lo pair, S summed so the
 // update is accurate to the pair's precision; correctly rounded D (the same
 // function the residual kernel evaluates).
 template <int LIM, int ROUNDS>
-__global__ void __launch_bounds__(256) k_pass_ff(Layout L, const float *__restrict__ sp,
-                                                 const float *__restrict__ ah2, const float *__restrict__ jh2,
-                                                 float *__restrict__ phi, float *__restrict__ phlo,
-                                                 float *__restrict__ D, int colour, int lim_rt, float larsen_n,
-                                                 float omega, float inv2h, float floor_, int rounds_rt) {
+__device__ __forceinline__ void pass_ff_body(const Layout &L, const float *__restrict__ sp,
+                                             const float *__restrict__ ah2, const float *__restrict__ jh2,
+                                             float *__restrict__ phi, float *__restrict__ phlo,
+                                             float *__restrict__ D, int colour, int t, int J, int K, int lim_rt,
+                                             float larsen_n, float omega, float inv2h, float floor_,
+                                             int rounds_rt) {
     const int lim = LIM >= 0 ? LIM : lim_rt;
     const int local_iters = ROUNDS > 0 ? ROUNDS : rounds_rt;
     Nbrs o;
-    if (!pass_cell(L, colour, blockIdx.x * blockDim.x + threadIdx.x, blockIdx.y * blockDim.y + threadIdx.y + 1,
-                   blockIdx.z + 1, o) ||
-        blockIdx.y * blockDim.y + threadIdx.y >= L.ny)
-        return;
+    if (J > L.ny || !pass_cell(L, colour, t, J, K, o)) return;
     const float p0 = phi[o.own], p0lo = phlo[o.own];
     float ps[6], ls[6], Ds[6];
 #pragma unroll
@@ -386,6 +392,28 @@ __global__ void __launch_bounds__(256) k_pass_ff(Layout L, const float *__restri
     phi[o.own] = nw.hi;
     phlo[o.own] = nw.lo;
     D[o.own] = Dp;
+}
+
+template <int LIM, int ROUNDS>
+__global__ void __launch_bounds__(256) k_pass_ff(Layout L, const float *__restrict__ sp,
+                                                 const float *__restrict__ ah2, const float *__restrict__ jh2,
+                                                 float *__restrict__ phi, float *__restrict__ phlo,
+                                                 float *__restrict__ D, int colour, int lim_rt, float larsen_n,
+                                                 float omega, float inv2h, float floor_, int rounds_rt) {
+    pass_ff_body<LIM, ROUNDS>(L, sp, ah2, jh2, phi, phlo, D, colour, blockIdx.x * blockDim.x + threadIdx.x,
+                              blockIdx.y * blockDim.y + threadIdx.y + 1, blockIdx.z + 1, lim_rt, larsen_n, omega,
+                              inv2h, floor_, rounds_rt);
+}
+
+// Descriptor of a batched grid, read by every thread with uniform 16-byte
+// loads (one transaction per warp, no shared-memory staging or barrier).
+__device__ __forceinline__ BatchDesc load_desc(const BatchDesc *__restrict__ p) {
+    BatchDesc d;
+    const int4 *src = reinterpret_cast<const int4 *>(p);
+    int4 *dst = reinterpret_cast<int4 *>(&d);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(BatchDesc) / 16); ++i) dst[i] = __ldg(src + i);
+    return d;
 }
 
 __global__ void __launch_bounds__(256) k_pass_d(Layout L, const double *__restrict__ sp,
@@ -430,12 +458,10 @@ __global__ void __launch_bounds__(256) k_pass_d(Layout L, const double *__restri
 // ---------------------------------------------------------------------------
 // Residual (Eq. 37) with D recomputed from the current phi.
 // ---------------------------------------------------------------------------
-__global__ void k_fresh_D_f(Layout L, const float *__restrict__ sp, const float *__restrict__ phi,
-                            const float *__restrict__ phlo, float *__restrict__ Df, int lim, float larsen_n,
-                            float inv2h, float floor_) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
+__device__ __forceinline__ void fresh_D_f_body(const Layout &L, const float *__restrict__ sp,
+                                               const float *__restrict__ phi, const float *__restrict__ phlo,
+                                               float *__restrict__ Df, int lim, float larsen_n, float inv2h,
+                                               float floor_, int i, int j, int k) {
     if (i >= L.nx || j >= L.ny) return;
     const int q = L.at(i, j, k);
     const int xm = L.at(i - 1, j, k), xp = L.at(i + 1, j, k), ym = L.at(i, j - 1, k), yp = L.at(i, j + 1, k);
@@ -451,6 +477,13 @@ __global__ void k_fresh_D_f(Layout L, const float *__restrict__ sp, const float 
     Df[q] = knudsen_D_f(gx, gy, gz, inv2h, sp[q], phi[q], floor_, lim, larsen_n);
 }
 
+__global__ void k_fresh_D_f(Layout L, const float *__restrict__ sp, const float *__restrict__ phi,
+                            const float *__restrict__ phlo, float *__restrict__ Df, int lim, float larsen_n,
+                            float inv2h, float floor_) {
+    fresh_D_f_body(L, sp, phi, phlo, Df, lim, larsen_n, inv2h, floor_, blockIdx.x * blockDim.x + threadIdx.x,
+                   blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z);
+}
+
 __global__ void k_fresh_D_d(Layout L, const double *__restrict__ sp, const double *__restrict__ phi,
                             double *__restrict__ Df, int lim, double larsen_n, double inv2h, double floor_) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -464,40 +497,48 @@ __global__ void k_fresh_D_d(Layout L, const double *__restrict__ sp, const doubl
 }
 
 // Per-voxel residual R_p dl^2 = jh2 - ah2 phi_p + sum_s D_ps (phi_s - phi_p)
-// in float-float; squares and the source squares summed in double.
+// in float-float; its square (over the margin set) and the source square in
+// double.
+__device__ __forceinline__ void residual_f_terms(const Layout &L, const float *__restrict__ ah2,
+                                                 const float *__restrict__ jh2, const float *__restrict__ phi,
+                                                 const float *__restrict__ phlo, const float *__restrict__ Df,
+                                                 const float *__restrict__ Dghost, int margin, int i, int j, int k,
+                                                 double &r2, double &j2) {
+    r2 = 0.0;
+    j2 = 0.0;
+    if (i >= L.nx || j >= L.ny) return;
+    const int q = L.at(i, j, k);
+    const int nb[6] = {L.at(i - 1, j, k), L.at(i + 1, j, k), L.at(i, j - 1, k),
+                       L.at(i, j + 1, k), L.at(i, j, k - 1), L.at(i, j, k + 1)};
+    const bool onface[6] = {i == 0, i == L.nx - 1, j == 0, j == L.ny - 1, k == 0, k == L.nz - 1};
+    float ps[6], ls[6], Ds[6];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        ps[s] = phi[nb[s]];
+        ls[s] = phlo ? phlo[nb[s]] : 0.0f;
+        // ghost neighbours keep their Dirichlet D (never recomputed)
+        Ds[s] = onface[s] ? Dghost[nb[s]] : Df[nb[s]];
+    }
+    const float ah = ah2[q];
+    const FFTerms T = ff_terms(phi[q], phlo ? phlo[q] : 0.0f, ps, ls, Ds, ah, jh2[q]);
+    const ff S = ff_S(T, Df[q]);
+    const double Sd = ff_to_d(S);
+    const bool in = i >= margin && i < L.nx - margin && j >= margin && j < L.ny - margin && k >= margin &&
+                    k < L.nz - margin;
+    r2 = in ? Sd * Sd : 0.0;
+    const double jd = (double)jh2[q];
+    j2 = jd * jd;
+}
+
 __global__ void __launch_bounds__(256) k_residual_f(Layout L, const float *__restrict__ ah2,
                                                     const float *__restrict__ jh2, const float *__restrict__ phi,
                                                     const float *__restrict__ phlo, const float *__restrict__ Df,
                                                     const float *__restrict__ Dghost, int margin,
                                                     double *__restrict__ partials) {
     __shared__ double sh[32];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int j = blockIdx.y * blockDim.y + threadIdx.y;
-    const int k = blockIdx.z;
-    double r2 = 0.0, j2 = 0.0;
-    if (i < L.nx && j < L.ny) {
-        const int q = L.at(i, j, k);
-        const int nb[6] = {L.at(i - 1, j, k), L.at(i + 1, j, k), L.at(i, j - 1, k),
-                           L.at(i, j + 1, k), L.at(i, j, k - 1), L.at(i, j, k + 1)};
-        const bool onface[6] = {i == 0, i == L.nx - 1, j == 0, j == L.ny - 1, k == 0, k == L.nz - 1};
-        float ps[6], ls[6], Ds[6];
-#pragma unroll
-        for (int s = 0; s < 6; ++s) {
-            ps[s] = phi[nb[s]];
-            ls[s] = phlo ? phlo[nb[s]] : 0.0f;
-            // ghost neighbours keep their Dirichlet D (never recomputed)
-            Ds[s] = onface[s] ? Dghost[nb[s]] : Df[nb[s]];
-        }
-        const float ah = ah2[q];
-        const FFTerms T = ff_terms(phi[q], phlo ? phlo[q] : 0.0f, ps, ls, Ds, ah, jh2[q]);
-        const ff S = ff_S(T, Df[q]);
-        const double Sd = ff_to_d(S);
-        const bool in = i >= margin && i < L.nx - margin && j >= margin && j < L.ny - margin && k >= margin &&
-                        k < L.nz - margin;
-        r2 = in ? Sd * Sd : 0.0;
-        const double jd = (double)jh2[q];
-        j2 = jd * jd;
-    }
+    double r2, j2;
+    residual_f_terms(L, ah2, jh2, phi, phlo, Df, Dghost, margin, blockIdx.x * blockDim.x + threadIdx.x,
+                     blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z, r2, j2);
     r2 = block_sum(r2, sh);
     __syncthreads();
     j2 = block_sum(j2, sh);
@@ -505,6 +546,64 @@ __global__ void __launch_bounds__(256) k_residual_f(Layout L, const float *__res
         const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
         partials[2 * b] = r2;
         partials[2 * b + 1] = j2;
+    }
+}
+
+// Batched fresh D / residual / finalize: CTA b works on grid cta_grid[b] with
+// the same block decomposition as the solo launch, writes its partial sums to
+// the grid's own slots, and one block per grid sums them in the solo order.
+__global__ void __launch_bounds__(256) k_fresh_D_batch(const BatchDesc *__restrict__ descs,
+                                                       const int *__restrict__ cta_grid, int lim) {
+    const BatchDesc d = load_desc(descs + __ldg(cta_grid + blockIdx.x));
+    if (!d.active) return;
+    const int local = blockIdx.x - d.res_first;
+    const int bx = local % d.res_bx, rest = local / d.res_bx;
+    const int by = rest % d.res_by, bz = rest / d.res_by;
+    fresh_D_f_body(d.L, d.sp, d.phi, d.mode ? d.phlo : nullptr, d.Df, lim, d.larsen_n, d.inv2h, d.floor_,
+                   bx * blockDim.x + threadIdx.x, by * blockDim.y + threadIdx.y, bz);
+}
+
+__global__ void __launch_bounds__(256) k_residual_batch(const BatchDesc *__restrict__ descs,
+                                                        const int *__restrict__ cta_grid, int margin,
+                                                        double *__restrict__ partials) {
+    __shared__ double sh[32];
+    const BatchDesc d = load_desc(descs + __ldg(cta_grid + blockIdx.x));
+    if (!d.active) return;
+    const int local = blockIdx.x - d.res_first;
+    const int bx = local % d.res_bx, rest = local / d.res_bx;
+    const int by = rest % d.res_by, bz = rest / d.res_by;
+    double r2, j2;
+    residual_f_terms(d.L, d.ah2, d.jh2, d.phi, d.mode ? d.phlo : nullptr, d.Df, d.D, margin,
+                     bx * blockDim.x + threadIdx.x, by * blockDim.y + threadIdx.y, bz, r2, j2);
+    r2 = block_sum(r2, sh);
+    __syncthreads();
+    j2 = block_sum(j2, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) {
+        partials[2 * (d.res_slot + local)] = r2;
+        partials[2 * (d.res_slot + local) + 1] = j2;
+    }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_finalize_batch(const BatchDesc *__restrict__ descs,
+                                                                const int *__restrict__ res_count,
+                                                                const double *__restrict__ partials,
+                                                                double *__restrict__ result) {
+    __shared__ double sh[32];
+    const BatchDesc &d = descs[blockIdx.x];
+    if (!d.active) return;
+    const int n = res_count[blockIdx.x];
+    const double *p = partials + 2 * (long long)d.res_slot;
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        a += p[2 * i];
+        b += p[2 * i + 1];
+    }
+    a = block_sum(a, sh);
+    __syncthreads();
+    b = block_sum(b, sh);
+    if (threadIdx.x == 0) {
+        result[2 * blockIdx.x] = a;
+        result[2 * blockIdx.x + 1] = b;
     }
 }
 
@@ -793,6 +892,28 @@ cudaError_t launch_pass(Family fam, const Layout &L, const Fields &f, const Pass
                                     p.omega, p.inv2h, p.floor_, p.local_iters);
         break;
     }
+    return cudaGetLastError();
+}
+
+void pass_dims(const Layout &L, int *bx, int *by) {
+    const dim3 g = pass_grid(L, dim3(32, 8, 1));
+    *bx = (int)g.x;
+    *by = (int)g.y;
+}
+
+void residual_dims(const Layout &L, int *bx, int *by) {
+    const dim3 g = vox_grid(L);
+    *bx = (int)g.x;
+    *by = (int)g.y;
+}
+
+cudaError_t launch_residual_batch(const BatchDesc *descs, const int *cta_grid, int nctas, int ngrids,
+                                  const int *res_count, double *partials, double *result, int lim, int margin,
+                                  cudaStream_t s) {
+    if (nctas <= 0) return cudaSuccess;
+    k_fresh_D_batch<<<nctas, vox_block(), 0, s>>>(descs, cta_grid, lim);
+    k_residual_batch<<<nctas, vox_block(), 0, s>>>(descs, cta_grid, margin, partials);
+    k_finalize_batch<<<ngrids, kRedThreads, 0, s>>>(descs, res_count, partials, result);
     return cudaGetLastError();
 }
 
