@@ -62,11 +62,13 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample length")
     ap.add_argument("--no-extras", action="store_true", help="skip cpu baseline / 256^3 roofline / e2e")
-    ap.add_argument("--workload", choices=["cloud", "batch"], default="cloud",
+    ap.add_argument("--workload", choices=["cloud", "batch", "serve"], default="cloud",
                     help="cloud: the 128^3 solve (default); batch: independent solves of uneven size, "
                          "batched in shared launches vs one after another")
     ap.add_argument("--count", type=int, default=16, help="batch workload: number of solves")
     ap.add_argument("--sizes", default="32,48,64,96", help="batch workload: edge lengths drawn from")
+    ap.add_argument("--rate", type=float, default=30.0, help="serve workload: Poisson arrival rate (req/s)")
+    ap.add_argument("--requests", type=int, default=120, help="serve workload: number of requests")
     return ap.parse_args()
 
 
@@ -527,12 +529,119 @@ def run_batch(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """A Poisson stream of independent solves (edges U{24..64}, a 96^3 request
+    every 50th, per-request fBm medium, albedo U[0.8, 0.99], point or oblique
+    light, LP, rel. residual 1e-6) served with continuous batching, against
+    the same stream solved one request at a time (FIFO) and plain FP64 solves
+    one at a time."""
+    import numpy as np
+    import torch
+
+    import fld_inputs
+    import paper_1403_8105_gb300 as fld
+    from paper_1403_8105_gb300 import serve
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rng = np.random.default_rng(77)
+    arr = serve.poisson_arrivals(args.requests, args.rate, 77)
+    cache = {}
+
+    def medium(n, seed, albedo):
+        key = (n, seed % 6)
+        if key not in cache:
+            sig, _ = fld_inputs.cloud_medium(n, seed=key[1], albedo=0.9)
+            cache[key] = torch.from_numpy(sig).to(dev)
+        return cache[key], torch.full((n, n, n), albedo, dtype=torch.float32, device=dev)
+
+    def make_requests():
+        reqs = []
+        r2 = np.random.default_rng(78)
+        for i in range(args.requests):
+            n = 96 if (i + 1) % 50 == 0 else int(r2.integers(24, 65))
+            seed = int(r2.integers(0, 1 << 30))
+            albedo = float(r2.uniform(0.8, 0.99))
+            if r2.integers(0, 2):
+                light = fld_inputs.Light(kind="point", pos=(float(r2.uniform(0.1, 0.9)), float(r2.uniform(0.1, 0.9)),
+                                                             float(r2.uniform(1.05, 1.5))), power=2.0)
+            else:
+                light = fld_inputs.Light(kind="directional", dir=(float(r2.uniform(-0.3, 0.3)),
+                                                                  float(r2.uniform(-0.3, 0.3)), -1.0))
+            reqs.append(serve.Request(rid=i, arrival=float(arr[i]), n=n, medium=medium(n, seed, albedo), light=light,
+                                      footprint=serve.footprint_bytes(n)))
+        return reqs
+
+    p = fld.params(limiter="lp", precision="mixed", tol=args.tol, check_every=64, max_iters=args.max_iters)
+    stream = torch.cuda.Stream(device=dev)
+    # warm-up: one small solve
+    w = make_requests()[:2]
+    torch.cuda.synchronize()
+    be = serve.GpuBackend(p, stream=stream.cuda_stream)
+    serve.serve([serve.Request(rid=r.rid, arrival=0.0, n=r.n, medium=r.medium, light=r.light,
+                               footprint=r.footprint) for r in w], be)
+    be.close()
+
+    reqs = make_requests()
+    torch.cuda.synchronize()
+    be = serve.GpuBackend(p, stream=stream.cuda_stream)
+    try:
+        reqs, st = serve.serve(reqs, be, max_active=64)
+    finally:
+        be.close()
+    upd = sum(r.result.iterations * r.n ** 3 for r in reqs)
+    cont = dict(st, voxel_updates_per_s=upd / st["span_s"],
+                converged=sum(r.result.status == fld.FLD_OK for r in reqs))
+
+    def one_at_a_time(reqs, params, limit):
+        t0 = time.perf_counter()
+        lat, upd, n_done = [], 0, 0
+        for r in reqs[:limit]:
+            now = time.perf_counter() - t0
+            if now < r.arrival:
+                time.sleep(r.arrival - now)
+            g = fld.Grid(r.n, r.n, r.n, 1.0 / r.n, stream=stream.cuda_stream)
+            g.set_medium(*r.medium)
+            if r.light.kind == "point":
+                g.bake_point(r.light.pos, r.light.power)
+            else:
+                g.bake_directional(r.light.dir, r.light.radiance)
+            res = g.solve(params)
+            g.close()
+            lat.append(time.perf_counter() - t0 - r.arrival)
+            upd += res.iterations * r.n ** 3
+            n_done += 1
+        span = time.perf_counter() - t0 - reqs[0].arrival
+        return {"requests": n_done, "latency_s_p50": float(np.percentile(lat, 50)),
+                "latency_s_p99": float(np.percentile(lat, 99)), "throughput_req_s": n_done / span,
+                "voxel_updates_per_s": upd / span}
+
+    seq = one_at_a_time(make_requests(), p, args.requests)
+    p64 = fld.params(limiter="lp", precision="fp64", tol=args.tol, check_every=64, max_iters=args.max_iters)
+    seq64 = one_at_a_time(make_requests(), p64, min(12, args.requests))
+    offered = args.rate
+    line = {
+        "metric": METRIC, "value": cont["voxel_updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+        "ms_per_step": cont["span_s"] * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (float-float correction sweeps)", "data": "synthetic",
+        "config": {"workload": f"Poisson stream of {args.requests} FLD solves at {offered:g} req/s, edges U{{24..64}}, "
+                               f"every 50th 96^3, per-request fBm medium/albedo/light, LP, rel. residual {args.tol:g}",
+                   "admission": "free device memory >= footprint / 0.9 and < 64 solves in flight"},
+        "continuous_batching": cont, "one_at_a_time_mixed": seq, "one_at_a_time_fp64_first12": seq64,
+        "offered_req_s": offered,
+        "throughput_gain_vs_one_at_a_time": cont["throughput_req_s"] / seq["throughput_req_s"],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "serve":
+        run_serve(args)
     else:
         run_gpu(args)
 

@@ -196,13 +196,12 @@ fld_status fld_iterate(fld_grid g, const fld_solve_params *p, int iterations);
 fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r);
 
 /* Solve `count` independent grids together (not a paper item; the batched
- * form of fld_solve).  Grids are taken in order of size and packed into groups
- * whose per-iteration working set (24 bytes per voxel) fits in 3/4 of the
- * GPU's L2; groups run one after another.  Within a group every colour pass of
- * every still-active grid runs in one launch, blocks of p->check_every
- * iterations are replayed from one CUDA graph, the residuals of all grids are
- * reduced in one pass per check (per-grid slots), and grids leave the launch
- * as they converge.  Each grid follows
+ * form of fld_solve, built on the server below).  Grids are taken in order of
+ * size and packed into groups whose per-iteration working set (24 bytes per
+ * voxel) fits in 3/4 of the GPU's L2; groups run one after another.  Within a
+ * group all grids step together: their iteration blocks run concurrently and
+ * their residuals are reduced in one batched pass per check; grids leave as
+ * they converge.  Each grid follows
  * exactly the decisions fld_solve would take for it alone (same omega, check
  * schedule, precision switch and safeguard), so its result equals its solo
  * solve.  Precision FP32 or MIXED (FP64: FLD_ERR_INVALID_ARG).  All grids must
@@ -213,6 +212,44 @@ fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r)
  * batch.  Returns FLD_OK if every grid converged, else FLD_ERR_DIVERGED if one
  * diverged, else FLD_ERR_NOT_CONVERGED. */
 fld_status fld_solve_batch(fld_grid *grids, int count, const fld_solve_params *p, fld_solve_result *results);
+
+/* ---------------------------------------------------------------------------
+ * Server: continuous batching of independent solves (not a paper item).
+ * A server holds a changing set of grids being solved with one set of
+ * parameters (FP32 or MIXED).  fld_server_add admits a grid (medium and
+ * source already set): it is initialised, its first residual evaluated, and it
+ * joins the next step.  Each fld_server_step runs one block of p->check_every
+ * iterations for every active grid -- each grid replays its own block graph
+ * on a stream of a pool of 16, so grids run concurrently -- then evaluates the
+ * residuals of all active grids in one batched reduction and applies each
+ * grid's own decisions (tolerance, precision switch, safeguard), exactly as
+ * fld_solve would for that grid alone; finished grids leave the set and are
+ * reported (tag + fld_solve_result, `ms` = time from admission to finish).
+ * While in the server a grid's work is ordered on the server's stream; it
+ * returns to its own stream when it finishes.  A grid must not be used
+ * elsewhere while it is in a server.
+ * ------------------------------------------------------------------------- */
+typedef struct fld_server_s *fld_server;
+
+/* Create a server for the given parameters (copied).  stream: cudaStream_t
+ * or NULL (the server creates one). */
+fld_status fld_server_create(const fld_solve_params *p, void *stream, fld_server *out);
+
+/* Admit grid g under a caller-chosen tag.  Synchronises g's stream. */
+fld_status fld_server_add(fld_server s, fld_grid g, long long tag);
+
+/* One step (see above).  Up to `capacity` finished grids are reported in
+ * tags[] / results[] and counted in *nfinished; more are kept for the next
+ * call.  With no active grid, only pending reports are returned. */
+fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *results, int capacity,
+                           int *nfinished);
+
+/* Number of grids still iterating. */
+fld_status fld_server_active(fld_server s, int *count);
+
+/* Destroy the server (grids still inside return to their own streams, their
+ * state as left by the last step). */
+void fld_server_destroy(fld_server s);
 
 /* Relative residual Rbar/jbar of the current phi (Eq. 37 with D recomputed
  * from phi, RMS over the unknowns beyond p->residual_margin), evaluated in

@@ -27,7 +27,8 @@ __all__ = [
     "load", "library_path", "fld_default_params", "fld_create_grid", "fld_set_medium", "fld_set_source",
     "fld_get_source", "fld_bake_directional", "fld_bake_point", "fld_set_state", "fld_get_state",
     "fld_iterate", "fld_solve", "fld_solve_batch", "fld_residual", "fld_residual_noalloc", "fld_destroy",
-    "fld_status_string",
+    "fld_server_create", "fld_server_add", "fld_server_step", "fld_server_active", "fld_server_destroy",
+    "Server", "fld_status_string",
     "fld_last_error", "Grid", "params",
 ]
 
@@ -110,6 +111,12 @@ def load(build_if_missing: bool = True):
             "fld_iterate": (c_int, [_vp, P, c_int]),
             "fld_solve": (c_int, [_vp, P, R]),
             "fld_solve_batch": (c_int, [ctypes.POINTER(_vp), c_int, P, R]),
+            "fld_server_create": (c_int, [P, _vp, ctypes.POINTER(_vp)]),
+            "fld_server_add": (c_int, [_vp, _vp, ctypes.c_longlong]),
+            "fld_server_step": (c_int, [_vp, ctypes.POINTER(ctypes.c_longlong), R, c_int,
+                                        ctypes.POINTER(c_int)]),
+            "fld_server_active": (c_int, [_vp, ctypes.POINTER(c_int)]),
+            "fld_server_destroy": (None, [_vp]),
             "fld_residual": (c_int, [_vp, P, ctypes.POINTER(c_double)]),
             "fld_residual_noalloc": (c_int, [c_int, c_int, c_int, c_double, P, _vp, _vp, _vp, _vp, _vp,
                                              ctypes.POINTER(c_double), _vp]),
@@ -246,6 +253,71 @@ def fld_solve_batch(grids, p: SolveParams, check: bool = True):
     if check:
         _check(st, "fld_solve_batch", allow=(FLD_OK, FLD_ERR_NOT_CONVERGED, FLD_ERR_DIVERGED))
     return st, list(out)
+
+
+def fld_server_create(p: SolveParams, stream=None):
+    out = _vp()
+    s = None if stream is None else _vp(int(stream))
+    _check(load().fld_server_create(ctypes.byref(p), s, ctypes.byref(out)), "fld_server_create")
+    return out
+
+
+def fld_server_add(s, g, tag: int) -> None:
+    _check(load().fld_server_add(s, g.handle if isinstance(g, Grid) else g, int(tag)), "fld_server_add")
+
+
+def fld_server_step(s, capacity: int = 256):
+    """One step; returns [(tag, SolveResult)] of the grids that finished."""
+    tags = (ctypes.c_longlong * max(1, capacity))()
+    res = (SolveResult * max(1, capacity))()
+    n = ctypes.c_int(0)
+    _check(load().fld_server_step(s, tags, res, int(capacity), ctypes.byref(n)), "fld_server_step")
+    return [(int(tags[i]), res[i]) for i in range(n.value)]
+
+
+def fld_server_active(s) -> int:
+    n = ctypes.c_int(0)
+    _check(load().fld_server_active(s, ctypes.byref(n)), "fld_server_active")
+    return n.value
+
+
+def fld_server_destroy(s) -> None:
+    if s:
+        load().fld_server_destroy(s)
+
+
+class Server:
+    """Owning wrapper of an fld_server handle."""
+
+    def __init__(self, p: SolveParams, stream=None):
+        self.handle = fld_server_create(p, stream)
+
+    def add(self, grid, tag: int):
+        fld_server_add(self.handle, grid, tag)
+
+    def step(self, capacity: int = 256):
+        return fld_server_step(self.handle, capacity)
+
+    @property
+    def active(self) -> int:
+        return fld_server_active(self.handle)
+
+    def close(self):
+        if self.handle:
+            fld_server_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def fld_residual(g, p: SolveParams) -> float:

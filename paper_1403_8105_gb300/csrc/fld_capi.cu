@@ -844,326 +844,330 @@ fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r)
 }
 
 
-// Solve one group of grids in shared launches (see fld_solve_batch).
-static fld_status solve_group(fld_grid *grids, int count, const fld_solve_params *p, fld_solve_result *results,
-                              double t_offset_ms) {
-    fld_status st = FLD_OK;
-    // Prepare and initialise every grid on its own stream first.
-    std::vector<Family> fam(count, FAM_F32);
-    for (int a = 0; a < count; ++a) {
-        fld_grid_s *g = grids[a];
-        FLD_CK(cudaStreamSynchronize(g->stream));
-        if ((st = prepare(g, p, FAM_F32)) != FLD_OK) return st;
-        if (!p->warm_start) {
-            if ((st = init_state(g, p, FAM_F32)) != FLD_OK) return st;
-        } else if (p->precision == FLD_PREC_MIXED && !g->valid_d && g->lo_live) {
-            fam[a] = FAM_FF;
-        }
-        if ((st = sync_family(g, fam[a])) != FLD_OK) return st;
-        FLD_CK(cudaStreamSynchronize(g->stream));
-    }
-    // From here on all work of the batch is ordered on the first grid's stream.
-    cudaStream_t bs = grids[0]->stream;
-    std::vector<cudaStream_t> own(count);
-    for (int a = 0; a < count; ++a) {
-        own[a] = grids[a]->stream;
-        grids[a]->stream = bs;
-    }
-    struct Restore {
-        fld_grid *g;
-        std::vector<cudaStream_t> *s;
-        ~Restore() {
-            for (size_t a = 0; a < s->size(); ++a) g[a]->stream = (*s)[a];
-        }
-    } restore{grids, &own};
+// ===========================================================================
+// Server: grids join and leave a running set of solves (continuous batching).
+// Each step runs one block of check_every iterations for every active grid --
+// each grid replays its own block graph (the one fld_solve uses) on a stream
+// of a small pool, so independent grids run concurrently -- then reduces the
+// residuals of all active grids in one batched pass and applies each grid's
+// own decisions.  A grid therefore takes exactly the path of its solo solve.
+// ===========================================================================
+struct ServerEntry {
+    fld_grid_s *g = nullptr;
+    long long tag = 0;
+    cudaStream_t own_stream = nullptr;
+    Controller ctl;
+    Family fam = FAM_F32;
+    PassParams pp{};
+    Family snap_fam = FAM_F32;
+    bool snap_lo = false;
+    fld_solve_result res{};
+    std::chrono::steady_clock::time_point t_add;
+};
 
-    const double sw = p->fp32_switch > 0.0 ? p->fp32_switch : 2e-5;
-    std::vector<BatchDesc> hd(count);
-    std::vector<int> res_count(count);
-    int total_res = 0;
-    const int rounds = p->local_iters < 1 ? 1 : p->local_iters;
-    for (int a = 0; a < count; ++a) {
-        fld_grid_s *g = grids[a];
-        const PassParams pp = pass_params(g, p);
-        BatchDesc &d = hd[a];
-        d.L = g->L;
-        d.sp = g->f.sp; d.ah2 = g->f.ah2; d.jh2 = g->f.jh2; d.phi = g->f.phi; d.phlo = g->f.phlo;
-        d.D = g->f.D; d.Df = g->f.Df;
-        d.omega = (float)pp.omega; d.inv2h = (float)pp.inv2h; d.floor_ = (float)pp.floor_;
-        d.larsen_n = (float)pp.larsen_n; d.lim = pp.lim; d.rounds = rounds;
-        d.mode = fam[a] == FAM_FF ? 1 : 0;
-        d.active = 1;
-        pass_dims(g->L, &d.pass_bx, &d.pass_by);
-        residual_dims(g->L, &d.res_bx, &d.res_by);
-        res_count[a] = d.res_bx * d.res_by * g->nz;
-        d.res_slot = total_res;
-        total_res += res_count[a];
-    }
-    // CTA table of the batched residual (rebuilt over the active grids as
-    // grids finish).
-    std::vector<int> res_tab;
-    auto build_tables = [&]() {
-        res_tab.clear();
-        for (int a = 0; a < count; ++a) {
-            if (!hd[a].active) continue;
-            hd[a].res_first = (int)res_tab.size();
-            res_tab.insert(res_tab.end(), (size_t)res_count[a], a);
-        }
-    };
-    build_tables();
-
-    // Device workspace of this call.
+struct fld_server_s {
+    int device = 0;
+    cudaStream_t bs = nullptr;
+    bool own_bs = false;
+    fld_solve_params p{};
+    double sw = 2e-5;
+    std::vector<ServerEntry> active;
+    std::vector<ServerEntry> done;      // finished, not yet reported
     BatchDesc *d_desc = nullptr;
     int *d_res = nullptr, *d_count = nullptr;
     double *d_part = nullptr, *d_out = nullptr;
-    struct Free {
-        void *p[5];
-        ~Free() {
-            for (void *q : p)
-                if (q) cudaFree(q);
-        }
-    } fr{{nullptr, nullptr, nullptr, nullptr, nullptr}};
-    if (cudaMalloc((void **)&d_desc, sizeof(BatchDesc) * count) != cudaSuccess ||
-        cudaMalloc((void **)&d_res, sizeof(int) * (size_t)total_res) != cudaSuccess ||
-        cudaMalloc((void **)&d_count, sizeof(int) * count) != cudaSuccess ||
-        cudaMalloc((void **)&d_part, sizeof(double) * 2 * (size_t)total_res) != cudaSuccess ||
-        cudaMalloc((void **)&d_out, sizeof(double) * 2 * count) != cudaSuccess) {
+    int cap_grids = 0, cap_res = 0;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> join;
+    cudaEvent_t fork = nullptr;
+    long long launches = 0;
+};
+
+namespace {
+
+void server_free_workspace(fld_server_s *s) {
+    void *ptrs[] = {s->d_desc, s->d_res, s->d_count, s->d_part, s->d_out};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    s->d_desc = nullptr; s->d_res = nullptr; s->d_count = nullptr; s->d_part = nullptr; s->d_out = nullptr;
+    s->cap_grids = s->cap_res = 0;
+}
+
+fld_status server_workspace(fld_server_s *s, int grids, int res) {
+    if (grids <= s->cap_grids && res <= s->cap_res) return FLD_OK;
+    FLD_CK(cudaStreamSynchronize(s->bs));
+    server_free_workspace(s);
+    const int cg = grids + grids / 2 + 4, cr = res + res / 2 + 64;
+    if (cudaMalloc((void **)&s->d_desc, sizeof(BatchDesc) * cg) != cudaSuccess ||
+        cudaMalloc((void **)&s->d_res, sizeof(int) * (size_t)cr) != cudaSuccess ||
+        cudaMalloc((void **)&s->d_count, sizeof(int) * cg) != cudaSuccess ||
+        cudaMalloc((void **)&s->d_part, sizeof(double) * 2 * (size_t)cr) != cudaSuccess ||
+        cudaMalloc((void **)&s->d_out, sizeof(double) * 2 * cg) != cudaSuccess) {
         (void)cudaGetLastError();
-        fr.p[0] = d_desc; fr.p[1] = d_res; fr.p[2] = d_count; fr.p[3] = d_part; fr.p[4] = d_out;
+        server_free_workspace(s);
         return fail(FLD_ERR_OOM, "cudaMalloc of the batch workspace failed");
     }
-    fr.p[0] = d_desc; fr.p[1] = d_res; fr.p[2] = d_count; fr.p[3] = d_part; fr.p[4] = d_out;
-    FLD_CK(cudaMemcpyAsync(d_count, res_count.data(), sizeof(int) * count, cudaMemcpyHostToDevice, bs));
-    auto upload = [&](bool tables) -> fld_status {
-        FLD_CK(cudaMemcpyAsync(d_desc, hd.data(), sizeof(BatchDesc) * count, cudaMemcpyHostToDevice, bs));
-        if (tables) {
-            if (!res_tab.empty())
-                FLD_CK(cudaMemcpyAsync(d_res, res_tab.data(), sizeof(int) * res_tab.size(), cudaMemcpyHostToDevice, bs));
-        }
-        return FLD_OK;
-    };
-    if ((st = upload(true)) != FLD_OK) return st;
+    s->cap_grids = cg;
+    s->cap_res = cr;
+    return FLD_OK;
+}
 
-    std::vector<fld_solve_result> res(count);
-    std::vector<Controller> ctl(count);
-    std::vector<PassParams> ppv(count);
-    for (int a = 0; a < count; ++a) ppv[a] = pass_params(grids[a], p);
-    std::vector<Family> snap_fam(count);
-    std::vector<bool> snap_lo(count);
-    std::vector<double> host_out(2 * count);
-    long long launches = 0;
-    for (int a = 0; a < count; ++a) {
-        memset(&res[a], 0, sizeof(fld_solve_result));
-        res[a].status = FLD_ERR_NOT_CONVERGED;
-        res[a].jbar = grids[a]->jbar;
-        res[a].omega = hd[a].omega;
-        ctl[a].precision = p->precision;
-        ctl[a].tol = p->tol;
-        ctl[a].sw = sw;
-        ctl[a].fam = fam[a];
-    }
-    const auto t0 = std::chrono::steady_clock::now();
-    auto elapsed_ms = [&]() {
-        return t_offset_ms + std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    };
-    auto residuals = [&]() -> fld_status {
-        FLD_CK(launch_residual_batch(d_desc, d_res, (int)res_tab.size(), count, d_count, d_part, d_out, p->limiter,
-                                     p->residual_margin, bs));
-        launches += 3;
-        FLD_CK(cudaMemcpyAsync(host_out.data(), d_out, sizeof(double) * 2 * count, cudaMemcpyDeviceToHost, bs));
-        FLD_CK(cudaStreamSynchronize(bs));
-        return FLD_OK;
-    };
-    auto rel_of = [&](int a) {
-        fld_grid_s *g = grids[a];
-        const int m = p->residual_margin;
-        const long long ex = g->nx - 2LL * m, ey = g->ny - 2LL * m, ez = g->nz - 2LL * m;
-        const long long cnt = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
-        const double rb = cnt > 0 ? sqrt(host_out[2 * a] / (double)cnt) : 0.0;
-        const double jb = sqrt(host_out[2 * a + 1] / (double)nvox(g));
-        return jb > 0.0 ? rb / jb : rb / (g->h * g->h);
-    };
-    auto finish = [&](int a, fld_status s2, double rel) {
-        hd[a].active = 0;
-        res[a].status = s2;
-        res[a].rel_residual = rel;
-        res[a].ms = elapsed_ms();
-    };
-    // first check
-    if ((st = residuals()) != FLD_OK) return st;
-    int active = 0;
-    for (int a = 0; a < count; ++a) {
-        const double rel = rel_of(a);
-        res[a].rel_residual = rel;
-        ++res[a].checks;
-        const Action act = ctl[a].first(rel);
-        if (act == ACT_CONVERGED) finish(a, FLD_OK, rel);
-        else if (act == ACT_DIVERGED) finish(a, FLD_ERR_DIVERGED, rel);
-        else {
-            if ((st = snapshot(grids[a], fam[a], true)) != FLD_OK) return st;
-            snap_fam[a] = fam[a];
-            snap_lo[a] = grids[a]->lo_live;
-            ++active;
-        }
-    }
-    if ((st = upload(false)) != FLD_OK) return st;
+double rel_from_sums(const fld_grid_s *g, int margin, double r2, double j2) {
+    const long long ex = g->nx - 2LL * margin, ey = g->ny - 2LL * margin, ez = g->nz - 2LL * margin;
+    const long long cnt = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
+    const double rb = cnt > 0 ? sqrt(r2 / (double)cnt) : 0.0;
+    const double jb = sqrt(j2 / (double)nvox(g));
+    return jb > 0.0 ? rb / jb : rb / (g->h * g->h);
+}
 
-    // The sweeps of the active grids are one CUDA graph: each grid's chain of
-    // solo pass kernels is captured on one stream of a small pool, forked from
-    // and joined back to the batch stream, so independent grids run
-    // concurrently and each runs exactly the kernels of its solo solve.  The
-    // graph covers up to kGraphIters iterations and is replayed per check; it
-    // is captured again when the active set, a grid's precision or its omega
-    // changes.
-    constexpr int kGraphIters = 64;
-    const int nside = count < 16 ? count : 16;
-    std::vector<cudaStream_t> side(nside, nullptr);
-    std::vector<cudaEvent_t> join(nside, nullptr);
-    cudaEvent_t fork = nullptr;
-    struct SideFree {
-        std::vector<cudaStream_t> *s;
-        std::vector<cudaEvent_t> *j;
-        cudaEvent_t *f;
-        ~SideFree() {
-            for (auto x : *s)
-                if (x) cudaStreamDestroy(x);
-            for (auto x : *j)
-                if (x) cudaEventDestroy(x);
-            if (*f) cudaEventDestroy(*f);
-        }
-    } sf{&side, &join, &fork};
-    FLD_CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
-    for (int i = 0; i < nside; ++i) {
-        FLD_CK(cudaStreamCreateWithFlags(&side[i], cudaStreamNonBlocking));
-        FLD_CK(cudaEventCreateWithFlags(&join[i], cudaEventDisableTiming));
+void server_retire(fld_server_s *s, size_t i, fld_status st, double rel) {
+    ServerEntry &e = s->active[i];
+    e.res.status = st;
+    e.res.rel_residual = rel;
+    e.res.omega = e.pp.omega;
+    e.res.omega_backoffs = e.ctl.backoffs;
+    e.res.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - e.t_add).count();
+    e.g->valid_float = true;
+    e.g->valid_d = false;
+    e.g->stream = e.own_stream;
+    s->done.push_back(e);
+    s->active.erase(s->active.begin() + (long)i);
+}
+
+}  // namespace
+
+fld_status fld_server_create(const fld_solve_params *p, void *stream, fld_server *out) {
+    if (!out) return fail(FLD_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (!p) return fail(FLD_ERR_INVALID_ARG, "params is NULL");
+    if (p->precision != FLD_PREC_FP32 && p->precision != FLD_PREC_MIXED)
+        return fail(FLD_ERR_INVALID_ARG, "the server runs the FP32 / MIXED sweeps; use fld_solve for FP64");
+    if (p->limiter < FLD_LIM_CDA || p->limiter > FLD_LIM_LP) return fail(FLD_ERR_INVALID_ARG, "unknown limiter");
+    if (p->limiter == FLD_LIM_LARSEN && !(p->larsen_n > 0.0)) return fail(FLD_ERR_INVALID_ARG, "larsen_n must be > 0");
+    if (p->omega > 0.0 && !(p->omega < 2.0)) return fail(FLD_ERR_INVALID_ARG, "omega must lie in (0, 2)");
+    if (p->local_iters > 64 || p->residual_margin < 0) return fail(FLD_ERR_INVALID_ARG, "bad local_iters / margin");
+    if (!(p->tol >= 0.0) || p->max_iters < 0 || p->check_every < 1)
+        return fail(FLD_ERR_INVALID_ARG, "bad tol / max_iters / check_every");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
+        (void)cudaGetLastError();
+        return fail(FLD_ERR_NO_DEVICE, "no CUDA device available");
     }
-    cudaGraphExec_t exec = nullptr;
-    int graph_k = -1;
-    bool dirty = true;
-    struct GraphFree {
-        cudaGraphExec_t *e;
-        ~GraphFree() {
-            if (*e) cudaGraphExecDestroy(*e);
+    fld_server_s *s = new (std::nothrow) fld_server_s();
+    if (!s) return fail(FLD_ERR_OOM, "host allocation failed");
+    s->p = *p;
+    s->sw = p->fp32_switch > 0.0 ? p->fp32_switch : 2e-5;
+    cudaError_t e = cudaGetDevice(&s->device);
+    if (e == cudaSuccess) {
+        if (stream) {
+            s->bs = (cudaStream_t)stream;
+        } else {
+            e = cudaStreamCreate(&s->bs);
+            s->own_bs = e == cudaSuccess;
         }
-    } gf{&exec};
-    auto capture = [&](int kg) -> fld_status {
-        if (exec) {
-            cudaGraphExecDestroy(exec);
-            exec = nullptr;
+    }
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->fork, cudaEventDisableTiming);
+    const int nside = 16;
+    for (int i = 0; i < nside && e == cudaSuccess; ++i) {
+        cudaStream_t ss = nullptr;
+        cudaEvent_t ev = nullptr;
+        e = cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (ss) s->side.push_back(ss);
+        if (ev) s->join.push_back(ev);
+    }
+    if (e != cudaSuccess) {
+        fld_server_destroy(s);
+        return cuda_fail(e, "server setup");
+    }
+    *out = s;
+    return FLD_OK;
+}
+
+void fld_server_destroy(fld_server s) {
+    if (!s) return;
+    cudaSetDevice(s->device);
+    if (s->bs) cudaStreamSynchronize(s->bs);
+    for (ServerEntry &e : s->active) e.g->stream = e.own_stream;   // grids go back to their owners
+    server_free_workspace(s);
+    for (auto x : s->side) cudaStreamDestroy(x);
+    for (auto x : s->join) cudaEventDestroy(x);
+    if (s->fork) cudaEventDestroy(s->fork);
+    if (s->own_bs && s->bs) cudaStreamDestroy(s->bs);
+    delete s;
+}
+
+fld_status fld_server_add(fld_server s, fld_grid g, long long tag) {
+    if (!s || !g) return fail(FLD_ERR_INVALID_ARG, "server or grid is NULL");
+    if (g->device != s->device) return fail(FLD_ERR_INVALID_ARG, "the grid lives on another device");
+    for (const ServerEntry &e : s->active)
+        if (e.g == g) return fail(FLD_ERR_INVALID_ARG, "the grid is already being solved");
+    fld_status st = enter(g);
+    if (st != FLD_OK) return st;
+    const fld_solve_params *p = &s->p;
+    ServerEntry e;
+    e.g = g;
+    e.tag = tag;
+    e.t_add = std::chrono::steady_clock::now();
+    FLD_CK(cudaStreamSynchronize(g->stream));
+    if ((st = prepare(g, p, FAM_F32)) != FLD_OK) return st;
+    if (!p->warm_start) {
+        if ((st = init_state(g, p, FAM_F32)) != FLD_OK) return st;
+    } else if (p->precision == FLD_PREC_MIXED && !g->valid_d && g->lo_live) {
+        e.fam = FAM_FF;
+    }
+    if ((st = sync_family(g, e.fam)) != FLD_OK) return st;
+    e.pp = pass_params(g, p);
+    e.ctl.precision = p->precision;
+    e.ctl.tol = p->tol;
+    e.ctl.sw = s->sw;
+    e.ctl.fam = e.fam;
+    memset(&e.res, 0, sizeof(e.res));
+    e.res.jbar = g->jbar;
+    e.res.omega = e.pp.omega;
+    // the first check, as in fld_solve
+    double rel = 0.0;
+    if ((st = residual_now(g, e.fam, e.pp, p->residual_margin, &rel)) != FLD_OK) return st;
+    e.res.checks = 1;
+    e.res.rel_residual = rel;
+    e.own_stream = g->stream;
+    const Action a = e.ctl.first(rel);
+    if (a == ACT_SAVE) {
+        if ((st = snapshot(g, e.fam, true)) != FLD_OK) return st;
+        e.snap_fam = e.fam;
+        e.snap_lo = g->lo_live;
+    }
+    FLD_CK(cudaStreamSynchronize(g->stream));
+    g->stream = s->bs;   // from here on the grid's work is ordered on the server stream
+    s->active.push_back(e);
+    if (a == ACT_CONVERGED) server_retire(s, s->active.size() - 1, FLD_OK, rel);
+    else if (a == ACT_DIVERGED) server_retire(s, s->active.size() - 1, FLD_ERR_DIVERGED, rel);
+    return FLD_OK;
+}
+
+fld_status fld_server_active(fld_server s, int *count) {
+    if (!s || !count) return fail(FLD_ERR_INVALID_ARG, "server or count is NULL");
+    *count = (int)s->active.size();
+    return FLD_OK;
+}
+
+fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *results, int capacity, int *nfinished) {
+    if (!s || !nfinished) return fail(FLD_ERR_INVALID_ARG, "server or nfinished is NULL");
+    if (capacity > 0 && (!tags || !results)) return fail(FLD_ERR_INVALID_ARG, "tags / results are NULL");
+    *nfinished = 0;
+    FLD_CK(cudaSetDevice(s->device));
+    const fld_solve_params *p = &s->p;
+    fld_status st = FLD_OK;
+    const size_t n = s->active.size();
+    if (n > 0) {
+        // -- one block of iterations per active grid, grids spread over the pool
+        FLD_CK(cudaEventRecord(s->fork, s->bs));
+        const size_t nside = s->side.size() < n ? s->side.size() : n;
+        for (size_t i = 0; i < nside; ++i) FLD_CK(cudaStreamWaitEvent(s->side[i], s->fork, 0));
+        std::vector<int> k(n);
+        for (size_t i = 0; i < n; ++i) {
+            ServerEntry &e = s->active[i];
+            k[i] = p->check_every;
+            if (k[i] > p->max_iters - e.res.iterations) k[i] = p->max_iters - e.res.iterations;
+            if (k[i] <= 0) continue;
+            e.g->stream = s->side[i % nside];
+            st = run_block(e.g, e.fam, e.pp, k[i]);
+            e.g->stream = s->bs;
+            if (st != FLD_OK) return st;
+            s->launches += 2LL * k[i];
+            e.res.iterations += k[i];
+            if (e.fam == FAM_F32) e.res.iterations_fp32 += k[i];
+            else e.res.iterations_corr += k[i];
         }
-        cudaGraph_t graph = nullptr;
-        FLD_CK(cudaStreamBeginCapture(bs, cudaStreamCaptureModeThreadLocal));
-        cudaError_t ce = cudaEventRecord(fork, bs);
-        for (int i = 0; i < nside && ce == cudaSuccess; ++i) ce = cudaStreamWaitEvent(side[i], fork, 0);
-        int slot = 0;
-        for (int a = 0; a < count && ce == cudaSuccess; ++a) {
-            if (!hd[a].active) continue;
-            cudaStream_t ss = side[slot++ % nside];
-            for (int i = 0; i < kg && ce == cudaSuccess; ++i)
-                for (int c = 0; c < 2 && ce == cudaSuccess; ++c)
-                    ce = launch_pass(fam[a], grids[a]->L, grids[a]->f, ppv[a], c, ss);
+        for (size_t i = 0; i < nside; ++i) {
+            FLD_CK(cudaEventRecord(s->join[i], s->side[i]));
+            FLD_CK(cudaStreamWaitEvent(s->bs, s->join[i], 0));
         }
-        for (int i = 0; i < nside && ce == cudaSuccess; ++i) {
-            ce = cudaEventRecord(join[i], side[i]);
-            if (ce == cudaSuccess) ce = cudaStreamWaitEvent(bs, join[i], 0);
+        // -- residuals of all active grids in one batched pass
+        std::vector<BatchDesc> hd(n);
+        std::vector<int> res_tab, res_count(n);
+        int slots = 0;
+        for (size_t i = 0; i < n; ++i) {
+            const ServerEntry &e = s->active[i];
+            BatchDesc &d = hd[i];
+            memset(&d, 0, sizeof(d));
+            d.L = e.g->L;
+            d.sp = e.g->f.sp; d.ah2 = e.g->f.ah2; d.jh2 = e.g->f.jh2; d.phi = e.g->f.phi; d.phlo = e.g->f.phlo;
+            d.D = e.g->f.D; d.Df = e.g->f.Df;
+            d.omega = (float)e.pp.omega; d.inv2h = (float)e.pp.inv2h; d.floor_ = (float)e.pp.floor_;
+            d.larsen_n = (float)e.pp.larsen_n; d.lim = e.pp.lim; d.rounds = e.pp.local_iters;
+            d.mode = e.fam == FAM_FF ? 1 : 0;
+            d.active = 1;
+            residual_dims(e.g->L, &d.res_bx, &d.res_by);
+            res_count[i] = d.res_bx * d.res_by * e.g->nz;
+            d.res_first = (int)res_tab.size();
+            d.res_slot = slots;
+            slots += res_count[i];
+            res_tab.insert(res_tab.end(), (size_t)res_count[i], (int)i);
         }
-        cudaError_t ce2 = cudaStreamEndCapture(bs, &graph);
-        if (ce != cudaSuccess || ce2 != cudaSuccess) {
-            if (graph) cudaGraphDestroy(graph);
-            return cuda_fail(ce != cudaSuccess ? ce : ce2, "batched graph capture");
-        }
-        ce = cudaGraphInstantiate(&exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ce != cudaSuccess) {
-            exec = nullptr;
-            return cuda_fail(ce, "cudaGraphInstantiate (batch)");
-        }
-        graph_k = kg;
-        dirty = false;
-        return FLD_OK;
-    };
-    int it = 0;
-    while (active > 0 && it < p->max_iters) {
-        int k = p->check_every;
-        if (k > p->max_iters - it) k = p->max_iters - it;
-        // k iterations as reps replays of a kg-iteration graph
-        int kg = k < kGraphIters ? k : kGraphIters;
-        while (k % kg) --kg;
-        if (!exec || dirty || graph_k != kg)
-            if ((st = capture(kg)) != FLD_OK) return st;
-        for (int rep = 0; rep < k / kg; ++rep) FLD_CK(cudaGraphLaunch(exec, bs));
-        launches += 2LL * k * active;
-        it += k;
-        for (int a = 0; a < count; ++a) {
-            if (!hd[a].active) continue;
-            res[a].iterations += k;
-            if (hd[a].mode == 0) res[a].iterations_fp32 += k;
-            else res[a].iterations_corr += k;
-        }
-        if ((st = residuals()) != FLD_OK) return st;
-        bool changed = false;
-        for (int a = 0; a < count; ++a) {
-            if (!hd[a].active) continue;
-            fld_grid_s *g = grids[a];
-            const double rel = rel_of(a);
-            res[a].rel_residual = rel;
-            ++res[a].checks;
-            const Action act = ctl[a].next(rel, ppv[a].omega);
-            switch (act) {
-            case ACT_CONVERGED: finish(a, FLD_OK, rel); --active; changed = dirty = true; break;
-            case ACT_DIVERGED: finish(a, FLD_ERR_DIVERGED, rel); --active; changed = dirty = true; break;
-            case ACT_STALLED: finish(a, FLD_ERR_NOT_CONVERGED, rel); --active; changed = dirty = true; break;
+        if ((st = server_workspace(s, (int)n, slots)) != FLD_OK) return st;
+        FLD_CK(cudaMemcpyAsync(s->d_desc, hd.data(), sizeof(BatchDesc) * n, cudaMemcpyHostToDevice, s->bs));
+        FLD_CK(cudaMemcpyAsync(s->d_res, res_tab.data(), sizeof(int) * res_tab.size(), cudaMemcpyHostToDevice, s->bs));
+        FLD_CK(cudaMemcpyAsync(s->d_count, res_count.data(), sizeof(int) * n, cudaMemcpyHostToDevice, s->bs));
+        FLD_CK(launch_residual_batch(s->d_desc, s->d_res, (int)res_tab.size(), (int)n, s->d_count, s->d_part,
+                                     s->d_out, p->limiter, p->residual_margin, s->bs));
+        s->launches += 3;
+        std::vector<double> out(2 * n);
+        FLD_CK(cudaMemcpyAsync(out.data(), s->d_out, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, s->bs));
+        FLD_CK(cudaStreamSynchronize(s->bs));
+        // -- each grid's own decisions (same as fld_solve)
+        std::vector<std::pair<size_t, std::pair<fld_status, double>>> retire;
+        for (size_t i = 0; i < n; ++i) {
+            ServerEntry &e = s->active[i];
+            fld_grid_s *g = e.g;
+            const double rel = rel_from_sums(g, p->residual_margin, out[2 * i], out[2 * i + 1]);
+            e.res.rel_residual = rel;
+            ++e.res.checks;
+            const Action a = e.ctl.next(rel, e.pp.omega);
+            switch (a) {
+            case ACT_CONVERGED: retire.push_back({i, {FLD_OK, rel}}); break;
+            case ACT_DIVERGED: retire.push_back({i, {FLD_ERR_DIVERGED, rel}}); break;
+            case ACT_STALLED: retire.push_back({i, {FLD_ERR_NOT_CONVERGED, rel}}); break;
             case ACT_SAVE:
-                if ((st = snapshot(g, fam[a], true)) != FLD_OK) return st;
-                snap_fam[a] = fam[a];
-                snap_lo[a] = g->lo_live;
+                if ((st = snapshot(g, e.fam, true)) != FLD_OK) return st;
+                e.snap_fam = e.fam;
+                e.snap_lo = g->lo_live;
                 break;
             case ACT_RESTORE:
-                if ((st = snapshot(g, snap_fam[a], false)) != FLD_OK) return st;
-                fam[a] = snap_fam[a];
-                ctl[a].fam = fam[a];
-                g->lo_live = snap_lo[a];
-                hd[a].mode = fam[a] == FAM_FF ? 1 : 0;
-                ppv[a].omega = 1.0 + 0.97 * (ppv[a].omega - 1.0);
-                hd[a].omega = (float)ppv[a].omega;
-                changed = dirty = true;
+                if ((st = snapshot(g, e.snap_fam, false)) != FLD_OK) return st;
+                e.fam = e.snap_fam;
+                e.ctl.fam = e.fam;
+                g->lo_live = e.snap_lo;
+                e.pp.omega = 1.0 + 0.97 * (e.pp.omega - 1.0);
                 break;
             case ACT_SWITCH:
                 if ((st = sync_family(g, FAM_FF)) != FLD_OK) return st;
-                fam[a] = FAM_FF;
-                ctl[a].fam = FAM_FF;
-                ctl[a].begin_phase();
-                hd[a].mode = 1;
-                changed = dirty = true;
+                e.fam = FAM_FF;
+                e.ctl.fam = FAM_FF;
+                e.ctl.begin_phase();
                 break;
             case ACT_CONTINUE: break;
             }
+            if (a != ACT_CONVERGED && a != ACT_DIVERGED && a != ACT_STALLED && e.res.iterations >= p->max_iters)
+                retire.push_back({i, {FLD_ERR_NOT_CONVERGED, rel}});
         }
-        if (changed) {
-            long long live = 0;
-            for (int a = 0; a < count; ++a)
-                if (hd[a].active) live += res_count[a];
-            const bool compact = active > 0 && live < (long long)(0.7 * (double)res_tab.size());
-            if (compact) build_tables();
-            if ((st = upload(compact)) != FLD_OK) return st;
+        for (size_t r = retire.size(); r-- > 0;) {
+            ServerEntry &e = s->active[retire[r].first];
+            e.res.kernels = s->launches;
+            server_retire(s, retire[r].first, retire[r].second.first, retire[r].second.second);
         }
+        FLD_CK(cudaStreamSynchronize(s->bs));
     }
-    fld_status worst = FLD_OK;
-    for (int a = 0; a < count; ++a) {
-        if (hd[a].active) finish(a, FLD_ERR_NOT_CONVERGED, res[a].rel_residual);
-        fld_grid_s *g = grids[a];
-        g->valid_float = true;
-        g->valid_d = false;
-        res[a].omega = ppv[a].omega;
-        res[a].omega_backoffs = ctl[a].backoffs;
-        res[a].kernels = launches;
-        if (res[a].status == FLD_ERR_DIVERGED) worst = FLD_ERR_DIVERGED;
-        else if (res[a].status != FLD_OK && worst == FLD_OK) worst = FLD_ERR_NOT_CONVERGED;
-        if (results) results[a] = res[a];
+    // -- report finished grids (oldest first)
+    int m = 0;
+    while (m < capacity && !s->done.empty()) {
+        tags[m] = s->done.front().tag;
+        results[m] = s->done.front().res;
+        s->done.erase(s->done.begin());
+        ++m;
     }
-    FLD_CK(cudaStreamSynchronize(bs));
-    if (worst != FLD_OK) g_last_error = "not every solve of the batch converged (see the per-grid results)";
-    return worst;
+    *nfinished = m;
+    return FLD_OK;
 }
 
 fld_status fld_solve_batch(fld_grid *grids, int count, const fld_solve_params *p, fld_solve_result *results) {
@@ -1181,12 +1185,10 @@ fld_status fld_solve_batch(fld_grid *grids, int count, const fld_solve_params *p
         return fail(FLD_ERR_INVALID_ARG, "batched solves run the FP32 / MIXED sweeps; use fld_solve for FP64");
     if (!(p->tol >= 0.0)) return fail(FLD_ERR_INVALID_ARG, "tol must be >= 0");
     if (p->max_iters < 0 || p->check_every < 1) return fail(FLD_ERR_INVALID_ARG, "bad max_iters / check_every");
-    // Grids of one shared launch should keep their per-iteration working set
-    // (24 bytes per voxel: sigma', sigma_a', j, phi hi/lo, D) within L2: a
-    // group larger than L2 streams from HBM on every pass, while each grid
-    // alone would not.  Grids are taken in order of size and packed greedily
-    // into groups of at most 3/4 of the L2 capacity; groups run one after
-    // another, small grids share launches, large grids run alone.
+    // Grids of one group should keep their per-iteration working set (24 bytes
+    // per voxel: sigma', sigma_a', j, phi hi/lo, D) within L2.  Grids are taken
+    // in order of size and packed greedily into groups of at most 3/4 of the
+    // L2 capacity; groups run one after another, small grids share steps.
     int l2 = 0;
     if (cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, grids[0]->device) != cudaSuccess || l2 <= 0) {
         (void)cudaGetLastError();
@@ -1197,31 +1199,43 @@ fld_status fld_solve_batch(fld_grid *grids, int count, const fld_solve_params *p
     for (int a = 0; a < count; ++a) order[a] = a;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return nvox(grids[x]) < nvox(grids[y]); });
     std::vector<fld_solve_result> res(count);
-    fld_status worst = FLD_OK;
+    fld_server srv = nullptr;
+    if ((st = fld_server_create(p, grids[0]->stream, &srv)) != FLD_OK) return st;
     const auto t0 = std::chrono::steady_clock::now();
     size_t a = 0;
-    while (a < order.size()) {
-        std::vector<fld_grid> group;
-        std::vector<int> idx;
+    std::vector<long long> tags(count);
+    std::vector<fld_solve_result> fin(count);
+    while (a < order.size() && st == FLD_OK) {
         double ws = 0.0;
+        int in_group = 0;
+        const double off = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         while (a < order.size()) {
             const double w = 24.0 * (double)nvox(grids[order[a]]);
-            if (!group.empty() && ws + w > budget) break;
-            group.push_back(grids[order[a]]);
-            idx.push_back(order[a]);
+            if (in_group > 0 && ws + w > budget) break;
+            if ((st = fld_server_add(srv, grids[order[a]], order[a])) != FLD_OK) break;
             ws += w;
+            ++in_group;
             ++a;
         }
-        std::vector<fld_solve_result> gr(group.size());
-        const double off = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
-        st = solve_group(group.data(), (int)group.size(), p, gr.data(), off);
-        if (st != FLD_OK && st != FLD_ERR_NOT_CONVERGED && st != FLD_ERR_DIVERGED) return st;
-        for (size_t b = 0; b < group.size(); ++b) res[idx[b]] = gr[b];
-        if (st == FLD_ERR_DIVERGED) worst = FLD_ERR_DIVERGED;
-        else if (st == FLD_ERR_NOT_CONVERGED && worst == FLD_OK) worst = FLD_ERR_NOT_CONVERGED;
+        int left = in_group;
+        while (st == FLD_OK && left > 0) {
+            int nf = 0;
+            if ((st = fld_server_step(srv, tags.data(), fin.data(), count, &nf)) != FLD_OK) break;
+            for (int b = 0; b < nf; ++b) {
+                res[tags[b]] = fin[b];
+                res[tags[b]].ms += off;
+            }
+            left -= nf;
+        }
     }
-    if (results)
-        for (int b = 0; b < count; ++b) results[b] = res[b];
+    fld_server_destroy(srv);
+    if (st != FLD_OK) return st;
+    fld_status worst = FLD_OK;
+    for (int b = 0; b < count; ++b) {
+        if (res[b].status == FLD_ERR_DIVERGED) worst = FLD_ERR_DIVERGED;
+        else if (res[b].status != FLD_OK && worst == FLD_OK) worst = FLD_ERR_NOT_CONVERGED;
+        if (results) results[b] = res[b];
+    }
     if (worst != FLD_OK) g_last_error = "not every solve of the batch converged (see the per-grid results)";
     return worst;
 }

@@ -1,0 +1,104 @@
+"""Host logic of the continuous-batching serving loop, on a fake backend and
+a fake clock (no GPU): arrivals, admission by free slots and free memory,
+arrival-order admission, latency accounting."""
+import numpy as np
+import pytest
+
+from paper_1403_8105_gb300 import serve
+
+
+class FakeClock:
+    def __init__(self):
+        self.t = 0.0
+
+    def __call__(self):
+        return self.t
+
+    def sleep(self, dt):
+        self.t += max(dt, 1e-4)
+
+
+class FakeBackend:
+    """Each admitted request needs `n // 8` steps; a step takes 0.01 s."""
+
+    def __init__(self, clock, free=10_000, step_s=0.01):
+        self.clock = clock
+        self.free = free
+        self.step_s = step_s
+        self.inflight = {}
+        self.log = []
+
+    def free_bytes(self):
+        return self.free
+
+    def admit(self, req):
+        self.free -= req.footprint
+        self.inflight[req.rid] = [req.n // 8, req.footprint]
+        self.log.append(("admit", req.rid, len(self.inflight)))
+        return req.rid
+
+    def active(self):
+        return len(self.inflight)
+
+    def step(self):
+        self.clock.t += self.step_s
+        out = []
+        for rid in list(self.inflight):
+            self.inflight[rid][0] -= 1
+            if self.inflight[rid][0] <= 0:
+                self.free += self.inflight.pop(rid)[1]
+                out.append((rid, {"status": 0}))
+        return out
+
+    def release(self, grid):
+        pass
+
+
+def _requests(count=40, rate=50.0, seed=3, foot=100):
+    arr = serve.poisson_arrivals(count, rate, seed)
+    rng = np.random.default_rng(seed)
+    return [serve.Request(rid=i, arrival=float(arr[i]), n=int(rng.integers(8, 64)), medium=None, light=None,
+                          footprint=foot) for i in range(count)]
+
+
+def test_poisson_arrivals_rate_and_order():
+    a = serve.poisson_arrivals(20000, 200.0, 1)
+    assert np.all(np.diff(a) > 0)
+    assert abs(20000 / a[-1] - 200.0) < 6.0          # ~3 sigma of the rate estimate
+    assert np.array_equal(a, serve.poisson_arrivals(20000, 200.0, 1))
+
+
+def test_every_request_completes_with_consistent_times():
+    clk = FakeClock()
+    reqs, st = serve.serve(_requests(), FakeBackend(clk), max_active=8, clock=clk, sleep=clk.sleep)
+    assert st["requests"] == 40
+    for r in reqs:
+        assert r.arrival <= r.admitted <= r.finished
+    assert st["latency_s_p99"] >= st["latency_s_p50"] > 0
+
+
+def test_admission_respects_slots_and_memory():
+    clk = FakeClock()
+    be = FakeBackend(clk, free=1000)
+    reqs, st = serve.serve(_requests(foot=300), be, max_active=8, memory_fraction=1.0, clock=clk, sleep=clk.sleep)
+    assert st["max_in_flight"] <= 3                      # 1000 B of room, 300 B each
+    assert all(n <= 3 for kind, rid, n in be.log)
+    clk = FakeClock()
+    be = FakeBackend(clk, free=10 ** 9)
+    reqs, st = serve.serve(_requests(), be, max_active=2, clock=clk, sleep=clk.sleep)
+    assert st["max_in_flight"] <= 2
+
+
+def test_admission_keeps_arrival_order():
+    clk = FakeClock()
+    be = FakeBackend(clk)
+    reqs, _ = serve.serve(_requests(), be, max_active=4, clock=clk, sleep=clk.sleep)
+    admitted = [rid for kind, rid, n in be.log]
+    arrival_order = [r.rid for r in sorted(reqs, key=lambda r: r.arrival)]
+    assert admitted == arrival_order
+
+
+def test_request_that_never_fits_is_reported():
+    clk = FakeClock()
+    with pytest.raises(RuntimeError):
+        serve.serve(_requests(count=3, foot=10 ** 6), FakeBackend(clk, free=1000), clock=clk, sleep=clk.sleep)
