@@ -41,8 +41,9 @@ UNIT = "voxel-updates/s"
 # algorithmic bytes per voxel update of one sweep (D stored, as in Algorithm 1):
 # reads phi, D, sigma', sigma_a' dl^2, j dl^2 and writes phi, D (4 bytes each);
 # the float-float correction sweep also reads and writes the low word of phi.
-BYTES_PER_UPDATE = {"fp32": 28, "ff": 36}
+BYTES_PER_UPDATE = {"fp32": 28, "fh": 36, "ff": 36}
 KERNEL_NAME = {"fp32": "k_pass_f32 (single-precision red/black pass)",
+               "fh": "k_pass_fh (hi/lo phi, FP32-summed red/black pass)",
                "ff": "k_pass_ff (float-float correction pass)"}
 
 
@@ -291,8 +292,10 @@ def run_gpu(args):
     launches = sum(int(r.kernels) + 3 for r in results)   # + set_medium validation (2) + bake (1)
 
     # sweep kernel timing inside the timed solves (graph blocks hold only passes)
-    fam_ms = {"fp32": sum(r.ms_sweep_fp32 for r in results), "ff": sum(r.ms_sweep_corr for r in results)}
-    fam_it = {"fp32": sum(r.iterations_fp32 for r in results), "ff": sum(r.iterations_corr for r in results)}
+    fam_ms = {"fp32": sum(r.ms_sweep_fp32 for r in results), "fh": sum(r.ms_sweep_mid for r in results),
+              "ff": sum(r.ms_sweep_corr for r in results)}
+    fam_it = {"fp32": sum(r.iterations_fp32 for r in results), "fh": sum(r.iterations_mid for r in results),
+              "ff": sum(r.iterations_corr for r in results)}
     dom = max(fam_ms, key=lambda k: fam_ms[k])
     peaks = measured_peaks()
     peak = peaks["hbm_gbs"] if peaks else 6800.0
@@ -310,8 +313,7 @@ def run_gpu(args):
                 "launches_measured": 2 * iters, "peak_source": peak_src, "l2_resident": l2_resident}
 
     roofline = roof(dom, fam_ms[dom], fam_it[dom], nvox, f"cloud{n}", True)
-    other = "ff" if dom == "fp32" else "fp32"
-    roof_other = roof(other, fam_ms[other], fam_it[other], nvox, f"cloud{n}", True)
+    roof_other = {f: roof(f, fam_ms[f], fam_it[f], nvox, f"cloud{n}", True) for f in fam_ms if f != dom}
 
     extras = {}
     if ranks.rank == 0 and not args.no_extras:
@@ -331,7 +333,8 @@ def run_gpu(args):
         "iterations_fp32_per_solve": [r.iterations_fp32 for r in results],
         "rel_residual": [r.rel_residual for r in results],
         "status": [fld.fld_status_string(r.status) for r in results],
-        "roofline": roofline, "roofline_other_pass": roof_other,
+        "roofline": roofline, "roofline_other_passes": roof_other,
+        "iterations_by_family_per_solve": {f: fam_it[f] // max(1, len(results)) for f in fam_it},
         "gpu_launches": launches,
         "clocks": clocks,
     }
@@ -358,14 +361,14 @@ def roofline_256(fld, torch, dev, sig_np, alb_np, roof):
     try:
         g.set_medium(sig, alb)
         g.bake_directional((0.0, 0.0, -1.0), 1.0)
-        for fam, prec in (("fp32", "fp32"), ("ff", "mixed")):
+        for fam, prec in (("fp32", "fp32"), ("fh", "pair"), ("ff", "mixed")):
             p = fld.params(limiter="lp", precision=prec, tol=0.0, local_iters=2, check_every=64, max_iters=64,
                            fp32_switch=1e30)
-            g.solve(p, check=False)            # warm-up (and graph capture)
-            p.warm_start = 1
+            g.solve(p, check=False)            # warm-up (and graph capture); MIXED switches after one block
+            p.warm_start = 1                   # ... and its warm start continues with float-float sweeps
             r = g.solve(p, check=False)
-            ms = r.ms_sweep_fp32 if fam == "fp32" else r.ms_sweep_corr
-            it = r.iterations_fp32 if fam == "fp32" else r.iterations_corr
+            ms = {"fp32": r.ms_sweep_fp32, "fh": r.ms_sweep_mid, "ff": r.ms_sweep_corr}[fam]
+            it = {"fp32": r.iterations_fp32, "fh": r.iterations_mid, "ff": r.iterations_corr}[fam]
             out[fam] = roof(fam, ms, it, n ** 3, f"cloud{n}", False)
     finally:
         g.close()

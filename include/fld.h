@@ -78,12 +78,15 @@ typedef enum { FLD_MEM_HOST = 0, FLD_MEM_DEVICE = 1 } fld_mem;
  *         evaluated with a double-single (float-float) sum so it is not
  *         limited by cancellation.
  * MIXED : single-precision sweeps until the residual stalls or falls below
- *         fp32_switch, then correction sweeps that keep phi as a
- *         float-float pair (about 44 significant bits) and form each update
- *         from an accurately summed residual; reaches residuals far below
- *         the single-precision floor (Sec. 6.2 notes 1e-4 as the practical
- *         single-precision limit). */
-typedef enum { FLD_PREC_FP64 = 0, FLD_PREC_FP32 = 1, FLD_PREC_MIXED = 2 } fld_precision;
+ *         fp32_switch; then sweeps that keep phi as a hi/lo float pair
+ *         (about 44 significant bits) with FP32-summed updates, until they
+ *         stall or reach 3 * tol; then correction sweeps that form each
+ *         update from a float-float sum with correctly rounded D.  Reaches
+ *         residuals far below the single-precision floor (Sec. 6.2 notes
+ *         1e-4 as the practical single-precision limit). */
+/* PAIR  : only the middle stage of MIXED -- phi kept as a hi/lo float pair,
+ *         updates summed in FP32 with the approximate D of the bulk sweeps. */
+typedef enum { FLD_PREC_FP64 = 0, FLD_PREC_FP32 = 1, FLD_PREC_MIXED = 2, FLD_PREC_PAIR = 3 } fld_precision;
 
 typedef struct {
     int limiter;          /* fld_limiter                                             */
@@ -133,6 +136,9 @@ typedef struct {
     long long kernels;     /* kernel launches the solve issued (incl. graph nodes)  */
     int omega_backoffs;    /* times the solve returned to its best state and
                               reduced omega after the residual diverged         */
+    int iterations_mid;    /* MIXED: sweeps with phi as a hi/lo pair and
+                              FP32-summed updates (between the two above)       */
+    double ms_sweep_mid;   /* device time inside those sweeps                     */
 } fld_solve_result;
 
 /* Fill *p with the defaults: LP limiter, Larsen n = 2, omega auto,

@@ -36,7 +36,7 @@ FLD_OK, FLD_ERR_INVALID_ARG, FLD_ERR_OOM, FLD_ERR_CUDA, FLD_ERR_STATE = 0, 1, 2,
 FLD_ERR_NOT_CONVERGED, FLD_ERR_DIVERGED, FLD_ERR_NO_DEVICE = 5, 6, 7
 FLD_MEM_HOST, FLD_MEM_DEVICE = 0, 1
 LIMITERS = {"cda": 0, "sum": 1, "max": 2, "kershaw": 3, "larsen": 4, "lp": 5}
-PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2}
+PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2, "pair": 3}
 
 
 class SolveParams(ctypes.Structure):
@@ -58,7 +58,7 @@ class SolveResult(ctypes.Structure):
         ("iterations_corr", ctypes.c_int), ("checks", ctypes.c_int), ("rel_residual", ctypes.c_double),
         ("jbar", ctypes.c_double), ("omega", ctypes.c_double), ("ms", ctypes.c_double),
         ("ms_sweep_fp32", ctypes.c_double), ("ms_sweep_corr", ctypes.c_double), ("kernels", ctypes.c_longlong),
-        ("omega_backoffs", ctypes.c_int),
+        ("omega_backoffs", ctypes.c_int), ("iterations_mid", ctypes.c_int), ("ms_sweep_mid", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -81,7 +81,7 @@ struct fld_grid_s {
     long long jbar_version = 0;
     bool valid_float = false, valid_d = false;   // which family holds the state
     bool lo_live = false;                        // phlo may be non-zero
-    GraphEntry graphs[3];
+    GraphEntry graphs[4];
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evb0 = nullptr, evb1 = nullptr;
     long long kernels = 0;                       // kernel launches issued so far
     // last good state of a solve (float family: phi, lo, D; FP64: phi, D)
@@ -208,6 +208,15 @@ fld_status init_state(fld_grid_s *g, const fld_solve_params *p, Family fam) {
     return FLD_OK;
 }
 
+// First sweep family of a precision mode.
+Family start_family(int precision) {
+    switch (precision) {
+    case FLD_PREC_FP64: return FAM_F64;
+    case FLD_PREC_PAIR: return FAM_FH;
+    default: return FAM_F32;
+    }
+}
+
 // Make the family's fields hold the current state.
 fld_status sync_family(fld_grid_s *g, Family fam) {
     if (fam == FAM_F64) {
@@ -235,7 +244,7 @@ fld_status sync_family(fld_grid_s *g, Family fam) {
             FLD_CK(cudaMemsetAsync(g->f.phlo, 0, sizeof(float) * (size_t)g->L.total, g->stream));
             g->lo_live = false;
         }
-        if (fam == FAM_FF) g->lo_live = true;
+        if (fam == FAM_FF || fam == FAM_FH) g->lo_live = true;
         g->valid_d = false;
     }
     return FLD_OK;
@@ -299,7 +308,7 @@ fld_status check_params(const fld_grid_s *g, const fld_solve_params *p) {
     if (p->limiter < FLD_LIM_CDA || p->limiter > FLD_LIM_LP) return fail(FLD_ERR_INVALID_ARG, "unknown limiter");
     if (p->limiter == FLD_LIM_LARSEN && !(p->larsen_n > 0.0)) return fail(FLD_ERR_INVALID_ARG, "larsen_n must be > 0");
     if (p->omega > 0.0 && !(p->omega < 2.0)) return fail(FLD_ERR_INVALID_ARG, "omega must lie in (0, 2)");
-    if (p->precision < FLD_PREC_FP64 || p->precision > FLD_PREC_MIXED)
+    if (p->precision < FLD_PREC_FP64 || p->precision > FLD_PREC_PAIR)
         return fail(FLD_ERR_INVALID_ARG, "unknown precision");
     if (p->local_iters > 64) return fail(FLD_ERR_INVALID_ARG, "local_iters must be <= 64");
     if (p->residual_margin < 0) return fail(FLD_ERR_INVALID_ARG, "residual_margin must be >= 0");
@@ -366,6 +375,9 @@ fld_status snapshot(fld_grid_s *g, Family fam, bool save) {
 // fld_solve_batch, so a grid takes the same path alone and in a batch).
 enum Action { ACT_CONTINUE, ACT_SAVE, ACT_RESTORE, ACT_SWITCH, ACT_CONVERGED, ACT_DIVERGED, ACT_STALLED };
 
+// The precision that follows `f` in a MIXED solve.
+Family next_family(Family f) { return f == FAM_F32 ? FAM_FH : FAM_FF; }
+
 struct Controller {
     int precision = FLD_PREC_MIXED;
     double tol = 1e-6, sw = 2e-5;
@@ -401,19 +413,23 @@ struct Controller {
         } else {
             ++since_best;
         }
-        // single precision has done what it can (Sec. 6.2: ~1e-4 is its limit)
+        // single precision has done what it can (Sec. 6.2: ~1e-4 is its limit):
+        // continue with phi as a hi/lo pair, first with FP32-summed updates,
+        // then with float-float sums near the tolerance
         if (precision == FLD_PREC_MIXED && fam == FAM_F32 && (rel <= sw || since_best >= kSwitchChecks))
+            return ACT_SWITCH;
+        if (precision == FLD_PREC_MIXED && fam == FAM_FH && (rel <= 3.0 * tol || since_best >= kSwitchChecks))
             return ACT_SWITCH;
         // The float-float and FP64 sweeps reach residuals near 1e-7; stalling
         // far above the tolerance there means over-relaxation is cycling, not
         // that the arithmetic is exhausted: back off omega.
-        if (fam != FAM_F32 && tol > 0.0 && since_best >= kSwitchChecks && best > 100.0 * tol) {
+        if ((fam == FAM_FF || fam == FAM_F64) && tol > 0.0 && since_best >= kSwitchChecks && best > 100.0 * tol) {
             if (backoffs >= kMaxBackoffs || omega <= 1.0) return ACT_STALLED;
             ++backoffs;
             since_best = 0;
             return ACT_RESTORE;
         }
-        if (since_best >= kStallChecks && !(precision == FLD_PREC_MIXED && fam == FAM_F32)) return ACT_STALLED;
+        if (since_best >= kStallChecks && !(precision == FLD_PREC_MIXED && fam != FAM_FF)) return ACT_STALLED;
         return a;
     }
 };
@@ -711,7 +727,7 @@ fld_status fld_iterate(fld_grid g, const fld_solve_params *p, int iterations) {
     if (st != FLD_OK) return st;
     if ((st = check_params(g, p)) != FLD_OK) return st;
     if (iterations < 0) return fail(FLD_ERR_INVALID_ARG, "iterations must be >= 0");
-    const Family fam = p->precision == FLD_PREC_FP64 ? FAM_F64 : (p->precision == FLD_PREC_FP32 ? FAM_F32 : FAM_FF);
+    const Family fam = p->precision == FLD_PREC_MIXED ? FAM_FF : start_family(p->precision);
     if ((st = prepare(g, p, fam)) != FLD_OK) return st;
     if (!p->warm_start) {
         if ((st = init_state(g, p, fam)) != FLD_OK) return st;
@@ -725,7 +741,7 @@ fld_status fld_residual(fld_grid g, const fld_solve_params *p, double *rel) {
     if (st != FLD_OK) return st;
     if ((st = check_params(g, p)) != FLD_OK) return st;
     if (!rel) return fail(FLD_ERR_INVALID_ARG, "rel is NULL");
-    const Family fam = p->precision == FLD_PREC_FP64 ? FAM_F64 : (p->precision == FLD_PREC_FP32 ? FAM_F32 : FAM_FF);
+    const Family fam = p->precision == FLD_PREC_FP64 ? FAM_F64 : FAM_FF;
     if ((st = prepare(g, p, fam)) != FLD_OK) return st;
     if (!g->valid_float && !g->valid_d) return fail(FLD_ERR_STATE, "the grid holds no state yet");
     Family use = fam;
@@ -743,9 +759,8 @@ fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r)
     fld_solve_result res;
     memset(&res, 0, sizeof(res));
     const long long kernels0 = g->kernels;
-    Family fam = p->precision == FLD_PREC_FP64 ? FAM_F64 : FAM_F32;
+    Family fam = start_family(p->precision);
     if ((st = prepare(g, p, fam)) != FLD_OK) return st;
-    if (p->precision == FLD_PREC_MIXED && (st = prepare(g, p, FAM_FF)) != FLD_OK) return st;
     if (!p->warm_start) {
         if ((st = init_state(g, p, fam)) != FLD_OK) return st;
     } else if (p->precision == FLD_PREC_MIXED && !g->valid_d && g->lo_live) {
@@ -792,12 +807,14 @@ fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r)
         FLD_CK(cudaEventRecord(g->evb1, g->stream));
         it += k;
         if (fam == FAM_F32) res.iterations_fp32 += k;
+        else if (fam == FAM_FH) res.iterations_mid += k;
         else res.iterations_corr += k;
         if ((st = residual_now(g, fam, pp, p->residual_margin, &rel)) != FLD_OK) return st;
         ++res.checks;
         float bms = 0.0f;   // the residual read above synchronised the stream
         FLD_CK(cudaEventElapsedTime(&bms, g->evb0, g->evb1));
         if (fam == FAM_F32) res.ms_sweep_fp32 += bms;
+        else if (fam == FAM_FH) res.ms_sweep_mid += bms;
         else res.ms_sweep_corr += bms;
         a = ctl.next(rel, pp.omega);
         switch (a) {
@@ -816,8 +833,8 @@ fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r)
             rel = ctl.best;
             break;
         case ACT_SWITCH:
-            if ((st = sync_family(g, FAM_FF)) != FLD_OK) return st;
-            fam = FAM_FF;
+            fam = next_family(fam);
+            if ((st = sync_family(g, fam)) != FLD_OK) return st;
             ctl.fam = fam;
             ctl.begin_phase();
             break;
@@ -940,8 +957,8 @@ fld_status fld_server_create(const fld_solve_params *p, void *stream, fld_server
     if (!out) return fail(FLD_ERR_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (!p) return fail(FLD_ERR_INVALID_ARG, "params is NULL");
-    if (p->precision != FLD_PREC_FP32 && p->precision != FLD_PREC_MIXED)
-        return fail(FLD_ERR_INVALID_ARG, "the server runs the FP32 / MIXED sweeps; use fld_solve for FP64");
+    if (p->precision == FLD_PREC_FP64 || p->precision < 0 || p->precision > FLD_PREC_PAIR)
+        return fail(FLD_ERR_INVALID_ARG, "the server runs the FP32 / MIXED / PAIR sweeps; use fld_solve for FP64");
     if (p->limiter < FLD_LIM_CDA || p->limiter > FLD_LIM_LP) return fail(FLD_ERR_INVALID_ARG, "unknown limiter");
     if (p->limiter == FLD_LIM_LARSEN && !(p->larsen_n > 0.0)) return fail(FLD_ERR_INVALID_ARG, "larsen_n must be > 0");
     if (p->omega > 0.0 && !(p->omega < 2.0)) return fail(FLD_ERR_INVALID_ARG, "omega must lie in (0, 2)");
@@ -1010,9 +1027,10 @@ fld_status fld_server_add(fld_server s, fld_grid g, long long tag) {
     e.tag = tag;
     e.t_add = std::chrono::steady_clock::now();
     FLD_CK(cudaStreamSynchronize(g->stream));
-    if ((st = prepare(g, p, FAM_F32)) != FLD_OK) return st;
+    e.fam = start_family(p->precision);
+    if ((st = prepare(g, p, e.fam)) != FLD_OK) return st;
     if (!p->warm_start) {
-        if ((st = init_state(g, p, FAM_F32)) != FLD_OK) return st;
+        if ((st = init_state(g, p, e.fam)) != FLD_OK) return st;
     } else if (p->precision == FLD_PREC_MIXED && !g->valid_d && g->lo_live) {
         e.fam = FAM_FF;
     }
@@ -1077,6 +1095,7 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
             s->launches += 2LL * k[i];
             e.res.iterations += k[i];
             if (e.fam == FAM_F32) e.res.iterations_fp32 += k[i];
+            else if (e.fam == FAM_FH) e.res.iterations_mid += k[i];
             else e.res.iterations_corr += k[i];
         }
         for (size_t i = 0; i < nside; ++i) {
@@ -1096,7 +1115,7 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
             d.D = e.g->f.D; d.Df = e.g->f.Df;
             d.omega = (float)e.pp.omega; d.inv2h = (float)e.pp.inv2h; d.floor_ = (float)e.pp.floor_;
             d.larsen_n = (float)e.pp.larsen_n; d.lim = e.pp.lim; d.rounds = e.pp.local_iters;
-            d.mode = e.fam == FAM_FF ? 1 : 0;
+            d.mode = e.fam == FAM_F32 ? 0 : 1;
             d.active = 1;
             residual_dims(e.g->L, &d.res_bx, &d.res_by);
             res_count[i] = d.res_bx * d.res_by * e.g->nz;
@@ -1141,9 +1160,9 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
                 e.pp.omega = 1.0 + 0.97 * (e.pp.omega - 1.0);
                 break;
             case ACT_SWITCH:
-                if ((st = sync_family(g, FAM_FF)) != FLD_OK) return st;
-                e.fam = FAM_FF;
-                e.ctl.fam = FAM_FF;
+                e.fam = next_family(e.fam);
+                if ((st = sync_family(g, e.fam)) != FLD_OK) return st;
+                e.ctl.fam = e.fam;
                 e.ctl.begin_phase();
                 break;
             case ACT_CONTINUE: break;

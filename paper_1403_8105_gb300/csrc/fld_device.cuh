@@ -208,8 +208,22 @@ __device__ __forceinline__ float grad_floor_f(float gx, float gy, float gz, floa
 }
 
 __device__ __forceinline__ float D_of_f(float gmax, float sp, float phi_p, float floor_, int lim, float larsen_n) {
-    const float R = gmax / fmaxf(sp * phi_p, floor_);
-    return limiter_f(lim, larsen_n, R) / sp;
+    const float den = fmaxf(sp * phi_p, floor_);
+    if (lim == LIM_LP) {
+        // one correctly rounded quotient per branch: R = gmax/den below 1
+        // (Laurent series), 1/R = den/gmax above (the exponential term,
+        // which needs R itself, only for 1 <= R < 9)
+        float F;
+        if (gmax < den) {
+            F = lp_series_f(gmax / den);
+        } else {
+            const float r = den / gmax;
+            const float tail = r > (1.0f / 9.0f) ? 2.0f / (expf(2.0f * (gmax / den)) - 1.0f) : 0.0f;
+            F = r * ((1.0f - r) + tail);
+        }
+        return F / sp;
+    }
+    return limiter_f(lim, larsen_n, gmax / den) / sp;
 }
 
 __device__ __forceinline__ float knudsen_D_f(float gx, float gy, float gz, float inv2h, float sp, float phi_p,

@@ -7,8 +7,10 @@
 
 namespace fld {
 
-// Arithmetic of one sweep family.
-enum Family : int { FAM_F32 = 0, FAM_FF = 1, FAM_F64 = 2 };
+// Arithmetic of one sweep family: FP32 (phi in float), FH (phi as a hi/lo
+// pair, update summed in FP32), FF (phi as a hi/lo pair, update summed in
+// float-float with correctly rounded D), FP64.
+enum Family : int { FAM_F32 = 0, FAM_FF = 1, FAM_F64 = 2, FAM_FH = 3 };
 
 struct PassParams {
     int lim;

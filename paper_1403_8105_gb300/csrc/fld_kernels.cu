@@ -354,6 +354,68 @@ __global__ void __launch_bounds__(256) k_pass_f32(Layout L, const float *__restr
                                inv2h, floor_, rounds_rt);
 }
 
+// Middle pass: phi kept as a hi/lo pair (no storage floor) but the update
+// summed in plain FP32 with the approximate D of the bulk sweeps -- about the
+// cost of the FP32 pass, reaching residuals a few times above the
+// float-float pass's.
+template <int LIM, int ROUNDS>
+__device__ __forceinline__ void pass_fh_body(const Layout &L, const float *__restrict__ sp,
+                                             const float *__restrict__ ah2, const float *__restrict__ jh2,
+                                             float *__restrict__ phi, float *__restrict__ phlo,
+                                             float *__restrict__ D, int colour, int t, int J, int K, int lim_rt,
+                                             float larsen_n, float omega, float inv2h, float floor_,
+                                             int rounds_rt) {
+    const int lim = LIM >= 0 ? LIM : lim_rt;
+    const int local_iters = ROUNDS > 0 ? ROUNDS : rounds_rt;
+    Nbrs o;
+    if (J > L.ny || !pass_cell(L, colour, t, J, K, o)) return;
+    const float p0 = phi[o.own], p0lo = phlo[o.own];
+    float d[6], Ds[6];
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        d[s] = (phi[o.nb[s]] - p0) + (phlo[o.nb[s]] - p0lo);   // phi_s - phi_p
+        Ds[s] = D[o.nb[s]];
+    }
+    const float s_ = sp[o.own], ah = ah2[o.own], jj = jh2[o.own];
+    const float gx = d[1] - d[0], gy = d[3] - d[2], gz = d[5] - d[4];
+    const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+    const float g = g2 > 0.0f ? g2 * rsqrtf(g2) * inv2h : 0.0f;
+    const float gmax = fmaxf(g, floor_);
+    const float inv_sp = __fdividef(1.0f, s_);
+    float A = 0.0f, B = 0.0f, C = 0.0f;
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        A += d[s];
+        B = fmaf(Ds[s], d[s], B);
+        C += Ds[s];
+    }
+    const float base = fmaf(0.5f, B, fmaf(-ah, p0, fmaf(-ah, p0lo, jj)));
+    const float den0 = fmaf(0.5f, C, ah);
+    float delta = 0.0f, Dp = 0.0f;
+#pragma unroll
+    for (int r = 0; r < (ROUNDS > 0 ? ROUNDS : 64); ++r) {
+        if (ROUNDS == 0 && r >= local_iters) break;
+        const float R = __fdividef(gmax, fmaxf(s_ * (p0 + delta), floor_));
+        Dp = limiter_fast(lim, larsen_n, R) * inv_sp;
+        delta = __fdividef(fmaf(0.5f * Dp, A, base), fmaf(3.0f, Dp, den0));
+    }
+    const ff nw = ff_add_f(ff{p0, p0lo}, __fmul_rn(omega, delta));
+    phi[o.own] = nw.hi;
+    phlo[o.own] = nw.lo;
+    D[o.own] = Dp;
+}
+
+template <int LIM, int ROUNDS>
+__global__ void __launch_bounds__(256) k_pass_fh(Layout L, const float *__restrict__ sp,
+                                                 const float *__restrict__ ah2, const float *__restrict__ jh2,
+                                                 float *__restrict__ phi, float *__restrict__ phlo,
+                                                 float *__restrict__ D, int colour, int lim_rt, float larsen_n,
+                                                 float omega, float inv2h, float floor_, int rounds_rt) {
+    pass_fh_body<LIM, ROUNDS>(L, sp, ah2, jh2, phi, phlo, D, colour, blockIdx.x * blockDim.x + threadIdx.x,
+                              blockIdx.y * blockDim.y + threadIdx.y + 1, blockIdx.z + 1, lim_rt, larsen_n, omega,
+                              inv2h, floor_, rounds_rt);
+}
+
 // Float-float correction pass: phi kept as a hi/lo pair, S summed so the
 // update is accurate to the pair's precision; correctly rounded D (the same
 // function the residual kernel evaluates).
@@ -887,6 +949,15 @@ cudaError_t launch_pass(Family fam, const Layout &L, const Fields &f, const Pass
                               (float)p.omega, (float)p.inv2h, (float)p.floor_, p.local_iters);
         break;
     }
+    case FAM_FH: {
+        auto k = k_pass_fh<-1, 0>;
+        if (p.local_iters == 2 && p.lim == LIM_LP) k = k_pass_fh<LIM_LP, 2>;
+        else if (p.local_iters == 2 && p.lim == LIM_KERSHAW) k = k_pass_fh<LIM_KERSHAW, 2>;
+        else if (p.local_iters == 2 && p.lim == LIM_LARSEN) k = k_pass_fh<LIM_LARSEN, 2>;
+        k<<<grd, blk, 0, s>>>(L, f.sp, f.ah2, f.jh2, f.phi, f.phlo, f.D, colour, p.lim, (float)p.larsen_n,
+                              (float)p.omega, (float)p.inv2h, (float)p.floor_, p.local_iters);
+        break;
+    }
     case FAM_F64:
         k_pass_d<<<grd, blk, 0, s>>>(L, f.sp64, f.ah264, f.jh264, f.phi64, f.D64, colour, p.lim, p.larsen_n,
                                     p.omega, p.inv2h, p.floor_, p.local_iters);
@@ -932,7 +1003,7 @@ cudaError_t launch_residual(Family fam, const Layout &L, const Fields &f, const 
         k_fresh_D_d<<<grd, blk, 0, s>>>(L, f.sp64, f.phi64, f.Df64, p.lim, p.larsen_n, p.inv2h, p.floor_);
         k_residual_d<<<grd, blk, 0, s>>>(L, f.ah264, f.jh264, f.phi64, f.Df64, f.D64, margin, f.partials);
     } else {
-        const float *lo = fam == FAM_FF ? f.phlo : nullptr;
+        const float *lo = fam == FAM_F32 ? nullptr : f.phlo;
         k_fresh_D_f<<<grd, blk, 0, s>>>(L, f.sp, f.phi, lo, f.Df, p.lim, (float)p.larsen_n, (float)p.inv2h,
                                         (float)p.floor_);
         k_residual_f<<<grd, blk, 0, s>>>(L, f.ah2, f.jh2, f.phi, lo, f.Df, f.D, margin, f.partials);

@@ -75,7 +75,7 @@ def test_one_iteration_fp64_matches_oracle(limiter, local):
     assert rel_max(D, ref.D) <= 1e-12
 
 
-@pytest.mark.parametrize("precision,tol", [("fp32", 3e-6), ("mixed", 3e-6)])
+@pytest.mark.parametrize("precision,tol", [("fp32", 3e-6), ("mixed", 3e-6), ("pair", 3e-6)])
 @pytest.mark.parametrize("limiter", ["lp", "kershaw", "larsen"])
 def test_one_iteration_single_matches_oracle(precision, tol, limiter):
     sig, alb, j, h = random_case((16, 12, 20), 5)
