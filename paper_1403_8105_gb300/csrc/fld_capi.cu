@@ -316,8 +316,6 @@ fld_status check_params(const fld_grid_s *g, const fld_solve_params *p) {
     return FLD_OK;
 }
 
-fld_grid_s *as_grid(fld_grid g) { return g; }
-
 fld_status enter(fld_grid g) {
     if (!g) return fail(FLD_ERR_INVALID_ARG, "grid is NULL");
     FLD_CK(cudaSetDevice(g->device));

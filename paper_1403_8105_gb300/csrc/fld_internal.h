@@ -106,7 +106,6 @@ cudaError_t launch_residual_batch(const BatchDesc *descs, const int *cta_grid, i
                                   const int *res_count, double *partials, double *result, int lim, int margin,
                                   cudaStream_t s);
 // Pass / residual grid dimensions of a layout (CTAs = x * y * nz).
-void pass_dims(const Layout &L, int *bx, int *by);
 void residual_dims(const Layout &L, int *bx, int *by);
 
 // Sets the thread-local text that fld_last_error() returns.

@@ -295,27 +295,14 @@ __device__ __forceinline__ float ff_den(const FFTerms &t, float ah, float Dp) {
     return __fadd_rn(__fadd_rn(ah, 3.0f * Dp), 0.5f * t.C);
 }
 
-// Plain single-precision pass (the bulk sweeps), for the cell of thread
-// (t, J, K).  LIM < 0 and ROUNDS = 0 select the limiter and the number of
-// local rounds at run time; the common cases are compiled with both fixed.
+// Arithmetic of one FP32 point update from its gathered values: the
+// neighbours' phi and D, its own phi and medium; returns the new phi and D.
 template <int LIM, int ROUNDS>
-__device__ __forceinline__ void pass_f32_body(const Layout &L, const float *__restrict__ sp,
-                                              const float *__restrict__ ah2, const float *__restrict__ jh2,
-                                              float *__restrict__ phi, float *__restrict__ D, int colour, int t,
-                                              int J, int K, int lim_rt, float larsen_n, float omega, float inv2h,
-                                              float floor_, int rounds_rt) {
+__device__ __forceinline__ void cell_f32(float p0, const float ps[6], const float Ds[6], float s_, float ah, float jj,
+                                         int lim_rt, float larsen_n, float omega, float inv2h, float floor_,
+                                         int rounds_rt, float &phi_new, float &D_new) {
     const int lim = LIM >= 0 ? LIM : lim_rt;
     const int local_iters = ROUNDS > 0 ? ROUNDS : rounds_rt;
-    Nbrs o;
-    if (J > L.ny || !pass_cell(L, colour, t, J, K, o)) return;
-    const float p0 = phi[o.own];
-    float ps[6], Ds[6];
-#pragma unroll
-    for (int s = 0; s < 6; ++s) {
-        ps[s] = phi[o.nb[s]];
-        Ds[s] = D[o.nb[s]];
-    }
-    const float s_ = sp[o.own], ah = ah2[o.own], jj = jh2[o.own];
     const float gx = ps[1] - ps[0], gy = ps[3] - ps[2], gz = ps[5] - ps[4];
     const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
     const float g = g2 > 0.0f ? g2 * rsqrtf(g2) * inv2h : 0.0f;     // |grad phi| (Eq. 34)
@@ -339,44 +326,115 @@ __device__ __forceinline__ void pass_f32_body(const Layout &L, const float *__re
         Dp = limiter_fast(lim, larsen_n, R) * inv_sp;                          // Eq. 33
         delta = __fdividef(fmaf(0.5f * Dp, A, base), fmaf(3.0f, Dp, den0));   // Eq. 32
     }
-    phi[o.own] = fmaf(omega, delta, p0);                                       // Eq. 36
-    D[o.own] = Dp;
+    phi_new = fmaf(omega, delta, p0);                                          // Eq. 36
+    D_new = Dp;
 }
 
+// Two adjacent unknowns t, t+1 (t even) of one colour in row (J, K) per
+// thread: in the colour-split layout they are one aligned float2 of every
+// field, their x-neighbours three consecutive elements of the other colour's
+// row and their y/z-neighbours a float2 one row/plane away.
+struct Pair {
+    int own, xv, ym, yp, zm, zp;              // offsets of the float2s (own colour at own, the other at the rest)
+    bool first, second;                       // which of the two cells are unknowns
+    bool left;                                // x-neighbours at xv-1, xv, xv+1 (else xv, xv+1, xv+2)
+};
+
+__device__ __forceinline__ void pair_cells(const Layout &L, int c, int t, int J, int K, Pair &q) {
+    const int par = (J + K + 1 + c) & 1;
+    const int I0 = 2 * t + 2 - par;                 // padded I of cell t
+    q.first = I0 <= L.nx;
+    q.second = I0 + 2 <= L.nx;
+    const int row = (K * L.py + J) * L.hpx + kXoff + 1;   // element of the row's first unknown
+    const int ob = (1 - c) * L.cs;
+    q.own = c * L.cs + row + t;
+    q.left = par == 1;                              // x-neighbours of cell t: (I0 - 1) and (I0 + 1)
+    q.xv = ob + row + t;
+    q.ym = ob + row - L.hpx + t;
+    q.yp = ob + row + L.hpx + t;
+    q.zm = ob + row - L.hpx * L.py + t;
+    q.zp = ob + row + L.hpx * L.py + t;
+}
+
+__device__ __forceinline__ float2 ld2(const float *__restrict__ p, int off) {
+    return *reinterpret_cast<const float2 *>(p + off);
+}
+
+// Gather the six neighbours of the two cells of a pair from one field.
+__device__ __forceinline__ void gather_pair(const float *__restrict__ f, const Pair &q, float v0[6], float v1[6]) {
+    const float2 xv = ld2(f, q.xv);
+    const float xe = q.left ? f[q.xv - 1] : f[q.xv + 2];
+    if (q.left) {
+        v0[0] = xe; v0[1] = xv.x; v1[0] = xv.x; v1[1] = xv.y;
+    } else {
+        v0[0] = xv.x; v0[1] = xv.y; v1[0] = xv.y; v1[1] = xe;
+    }
+    const float2 ym = ld2(f, q.ym), yp = ld2(f, q.yp), zm = ld2(f, q.zm), zp = ld2(f, q.zp);
+    v0[2] = ym.x; v0[3] = yp.x; v0[4] = zm.x; v0[5] = zp.x;
+    v1[2] = ym.y; v1[3] = yp.y; v1[4] = zm.y; v1[5] = zp.y;
+}
+
+// Programmatic dependent launch (PTX griddepcontrol): a pass lets the next
+// grid in its stream be scheduled as soon as all of its own CTAs are running,
+// and waits for the preceding grid to complete (with its writes visible)
+// before it reads phi, phi_lo or D.  The medium (sigma', sigma_a' h^2, j h^2)
+// is written only by earlier, fully completed kernels and is loaded before
+// the wait.  Without the launch attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_launch_dependents() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// Single-precision pass (the bulk sweeps), two unknowns per thread (40
+// registers: six CTAs per SM).
 template <int LIM, int ROUNDS>
-__global__ void __launch_bounds__(256) k_pass_f32(Layout L, const float *__restrict__ sp,
-                                                  const float *__restrict__ ah2, const float *__restrict__ jh2,
-                                                  float *__restrict__ phi, float *__restrict__ D, int colour,
-                                                  int lim_rt, float larsen_n, float omega, float inv2h, float floor_,
-                                                  int rounds_rt) {
-    pass_f32_body<LIM, ROUNDS>(L, sp, ah2, jh2, phi, D, colour, blockIdx.x * blockDim.x + threadIdx.x,
-                               blockIdx.y * blockDim.y + threadIdx.y + 1, blockIdx.z + 1, lim_rt, larsen_n, omega,
-                               inv2h, floor_, rounds_rt);
+__global__ void __launch_bounds__(256, 6) k_pass2_f32(Layout L, const float *__restrict__ sp,
+                                                   const float *__restrict__ ah2, const float *__restrict__ jh2,
+                                                   float *__restrict__ phi, float *__restrict__ D, int colour,
+                                                   int lim_rt, float larsen_n, float omega, float inv2h,
+                                                   float floor_, int rounds_rt) {
+    pdl_launch_dependents();
+    const int t = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int J = blockIdx.y * blockDim.y + threadIdx.y + 1, K = blockIdx.z + 1;
+    if (J > L.ny) return;
+    Pair q;
+    pair_cells(L, colour, t, J, K, q);
+    if (!q.first) return;
+    const float2 s2 = ld2(sp, q.own), a2 = ld2(ah2, q.own), j2 = ld2(jh2, q.own);
+    pdl_wait();
+    float ps0[6], ps1[6], Ds0[6], Ds1[6];
+    gather_pair(phi, q, ps0, ps1);
+    gather_pair(D, q, Ds0, Ds1);
+    const float2 p0 = ld2(phi, q.own);
+    float pn0, dn0, pn1, dn1;
+    cell_f32<LIM, ROUNDS>(p0.x, ps0, Ds0, s2.x, a2.x, j2.x, lim_rt, larsen_n, omega, inv2h, floor_, rounds_rt, pn0,
+                          dn0);
+    if (q.second) {
+        cell_f32<LIM, ROUNDS>(p0.y, ps1, Ds1, s2.y, a2.y, j2.y, lim_rt, larsen_n, omega, inv2h, floor_, rounds_rt,
+                              pn1, dn1);
+        *reinterpret_cast<float2 *>(phi + q.own) = make_float2(pn0, pn1);
+        *reinterpret_cast<float2 *>(D + q.own) = make_float2(dn0, dn1);
+    } else {
+        phi[q.own] = pn0;          // the element after the last unknown is a ghost: left untouched
+        D[q.own] = dn0;
+    }
 }
 
 // Middle pass: phi kept as a hi/lo pair (no storage floor) but the update
 // summed in plain FP32 with the approximate D of the bulk sweeps -- about the
 // cost of the FP32 pass, reaching residuals a few times above the
-// float-float pass's.
+// float-float pass's.  cell_fh is the arithmetic of one point; k_pass2_fh
+// updates two unknowns per thread (48 registers for five CTAs per SM).
 template <int LIM, int ROUNDS>
-__device__ __forceinline__ void pass_fh_body(const Layout &L, const float *__restrict__ sp,
-                                             const float *__restrict__ ah2, const float *__restrict__ jh2,
-                                             float *__restrict__ phi, float *__restrict__ phlo,
-                                             float *__restrict__ D, int colour, int t, int J, int K, int lim_rt,
-                                             float larsen_n, float omega, float inv2h, float floor_,
-                                             int rounds_rt) {
+__device__ __forceinline__ void cell_fh(float p0, float p0lo, const float ps[6], const float ls[6],
+                                        const float Ds[6], float s_, float ah, float jj, int lim_rt, float larsen_n,
+                                        float omega, float inv2h, float floor_, int rounds_rt, float &hi_new,
+                                        float &lo_new, float &D_new) {
     const int lim = LIM >= 0 ? LIM : lim_rt;
     const int local_iters = ROUNDS > 0 ? ROUNDS : rounds_rt;
-    Nbrs o;
-    if (J > L.ny || !pass_cell(L, colour, t, J, K, o)) return;
-    const float p0 = phi[o.own], p0lo = phlo[o.own];
-    float d[6], Ds[6];
+    float d[6];
 #pragma unroll
-    for (int s = 0; s < 6; ++s) {
-        d[s] = (phi[o.nb[s]] - p0) + (phlo[o.nb[s]] - p0lo);   // phi_s - phi_p
-        Ds[s] = D[o.nb[s]];
-    }
-    const float s_ = sp[o.own], ah = ah2[o.own], jj = jh2[o.own];
+    for (int s = 0; s < 6; ++s) d[s] = (ps[s] - p0) + (ls[s] - p0lo);   // phi_s - phi_p
     const float gx = d[1] - d[0], gy = d[3] - d[2], gz = d[5] - d[4];
     const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
     const float g = g2 > 0.0f ? g2 * rsqrtf(g2) * inv2h : 0.0f;
@@ -400,20 +458,45 @@ __device__ __forceinline__ void pass_fh_body(const Layout &L, const float *__res
         delta = __fdividef(fmaf(0.5f * Dp, A, base), fmaf(3.0f, Dp, den0));
     }
     const ff nw = ff_add_f(ff{p0, p0lo}, __fmul_rn(omega, delta));
-    phi[o.own] = nw.hi;
-    phlo[o.own] = nw.lo;
-    D[o.own] = Dp;
+    hi_new = nw.hi;
+    lo_new = nw.lo;
+    D_new = Dp;
 }
 
 template <int LIM, int ROUNDS>
-__global__ void __launch_bounds__(256) k_pass_fh(Layout L, const float *__restrict__ sp,
-                                                 const float *__restrict__ ah2, const float *__restrict__ jh2,
-                                                 float *__restrict__ phi, float *__restrict__ phlo,
-                                                 float *__restrict__ D, int colour, int lim_rt, float larsen_n,
-                                                 float omega, float inv2h, float floor_, int rounds_rt) {
-    pass_fh_body<LIM, ROUNDS>(L, sp, ah2, jh2, phi, phlo, D, colour, blockIdx.x * blockDim.x + threadIdx.x,
-                              blockIdx.y * blockDim.y + threadIdx.y + 1, blockIdx.z + 1, lim_rt, larsen_n, omega,
-                              inv2h, floor_, rounds_rt);
+__global__ void __launch_bounds__(256, 5) k_pass2_fh(Layout L, const float *__restrict__ sp,
+                                                  const float *__restrict__ ah2, const float *__restrict__ jh2,
+                                                  float *__restrict__ phi, float *__restrict__ phlo,
+                                                  float *__restrict__ D, int colour, int lim_rt, float larsen_n,
+                                                  float omega, float inv2h, float floor_, int rounds_rt) {
+    pdl_launch_dependents();
+    const int t = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int J = blockIdx.y * blockDim.y + threadIdx.y + 1, K = blockIdx.z + 1;
+    if (J > L.ny) return;
+    Pair q;
+    pair_cells(L, colour, t, J, K, q);
+    if (!q.first) return;
+    const float2 s2 = ld2(sp, q.own), a2 = ld2(ah2, q.own), j2 = ld2(jh2, q.own);
+    pdl_wait();
+    float ps0[6], ps1[6], ls0[6], ls1[6], Ds0[6], Ds1[6];
+    gather_pair(phi, q, ps0, ps1);
+    gather_pair(phlo, q, ls0, ls1);
+    gather_pair(D, q, Ds0, Ds1);
+    const float2 p0 = ld2(phi, q.own), l0 = ld2(phlo, q.own);
+    float h0, lo0, d0, h1, lo1, d1;
+    cell_fh<LIM, ROUNDS>(p0.x, l0.x, ps0, ls0, Ds0, s2.x, a2.x, j2.x, lim_rt, larsen_n, omega, inv2h, floor_,
+                         rounds_rt, h0, lo0, d0);
+    if (q.second) {
+        cell_fh<LIM, ROUNDS>(p0.y, l0.y, ps1, ls1, Ds1, s2.y, a2.y, j2.y, lim_rt, larsen_n, omega, inv2h, floor_,
+                             rounds_rt, h1, lo1, d1);
+        *reinterpret_cast<float2 *>(phi + q.own) = make_float2(h0, h1);
+        *reinterpret_cast<float2 *>(phlo + q.own) = make_float2(lo0, lo1);
+        *reinterpret_cast<float2 *>(D + q.own) = make_float2(d0, d1);
+    } else {
+        phi[q.own] = h0;
+        phlo[q.own] = lo0;
+        D[q.own] = d0;
+    }
 }
 
 // Float-float correction pass: phi kept as a hi/lo pair, S summed so the
@@ -430,6 +513,8 @@ __device__ __forceinline__ void pass_ff_body(const Layout &L, const float *__res
     const int local_iters = ROUNDS > 0 ? ROUNDS : rounds_rt;
     Nbrs o;
     if (J > L.ny || !pass_cell(L, colour, t, J, K, o)) return;
+    const float s_ = sp[o.own], ah = ah2[o.own], jj = jh2[o.own];
+    pdl_wait();
     const float p0 = phi[o.own], p0lo = phlo[o.own];
     float ps[6], ls[6], Ds[6];
 #pragma unroll
@@ -438,7 +523,6 @@ __device__ __forceinline__ void pass_ff_body(const Layout &L, const float *__res
         ls[s] = phlo[o.nb[s]];
         Ds[s] = D[o.nb[s]];
     }
-    const float s_ = sp[o.own], ah = ah2[o.own], jj = jh2[o.own];
     const FFTerms T = ff_terms(p0, p0lo, ps, ls, Ds, ah, jj);
     const float gmax = grad_floor_f(T.gx, T.gy, T.gz, inv2h, floor_);
     float delta = 0.0f, Dp = 0.0f;
@@ -462,6 +546,7 @@ __global__ void __launch_bounds__(256) k_pass_ff(Layout L, const float *__restri
                                                  float *__restrict__ phi, float *__restrict__ phlo,
                                                  float *__restrict__ D, int colour, int lim_rt, float larsen_n,
                                                  float omega, float inv2h, float floor_, int rounds_rt) {
+    pdl_launch_dependents();
     pass_ff_body<LIM, ROUNDS>(L, sp, ah2, jh2, phi, phlo, D, colour, blockIdx.x * blockDim.x + threadIdx.x,
                               blockIdx.y * blockDim.y + threadIdx.y + 1, blockIdx.z + 1, lim_rt, larsen_n, omega,
                               inv2h, floor_, rounds_rt);
@@ -862,6 +947,12 @@ inline dim3 pass_grid(const Layout &L, dim3 blk) {
     return dim3((half + blk.x - 1) / blk.x, (L.ny + blk.y - 1) / blk.y, L.nz);
 }
 
+// two unknowns per thread (k_pass2_*): ceil(half / 2) threads per half row
+inline dim3 pass2_grid(const Layout &L, dim3 blk) {
+    const int pairs = ((L.nx + 1) / 2 + 1) / 2;
+    return dim3((pairs + blk.x - 1) / blk.x, (L.ny + blk.y - 1) / blk.y, L.nz);
+}
+
 inline dim3 vox_block() { return dim3(32, 8, 1); }
 inline dim3 vox_grid(const Layout &L) {
     return dim3((L.nx + 31) / 32, (L.ny + 7) / 8, L.nz);
@@ -926,37 +1017,52 @@ cudaError_t launch_d_to_f(const Layout &L, const double *src, float *hi, float *
     return cudaGetLastError();
 }
 
+// Launch with programmatic stream serialisation: the kernel may be scheduled
+// while the preceding grid in the stream finishes (see pdl_wait).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*k)(KArgs...), dim3 grd, dim3 blk, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grd;
+    cfg.blockDim = blk;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 cudaError_t launch_pass(Family fam, const Layout &L, const Fields &f, const PassParams &p, int colour,
                         cudaStream_t s) {
     const dim3 blk(32, 8, 1);
     const dim3 grd = pass_grid(L, blk);
+    const dim3 grd2 = pass2_grid(L, blk);
     switch (fam) {
     case FAM_F32: {
-        auto k = k_pass_f32<-1, 0>;
-        if (p.local_iters == 2 && p.lim == LIM_LP) k = k_pass_f32<LIM_LP, 2>;
-        else if (p.local_iters == 2 && p.lim == LIM_KERSHAW) k = k_pass_f32<LIM_KERSHAW, 2>;
-        else if (p.local_iters == 2 && p.lim == LIM_LARSEN) k = k_pass_f32<LIM_LARSEN, 2>;
-        k<<<grd, blk, 0, s>>>(L, f.sp, f.ah2, f.jh2, f.phi, f.D, colour, p.lim, (float)p.larsen_n, (float)p.omega,
-                              (float)p.inv2h, (float)p.floor_, p.local_iters);
-        break;
+        auto k = k_pass2_f32<-1, 0>;
+        if (p.local_iters == 2 && p.lim == LIM_LP) k = k_pass2_f32<LIM_LP, 2>;
+        else if (p.local_iters == 2 && p.lim == LIM_KERSHAW) k = k_pass2_f32<LIM_KERSHAW, 2>;
+        else if (p.local_iters == 2 && p.lim == LIM_LARSEN) k = k_pass2_f32<LIM_LARSEN, 2>;
+        return launch_pdl(k, grd2, blk, s, L, f.sp, f.ah2, f.jh2, f.phi, f.D, colour, p.lim, (float)p.larsen_n,
+                          (float)p.omega, (float)p.inv2h, (float)p.floor_, p.local_iters);
     }
     case FAM_FF: {
         auto k = k_pass_ff<-1, 0>;
         if (p.local_iters == 2 && p.lim == LIM_LP) k = k_pass_ff<LIM_LP, 2>;
         else if (p.local_iters == 2 && p.lim == LIM_KERSHAW) k = k_pass_ff<LIM_KERSHAW, 2>;
         else if (p.local_iters == 2 && p.lim == LIM_LARSEN) k = k_pass_ff<LIM_LARSEN, 2>;
-        k<<<grd, blk, 0, s>>>(L, f.sp, f.ah2, f.jh2, f.phi, f.phlo, f.D, colour, p.lim, (float)p.larsen_n,
-                              (float)p.omega, (float)p.inv2h, (float)p.floor_, p.local_iters);
-        break;
+        return launch_pdl(k, grd, blk, s, L, f.sp, f.ah2, f.jh2, f.phi, f.phlo, f.D, colour, p.lim,
+                          (float)p.larsen_n, (float)p.omega, (float)p.inv2h, (float)p.floor_, p.local_iters);
     }
     case FAM_FH: {
-        auto k = k_pass_fh<-1, 0>;
-        if (p.local_iters == 2 && p.lim == LIM_LP) k = k_pass_fh<LIM_LP, 2>;
-        else if (p.local_iters == 2 && p.lim == LIM_KERSHAW) k = k_pass_fh<LIM_KERSHAW, 2>;
-        else if (p.local_iters == 2 && p.lim == LIM_LARSEN) k = k_pass_fh<LIM_LARSEN, 2>;
-        k<<<grd, blk, 0, s>>>(L, f.sp, f.ah2, f.jh2, f.phi, f.phlo, f.D, colour, p.lim, (float)p.larsen_n,
-                              (float)p.omega, (float)p.inv2h, (float)p.floor_, p.local_iters);
-        break;
+        auto k = k_pass2_fh<-1, 0>;
+        if (p.local_iters == 2 && p.lim == LIM_LP) k = k_pass2_fh<LIM_LP, 2>;
+        else if (p.local_iters == 2 && p.lim == LIM_KERSHAW) k = k_pass2_fh<LIM_KERSHAW, 2>;
+        else if (p.local_iters == 2 && p.lim == LIM_LARSEN) k = k_pass2_fh<LIM_LARSEN, 2>;
+        return launch_pdl(k, grd2, blk, s, L, f.sp, f.ah2, f.jh2, f.phi, f.phlo, f.D, colour, p.lim,
+                          (float)p.larsen_n, (float)p.omega, (float)p.inv2h, (float)p.floor_, p.local_iters);
     }
     case FAM_F64:
         k_pass_d<<<grd, blk, 0, s>>>(L, f.sp64, f.ah264, f.jh264, f.phi64, f.D64, colour, p.lim, p.larsen_n,
@@ -964,12 +1070,6 @@ cudaError_t launch_pass(Family fam, const Layout &L, const Fields &f, const Pass
         break;
     }
     return cudaGetLastError();
-}
-
-void pass_dims(const Layout &L, int *bx, int *by) {
-    const dim3 g = pass_grid(L, dim3(32, 8, 1));
-    *bx = (int)g.x;
-    *by = (int)g.y;
 }
 
 void residual_dims(const Layout &L, int *bx, int *by) {
