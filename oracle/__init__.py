@@ -70,6 +70,8 @@ def _load():
             lib.fldo_limiter.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double]
             lib.fldo_prep.restype = None
             lib.fldo_prep.argtypes = [ctypes.c_long, _fp, _fp, ctypes.c_double, _dp, _dp]
+            lib.fldo_prep_bf16.restype = None
+            lib.fldo_prep_bf16.argtypes = [ctypes.c_long, _fp, _fp, ctypes.c_double, _dp, _dp]
             lib.fldo_rms.restype = ctypes.c_double
             lib.fldo_rms.argtypes = [ctypes.c_long, _dp]
             lib.fldo_rb_iteration.restype = None
@@ -179,8 +181,10 @@ def omega_default(nx: int, ny: int, nz: int) -> float:
 def make_problem(sigma_t: np.ndarray, albedo: np.ndarray, j: np.ndarray, h: float, *,
                  limiter: str = "lp", larsen_n: float = 2.0, omega: float | None = None,
                  sigma_eps: float | None = None, eps: float = EPS, nthreads: int | None = None,
-                 local_iters: int = 1) -> Problem:
-    """Algorithm 1, first three steps: floor sigma, compute sigma_a' and jbar."""
+                 local_iters: int = 1, medium_bf16: bool = False) -> Problem:
+    """Algorithm 1, first three steps: floor sigma, compute sigma_a' and jbar.
+    medium_bf16: sigma' and sigma_a' formed in single precision and rounded
+    to bfloat16 (nearest, ties to even), then used exactly."""
     lib = _load()
     sigma_t = np.ascontiguousarray(sigma_t, dtype=np.float32)
     albedo = np.ascontiguousarray(albedo, dtype=np.float32)
@@ -189,7 +193,8 @@ def make_problem(sigma_t: np.ndarray, albedo: np.ndarray, j: np.ndarray, h: floa
         sigma_eps = sigma_eps_default(nx, ny, nz, h)
     sp = np.empty(sigma_t.shape, dtype=np.float64)
     sa = np.empty(sigma_t.shape, dtype=np.float64)
-    lib.fldo_prep(sigma_t.size, _f(sigma_t), _f(albedo), float(sigma_eps), _d(sp), _d(sa))
+    prep = lib.fldo_prep_bf16 if medium_bf16 else lib.fldo_prep
+    prep(sigma_t.size, _f(sigma_t), _f(albedo), float(sigma_eps), _d(sp), _d(sa))
     jd = np.ascontiguousarray(j, dtype=np.float64)
     jbar = lib.fldo_rms(jd.size, _d(jd))
     if omega is None:

@@ -186,6 +186,37 @@ void fldo_prep(long nvox, const float *sigma_t, const float *albedo, double sigm
     }
 }
 
+/* The same medium stored in bfloat16 (the reduced-precision medium of the
+ * 256^3 runs): sigma' = max(sigma_t, sigma_eps) and sigma_a' = (1 - albedo)
+ * sigma' are formed in single precision, one rounding per operation, and
+ * each is rounded to bfloat16 (8 significant bits), to nearest with ties to
+ * even.  Rounding to 8 bits is a decision taken in floating point, so it is
+ * taken on the same single-precision values the device rounds; the solve
+ * then uses the rounded values exactly. */
+static float bf16_round(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, sizeof u);
+    /* add half an 8-bit ulp (minus one when the kept part is even) and cut */
+    u += 0x7FFFu + ((u >> 16) & 1u);
+    u &= 0xFFFF0000u;
+    memcpy(&x, &u, sizeof x);
+    return x;
+}
+
+void fldo_prep_bf16(long nvox, const float *sigma_t, const float *albedo, double sigma_eps,
+                    double *sp, double *sa)
+{
+    const float seps = (float)sigma_eps;
+    for (long v = 0; v < nvox; ++v) {
+        const float s = sigma_t[v] > seps ? sigma_t[v] : seps;
+        const float one_minus = 1.0f - albedo[v];
+        const float a = one_minus * s;
+        sp[v] = (double)bf16_round(s);
+        sa[v] = (double)bf16_round(a);
+    }
+}
+
 /* jbar = sqrt(mean(j^2)) over the unknowns. */
 double fldo_rms(long nvox, const double *j)
 {
