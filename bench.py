@@ -42,8 +42,11 @@ UNIT = "voxel-updates/s"
 # reads phi, D, sigma', sigma_a' dl^2, j dl^2 and writes phi, D (4 bytes each);
 # the float-float correction sweep also reads and writes the low word of phi.
 BYTES_PER_UPDATE = {"fp32": 28, "fh": 36, "ff": 36}
-KERNEL_NAME = {"fp32": "k_pass_f32 (single-precision red/black pass)",
-               "fh": "k_pass_fh (hi/lo phi, FP32-summed red/black pass)",
+# with the bfloat16 medium the single-precision and hi/lo sweeps read sigma' and
+# sigma_a' in 2 bytes each
+BYTES_PER_UPDATE_BF16 = {"fp32": 24, "fh": 32, "ff": 36}
+KERNEL_NAME = {"fp32": "k_pass2_f32 (single-precision red/black pass, two unknowns per thread)",
+               "fh": "k_pass2_fh (hi/lo phi, FP32-summed red/black pass, two unknowns per thread)",
                "ff": "k_pass_ff (float-float correction pass)"}
 
 
@@ -63,7 +66,14 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample length")
     ap.add_argument("--no-extras", action="store_true", help="skip cpu baseline / 256^3 roofline / e2e")
-    ap.add_argument("--workload", choices=["cloud", "batch", "serve"], default="cloud",
+    ap.add_argument("--c3-n", type=int, default=256, help="c3 workload: edge of the timed solves")
+    ap.add_argument("--c3-set", choices=["one", "diag", "full"], default="diag",
+                    help="c3 workload: (seed, albedo) pairs -- one: (1, 0.95); diag: (1, 0.8), (2, 0.95), "
+                         "(3, 0.99); full: all 9 -- each with the three limiters")
+    ap.add_argument("--c3-limiters", default="lp,kershaw,larsen", help="c3 workload: limiters (comma list)")
+    ap.add_argument("--c3-oracle-n", type=int, default=32,
+                    help="c3 workload: edge of the same-recipe solves compared with the FP64 oracle's fixed point")
+    ap.add_argument("--workload", choices=["cloud", "batch", "serve", "c3"], default="cloud",
                     help="cloud: the 128^3 solve (default); batch: independent solves of uneven size, "
                          "batched in shared launches vs one after another")
     ap.add_argument("--count", type=int, default=16, help="batch workload: number of solves")
@@ -637,6 +647,140 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+C3_SEEDS = (1, 2, 3)
+C3_ALBEDOS = (0.8, 0.95, 0.99)
+C3_LIMITERS = ("lp", "kershaw", "larsen")
+
+
+def c3_cases(which, limiters=C3_LIMITERS):
+    if which == "one":
+        pairs = [(1, 0.95)]
+    elif which == "diag":
+        pairs = list(zip(C3_SEEDS, C3_ALBEDOS))
+    else:
+        pairs = [(s, a) for s in C3_SEEDS for a in C3_ALBEDOS]
+    return [(s, a, lim) for s, a in pairs for lim in limiters]
+
+
+def run_c3(args):
+    """The 256^3 three-limiter runs: fBm clouds with seeds 1-3 and albedo in
+    {0.8, 0.95, 0.99}, Levermore-Pomraning / Kershaw / Larsen (n = 2), unit
+    directional light along -z, sigma' and sigma_a' stored in bfloat16,
+    single-precision sweeps with hi/lo and float-float correction sweeps, to a
+    relative residual of 1e-6.  Per solve: device time of fld_solve (after the
+    bake, grid resident, L2 flushed before), iterations, the library's
+    residual, and the FP64 oracle's own residual of the returned phi on the
+    same rounded medium.  The same recipe at --c3-oracle-n, where the oracle
+    reaches its fixed point (1e-10) in seconds, gives the error of the
+    mixed-precision phi against the oracle per limiter, and the shift of the
+    oracle's phi* caused by rounding the medium to bfloat16."""
+    import numpy as np
+    import torch
+
+    import fld_inputs
+    import oracle
+    import paper_1403_8105_gb300 as fld
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    fld.load(build_if_missing=True)
+    stream = torch.cuda.Stream(device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    cases = c3_cases(args.c3_set, tuple(x for x in args.c3_limiters.split(",") if x))
+
+    def params(lim, n):
+        return fld.params(limiter=lim, larsen_n=2.0, precision="mixed", tol=args.tol, local_iters=2,
+                          check_every=args.check_every if n >= 128 else 32, max_iters=max(args.max_iters, 4000000),
+                          medium_bf16=1)
+
+    def baked_grid(n, seed, albedo):
+        sig, alb = fld_inputs.cloud_medium(n, seed=seed, albedo=albedo)
+        g = fld.Grid(n, n, n, 1.0 / n, stream=stream.cuda_stream)
+        g.set_medium(torch.from_numpy(sig).to(dev), torch.from_numpy(alb).to(dev))
+        g.bake_directional((0.0, 0.0, -1.0), 1.0)
+        return g, sig, alb
+
+    with torch.cuda.stream(stream):
+        for lim in C3_LIMITERS:                    # warm-up: module load, per-limiter kernels
+            g, _, _ = baked_grid(32, 0, 0.9)
+            g.solve(params(lim, 32))
+            g.close()
+        stream.synchronize()
+
+        sampler = ClockSampler(0)
+        sampler.start()
+        rows, total_ms, total_updates, launches = [], 0.0, 0, 0
+        for seed, albedo, lim in cases:
+            n = args.c3_n
+            g, sig, alb = baked_grid(n, seed, albedo)
+            flush.fill_(1.0)
+            stream.synchronize()
+            r = g.solve(params(lim, n))
+            stream.synchronize()
+            phi, D = g.get_state()
+            j = g.get_source().astype(np.float64)
+            g.close()
+            prob = oracle.make_problem(sig, alb, j, 1.0 / n, limiter=lim, larsen_n=2.0, medium_bf16=True)
+            prob.phi, prob.D = phi, D
+            rel_oracle = oracle.residual(prob)[0]
+            total_ms += r.ms
+            total_updates += r.iterations * n ** 3
+            launches += int(r.kernels) + 3
+            rows.append({"seed": seed, "albedo": albedo, "limiter": lim, "status": fld.fld_status_string(r.status),
+                         "time_to_residual_s": r.ms / 1e3, "iterations": r.iterations,
+                         "iterations_by_family": {"fp32": r.iterations_fp32, "fh": r.iterations_mid,
+                                                  "ff": r.iterations_corr},
+                         "rel_residual": r.rel_residual, "rel_residual_oracle_fp64": rel_oracle,
+                         "voxel_updates_per_s": r.iterations * n ** 3 / (r.ms / 1e3),
+                         "min_phi": float(phi[1:-1, 1:-1, 1:-1].min())})
+            print(json.dumps({"c3_case": rows[-1]}), flush=True)
+        clocks = sampler.stop()
+
+        # error against the oracle's fixed point on the same recipe at a size it can solve
+        small = []
+        m = args.c3_oracle_n
+        for seed, albedo, lim in cases:
+            g, sig, alb = baked_grid(m, seed, albedo)
+            r = g.solve(params(lim, m))
+            phi, _ = g.get_state()
+            j = g.get_source().astype(np.float64)
+            g.close()
+            ref, ref_rel = {}, {}
+            for bf in (True, False):
+                prob = oracle.make_problem(sig, alb, j, 1.0 / m, limiter=lim, larsen_n=2.0, local_iters=2,
+                                           medium_bf16=bf)
+                oracle.init_state(prob)
+                _, ref_rel[bf], _ = oracle.solve(prob, tol=1e-10, max_iters=400000, check_every=50)
+                ref[bf] = prob.phi[1:-1, 1:-1, 1:-1]
+            inner = phi[1:-1, 1:-1, 1:-1]
+            l2 = float(np.linalg.norm(inner - ref[True]) / np.linalg.norm(ref[True]))
+            mx = float(np.abs(inner - ref[True]).max() / np.abs(ref[True]).max())
+            quant = float(np.linalg.norm(ref[True] - ref[False]) / np.linalg.norm(ref[False]))
+            small.append({"seed": seed, "albedo": albedo, "limiter": lim, "n": m,
+                          "status": fld.fld_status_string(r.status), "iterations": r.iterations,
+                          "rel_l2_vs_oracle": l2, "rel_max_vs_oracle": mx, "oracle_rel_residual": ref_rel[True],
+                          "bf16_medium_shift_of_phi_star": quant})
+            print(json.dumps({"c3_oracle_case": small[-1]}), flush=True)
+
+    times = [row["time_to_residual_s"] for row in rows]
+    peaks = measured_peaks()
+    line = {
+        "metric": METRIC, "value": total_updates / (total_ms / 1e3), "unit": UNIT, "n_gpus": 1,
+        "steps": len(rows), "warmup": len(C3_LIMITERS), "ms_per_step": total_ms / max(1, len(rows)),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 sweeps, bf16 medium (float-float correction sweeps)", "data": "synthetic",
+        "config": {"workload": f"C3 fBm sphere clouds {args.c3_n}^3, seeds/albedos {args.c3_set}, limiters LP / "
+                               f"Kershaw / Larsen-2, bf16 sigma'/sigma_a', rel. residual {args.tol:g}",
+                   "grid": [args.c3_n] * 3, "l2": "flushed (256 MB write) before every solve",
+                   "parallelism": "1 GPU"},
+        "time_to_residual_s": {"p50": statistics.median(times), "max": max(times)},
+        "cases": rows, "oracle_error_same_recipe": small,
+        "peak_hbm_gbs": peaks["hbm_gbs"] if peaks else None,
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -645,6 +789,8 @@ def main():
         run_batch(args)
     elif args.workload == "serve":
         run_serve(args)
+    elif args.workload == "c3":
+        run_c3(args)
     else:
         run_gpu(args)
 

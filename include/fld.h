@@ -92,11 +92,12 @@ typedef struct {
     int limiter;          /* fld_limiter                                             */
     double larsen_n;      /* n of Larsen-n, > 0 (default 2)                          */
     double omega;         /* SOR factor of Eq. 36, 0 < omega < 2; <= 0 selects
-                             2/(1 + sin(pi/(n+1))) clamped to [1, 1.93], n the
+                             2/(1 + sin(pi/(n+1))) clamped to [1, 1.98], n the
                              largest extent.  fld_solve keeps the state with the
                              best residual and, if the residual turns non-finite
-                             or grows 1000-fold, returns to it with omega - 1
-                             reduced by 3 % (at most 8 times)                        */
+                             or grows 1000-fold (against the best and the initial
+                             residual), returns to it with omega - 1 reduced by
+                             3 % (at most 8 times)                                   */
     int local_iters;      /* rounds of Knudsen -> D_p -> phi' per point before the
                              SOR blend, >= 1.  1 is Algorithm 1 as printed; 2 makes
                              each point's update self-consistent in its own D_p,
@@ -119,6 +120,22 @@ typedef struct {
                              paper's eps*jbar*h and eps*h (Algorithm 1)             */
     double phi_b, D_b;    /* Dirichlet ghost values; < 0 selects eps*jbar*h and
                              eps*h                                                   */
+    int warmup_iters;     /* iterations run with omega = 1 before over-relaxation
+                             starts: over-relaxing the near-zero initial state
+                             diverges for omega above ~1.9 on grids of 192^3 and
+                             more, the same omega is stable after a short warm-up.
+                             -1 (default): 4 x the largest extent on a cold start,
+                             0 with warm_start; 0: none; > 0: that many           */
+    int medium_bf16;      /* 1: store sigma' and sigma_a' in bfloat16 (8 significant
+                             bits) for the single-precision and hi/lo sweeps, which
+                             then read 24 instead of 28 bytes per update.  Both are
+                             formed in single precision and rounded to nearest
+                             (ties to even); every kernel of the solve, including
+                             the FP64 residual and the float-float and FP64
+                             sweeps, uses the rounded values, so the fixed point
+                             is that of the rounded medium.  The rounding moves
+                             the medium by at most 2^-8 relative.  0 (default):
+                             the single-precision medium.  Not in the paper.  */
 } fld_solve_params;
 
 typedef struct {
@@ -143,7 +160,8 @@ typedef struct {
 
 /* Fill *p with the defaults: LP limiter, Larsen n = 2, omega auto,
  * local_iters 2, tol 1e-6, max_iters 1000000, check_every 64, paper sigma_eps
- * and eps, MIXED precision, margin 0, cold start, paper initial/ghost values. */
+ * and eps, MIXED precision, margin 0, cold start, paper initial/ghost values,
+ * automatic warm-up, single-precision medium. */
 void fld_default_params(fld_solve_params *p);
 
 /* Create a grid of nx*ny*nz unknowns (each >= 1) of edge h > 0 on the

@@ -47,7 +47,8 @@ class SolveParams(ctypes.Structure):
         ("check_every", ctypes.c_int), ("sigma_eps", ctypes.c_double), ("eps", ctypes.c_double),
         ("precision", ctypes.c_int), ("fp32_switch", ctypes.c_double), ("residual_margin", ctypes.c_int),
         ("warm_start", ctypes.c_int), ("phi0", ctypes.c_double), ("D0", ctypes.c_double),
-        ("phi_b", ctypes.c_double), ("D_b", ctypes.c_double),
+        ("phi_b", ctypes.c_double), ("D_b", ctypes.c_double), ("warmup_iters", ctypes.c_int),
+        ("medium_bf16", ctypes.c_int),
     ]
 
 

@@ -46,8 +46,13 @@ constexpr double kFloorNoEmission = 1e-30;   // floor of Eq. 35 when jbar = 0
 constexpr int kStallChecks = 48;              // checks without a new minimum before giving up
 constexpr int kSwitchChecks = 24;             // ... before single precision hands over (MIXED)
 constexpr double kGuardGrowth = 1e3;          // residual growth (vs the best) read as divergence
+constexpr int kSlowDivergeChecks = 32;        // ... or checks without a new minimum while above 4x the best
+constexpr int kFlatWindow = 8;                // single-precision floor: checks compared ...
+constexpr double kFlatGain = 0.05;            // ... and the smallest relative decrease that is progress
+constexpr double kFlatBelow = 0.1;            // ... below this fraction of the starting residual
 constexpr int kMaxBackoffs = 8;               // omega reductions before reporting divergence
-constexpr double kOmegaMax = 1.93;            // upper clamp of the automatic omega
+constexpr double kOmegaMax = 1.98;            // upper clamp of the automatic omega
+constexpr int kWarmupPerEdge = 4;             // automatic warm-up: iterations per voxel of the largest extent
 
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
@@ -58,7 +63,7 @@ struct GraphEntry {
 
 bool same_params(const PassParams &a, const PassParams &b) {
     return a.lim == b.lim && a.local_iters == b.local_iters && a.larsen_n == b.larsen_n && a.omega == b.omega &&
-           a.inv2h == b.inv2h && a.floor_ == b.floor_;
+           a.inv2h == b.inv2h && a.floor_ == b.floor_ && a.bf16 == b.bf16 && a.h2 == b.h2;
 }
 
 }  // namespace
@@ -77,6 +82,7 @@ struct fld_grid_s {
     long long version = 1;          // bumps when medium or source change
     long long prepared_f = 0, prepared_d = 0;
     double prepared_seps_f = -1.0, prepared_seps_d = -1.0;
+    int prepared_bf16_f = -1, prepared_bf16_d = -1;   // medium rounding of the prepared fields
     double jbar = 0.0;
     long long jbar_version = 0;
     bool valid_float = false, valid_d = false;   // which family holds the state
@@ -108,6 +114,22 @@ fld_status ensure_f64(fld_grid_s *g) {
     return FLD_OK;
 }
 
+// bfloat16 copies of sigma' and sigma_a' (medium_bf16).
+fld_status ensure_bf16(fld_grid_s *g) {
+    if (g->f.spb) return FLD_OK;
+    const size_t bytes = sizeof(uint16_t) * (size_t)g->L.total;
+    uint16_t **ptrs[2] = {&g->f.spb, &g->f.sab};
+    for (uint16_t **p : ptrs) {
+        cudaError_t e = cudaMalloc((void **)p, bytes);
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(FLD_ERR_OOM, "cudaMalloc of the bfloat16 medium failed");
+        }
+        FLD_CK(cudaMemsetAsync(*p, 0, bytes, g->stream));
+    }
+    return FLD_OK;
+}
+
 // sigma_eps = 1e-3 / L with L the largest grid extent (Sec. 5), unless given.
 double sigma_eps_of(const fld_grid_s *g, const fld_solve_params *p) {
     if (p->sigma_eps > 0.0) return p->sigma_eps;
@@ -126,6 +148,36 @@ double omega_of(const fld_grid_s *g, const fld_solve_params *p) {
     if (w < 1.0) w = 1.0;
     if (w > kOmegaMax) w = kOmegaMax;
     return w;
+}
+
+// Cold starts relax with omega = 1 for their first iterations.  Over-relaxing
+// the paper's near-zero initial state blows up within a few hundred sweeps
+// (omega 1.95 at 128^3, 1.93 at 192^3 and 256^3, in single and double
+// precision alike), while the same omega, and the Laplacian estimate above
+// it, stays stable once the first sweeps have spread the source.
+int warmup_of(const fld_grid_s *g, const fld_solve_params *p) {
+    if (p->warmup_iters >= 0) return p->warmup_iters;
+    if (p->warm_start) return 0;
+    int n = g->nx;
+    if (g->ny > n) n = g->ny;
+    if (g->nz > n) n = g->nz;
+    return kWarmupPerEdge * n;
+}
+
+// Length of the next block of iterations: check_every, cut at the end of the
+// warm-up and at max_iters.
+int block_len(int it, int check_every, int max_iters, int warm) {
+    int k = check_every;
+    if (it < warm && k > warm - it) k = warm - it;
+    if (k > max_iters - it) k = max_iters - it;
+    return k;
+}
+
+// Pass parameters of a block starting at iteration `it`.
+PassParams block_params(const PassParams &pp, int it, int warm) {
+    PassParams q = pp;
+    if (it < warm) q.omega = 1.0;
+    return q;
 }
 
 fld_status read_result(fld_grid_s *g, double out[2]) {
@@ -153,21 +205,25 @@ fld_status prepare(fld_grid_s *g, const fld_solve_params *p, Family fam) {
     if (st != FLD_OK) return st;
     const double seps = sigma_eps_of(g, p);
     const double h2 = g->h * g->h;
+    const int bf = p->medium_bf16 ? 1 : 0;
     if (fam == FAM_F64) {
         st = ensure_f64(g);
         if (st != FLD_OK) return st;
-        if (g->prepared_d != g->version || g->prepared_seps_d != seps) {
-            FLD_CK(launch_prep_d(g->L, g->f, seps, h2, g->stream));
+        if (g->prepared_d != g->version || g->prepared_seps_d != seps || g->prepared_bf16_d != bf) {
+            FLD_CK(launch_prep_d(g->L, g->f, seps, h2, bf != 0, g->stream));
             g->kernels += 1;
             g->prepared_d = g->version;
             g->prepared_seps_d = seps;
+            g->prepared_bf16_d = bf;
         }
     } else {
-        if (g->prepared_f != g->version || g->prepared_seps_f != seps) {
-            FLD_CK(launch_prep_f(g->L, g->f, (float)seps, (float)h2, g->stream));
+        if (bf && (st = ensure_bf16(g)) != FLD_OK) return st;
+        if (g->prepared_f != g->version || g->prepared_seps_f != seps || g->prepared_bf16_f != bf) {
+            FLD_CK(launch_prep_f(g->L, g->f, (float)seps, (float)h2, bf != 0, g->stream));
             g->kernels += 1;
             g->prepared_f = g->version;
             g->prepared_seps_f = seps;
+            g->prepared_bf16_f = bf;
         }
     }
     return FLD_OK;
@@ -182,6 +238,8 @@ PassParams pass_params(const fld_grid_s *g, const fld_solve_params *p) {
     q.inv2h = 1.0 / (2.0 * g->h);
     const double eps = p->eps > 0.0 ? p->eps : 1e-20;
     q.floor_ = g->jbar > 0.0 ? eps * g->jbar : kFloorNoEmission;
+    q.bf16 = p->medium_bf16 ? 1 : 0;
+    q.h2 = g->h * g->h;
     return q;
 }
 
@@ -312,6 +370,8 @@ fld_status check_params(const fld_grid_s *g, const fld_solve_params *p) {
         return fail(FLD_ERR_INVALID_ARG, "unknown precision");
     if (p->local_iters > 64) return fail(FLD_ERR_INVALID_ARG, "local_iters must be <= 64");
     if (p->residual_margin < 0) return fail(FLD_ERR_INVALID_ARG, "residual_margin must be >= 0");
+    if (p->medium_bf16 != 0 && p->medium_bf16 != 1) return fail(FLD_ERR_INVALID_ARG, "medium_bf16 must be 0 or 1");
+    if (p->warmup_iters < -1) return fail(FLD_ERR_INVALID_ARG, "warmup_iters must be >= -1");
     (void)g;
     return FLD_OK;
 }
@@ -381,25 +441,57 @@ struct Controller {
     double tol = 1e-6, sw = 2e-5;
     Family fam = FAM_F32;
     double best = INFINITY;   // best residual after at least one block
+    double initial = INFINITY;
     int since_best = 0;       // checks without a new minimum
     int backoffs = 0;
+    double recent[kFlatWindow + 1] = {};   // residuals of the last checks of this phase
+    int nrecent = 0;
 
-    void begin_phase() { since_best = 0; }
+    void begin_phase() {
+        since_best = 0;
+        nrecent = 0;
+    }
+    // End of the warm-up at omega = 1: the over-relaxed iteration starts
+    // from here like a new solve (its first blocks may sit above the warm-up's
+    // residual while the higher omega settles).
+    Action restart(double rel) {
+        best = INFINITY;
+        begin_phase();
+        return first(rel);
+    }
+    // The residual has reached a floor (of single precision, or of an
+    // over-relaxed cycle): it sits at its best, an order of magnitude below
+    // where the (over-relaxed) iteration started, and fell by less than
+    // kFlatGain over the last kFlatWindow checks.  (Right after omega rises
+    // the residual also hovers, but near its start.)
+    bool flat(double rel) {
+        recent[nrecent % (kFlatWindow + 1)] = rel;
+        ++nrecent;
+        if (nrecent <= kFlatWindow) return false;
+        const double then = recent[(nrecent - 1 - kFlatWindow) % (kFlatWindow + 1)];
+        return rel > (1.0 - kFlatGain) * then && rel < 1.1 * best && rel < kFlatBelow * initial;
+    }
     // First check (before any iteration): the state is kept as the fallback of
     // the safeguard, but progress is measured from the first block onwards
     // (SOR's early transient may sit above the initial residual for a while).
-    Action first(double rel) const {
+    Action first(double rel) {
+        initial = rel;
         if (rel <= tol) return ACT_CONVERGED;
         if (!isfinite(rel)) return ACT_DIVERGED;
         return ACT_SAVE;
     }
     // After a block of iterations.
     Action next(double rel, double omega) {
-        const bool diverging = !isfinite(rel) || rel > kGuardGrowth * best || (since_best >= 16 && rel > 2.0 * best);
+        // growth is measured against the initial residual too, so a first
+        // block that blows up is not taken for the best state
+        const double ref = best < initial ? best : initial;
+        const bool diverging = !isfinite(rel) || rel > kGuardGrowth * ref ||
+                               (since_best >= kSlowDivergeChecks && rel > 4.0 * best);
         if (diverging) {
             if (backoffs >= kMaxBackoffs || omega <= 1.0) return ACT_DIVERGED;
             ++backoffs;
             since_best = 0;
+            nrecent = 0;
             return ACT_RESTORE;
         }
         if (rel <= tol) return ACT_CONVERGED;
@@ -411,20 +503,35 @@ struct Controller {
         } else {
             ++since_best;
         }
+        const bool no_progress = since_best >= kSwitchChecks;
+        // No new minimum for a while although the residual never fell an
+        // order of magnitude below where the over-relaxed iteration started:
+        // that is omega cycling the nonlinear iteration (seen with omega
+        // 1.97 at 128^3), not a precision floor -- return to the best state
+        // with a smaller omega.
+        if (no_progress && omega > 1.0 && rel >= kFlatBelow * initial && backoffs < kMaxBackoffs) {
+            ++backoffs;
+            since_best = 0;
+            nrecent = 0;
+            return ACT_RESTORE;
+        }
         // single precision has done what it can (Sec. 6.2: ~1e-4 is its limit):
         // continue with phi as a hi/lo pair, first with FP32-summed updates,
         // then with float-float sums near the tolerance
-        if (precision == FLD_PREC_MIXED && fam == FAM_F32 && (rel <= sw || since_best >= kSwitchChecks))
+        const bool at_floor = flat(rel);
+        if (precision == FLD_PREC_MIXED && fam == FAM_F32 && (rel <= sw || no_progress || at_floor))
             return ACT_SWITCH;
-        if (precision == FLD_PREC_MIXED && fam == FAM_FH && (rel <= 3.0 * tol || since_best >= kSwitchChecks))
+        if (precision == FLD_PREC_MIXED && fam == FAM_FH && (rel <= 3.0 * tol || no_progress || at_floor))
             return ACT_SWITCH;
-        // The float-float and FP64 sweeps reach residuals near 1e-7; stalling
-        // far above the tolerance there means over-relaxation is cycling, not
-        // that the arithmetic is exhausted: back off omega.
-        if ((fam == FAM_FF || fam == FAM_F64) && tol > 0.0 && since_best >= kSwitchChecks && best > 100.0 * tol) {
+        // The float-float and FP64 sweeps reach residuals near 1e-7; a floor
+        // above the tolerance there is the over-relaxed nonlinear iteration
+        // cycling (seen from omega ~1.95 at 128^3), not the arithmetic: back
+        // off omega, which collapses it.
+        if ((fam == FAM_FF || fam == FAM_F64) && tol > 0.0 && (no_progress || at_floor) && best > tol) {
             if (backoffs >= kMaxBackoffs || omega <= 1.0) return ACT_STALLED;
             ++backoffs;
             since_best = 0;
+            nrecent = 0;
             return ACT_RESTORE;
         }
         if (since_best >= kStallChecks && !(precision == FLD_PREC_MIXED && fam != FAM_FF)) return ACT_STALLED;
@@ -459,6 +566,7 @@ void fld_default_params(fld_solve_params *p) {
     p->D0 = -1.0;
     p->phi_b = -1.0;
     p->D_b = -1.0;
+    p->warmup_iters = -1;
 }
 
 const char *fld_status_string(fld_status s) {
@@ -551,7 +659,7 @@ void fld_destroy(fld_grid g) {
         if (e.exec) cudaGraphExecDestroy(e.exec);
     void *ptrs[] = {g->f.sp, g->f.ah2, g->f.jh2, g->f.phi, g->f.phlo, g->f.D, g->f.Df, g->f.sp64, g->f.ah264,
                     g->f.jh264, g->f.phi64, g->f.D64, g->f.Df64, g->f.sigma_t, g->f.albedo, g->f.jsrc,
-                    g->f.partials, g->f.result};
+                    g->f.partials, g->f.result, g->f.spb, g->f.sab};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (g->ev0) cudaEventDestroy(g->ev0);
@@ -797,11 +905,11 @@ fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r)
     if (a == ACT_CONVERGED) outcome = FLD_OK;
     else if (a == ACT_DIVERGED) outcome = FLD_ERR_DIVERGED;
     else if ((st = save()) != FLD_OK) return st;
+    const int warm = warmup_of(g, p);
     while (outcome == FLD_ERR_NOT_CONVERGED && it < p->max_iters) {
-        int k = p->check_every;
-        if (k > p->max_iters - it) k = p->max_iters - it;
+        const int k = block_len(it, p->check_every, p->max_iters, warm);
         FLD_CK(cudaEventRecord(g->evb0, g->stream));
-        if ((st = run_block(g, fam, pp, k)) != FLD_OK) return st;
+        if ((st = run_block(g, fam, block_params(pp, it, warm), k)) != FLD_OK) return st;
         FLD_CK(cudaEventRecord(g->evb1, g->stream));
         it += k;
         if (fam == FAM_F32) res.iterations_fp32 += k;
@@ -814,7 +922,7 @@ fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r)
         if (fam == FAM_F32) res.ms_sweep_fp32 += bms;
         else if (fam == FAM_FH) res.ms_sweep_mid += bms;
         else res.ms_sweep_corr += bms;
-        a = ctl.next(rel, pp.omega);
+        a = (warm > 0 && it == warm) ? ctl.restart(rel) : ctl.next(rel, pp.omega);
         switch (a) {
         case ACT_CONVERGED: outcome = FLD_OK; break;
         case ACT_DIVERGED: outcome = FLD_ERR_DIVERGED; break;
@@ -874,6 +982,7 @@ struct ServerEntry {
     Controller ctl;
     Family fam = FAM_F32;
     PassParams pp{};
+    int warm = 0;                 // warm-up iterations at omega = 1
     Family snap_fam = FAM_F32;
     bool snap_lo = false;
     fld_solve_result res{};
@@ -1034,6 +1143,7 @@ fld_status fld_server_add(fld_server s, fld_grid g, long long tag) {
     }
     if ((st = sync_family(g, e.fam)) != FLD_OK) return st;
     e.pp = pass_params(g, p);
+    e.warm = warmup_of(g, p);
     e.ctl.precision = p->precision;
     e.ctl.tol = p->tol;
     e.ctl.sw = s->sw;
@@ -1083,11 +1193,10 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
         std::vector<int> k(n);
         for (size_t i = 0; i < n; ++i) {
             ServerEntry &e = s->active[i];
-            k[i] = p->check_every;
-            if (k[i] > p->max_iters - e.res.iterations) k[i] = p->max_iters - e.res.iterations;
+            k[i] = block_len(e.res.iterations, p->check_every, p->max_iters, e.warm);
             if (k[i] <= 0) continue;
             e.g->stream = s->side[i % nside];
-            st = run_block(e.g, e.fam, e.pp, k[i]);
+            st = run_block(e.g, e.fam, block_params(e.pp, e.res.iterations, e.warm), k[i]);
             e.g->stream = s->bs;
             if (st != FLD_OK) return st;
             s->launches += 2LL * k[i];
@@ -1140,7 +1249,8 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
             const double rel = rel_from_sums(g, p->residual_margin, out[2 * i], out[2 * i + 1]);
             e.res.rel_residual = rel;
             ++e.res.checks;
-            const Action a = e.ctl.next(rel, e.pp.omega);
+            const Action a = (e.warm > 0 && e.res.iterations == e.warm) ? e.ctl.restart(rel)
+                                                                         : e.ctl.next(rel, e.pp.omega);
             switch (a) {
             case ACT_CONVERGED: retire.push_back({i, {FLD_OK, rel}}); break;
             case ACT_DIVERGED: retire.push_back({i, {FLD_ERR_DIVERGED, rel}}); break;

@@ -195,6 +195,9 @@ __device__ __forceinline__ ff ff_mul_f(ff a, float b) {
 
 __device__ __forceinline__ double ff_to_d(ff a) { return (double)a.hi + (double)a.lo; }
 
+// bfloat16 bit pattern -> float (exact: the pattern is the float's upper half)
+__device__ __forceinline__ float bf16_bits_to_f(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+
 // ---------------------------------------------------------------------------
 // Knudsen number (Eq. 35) and D (Eq. 33) from the central gradient (Eq. 34).
 // g_x etc. are the already formed central differences phi(i+1) - phi(i-1).

@@ -19,6 +19,8 @@ struct PassParams {
     double omega;
     double inv2h;
     double floor_;   // eps * jbar (or the no-emission floor)
+    int bf16 = 0;    // single-precision / hi-lo sweeps read the bfloat16 medium
+    double h2 = 0;   // h^2, which scales the bfloat16 sigma_a'
 };
 
 // Device fields of one grid (padded layout unless noted).
@@ -27,6 +29,10 @@ struct Fields {
     float *sp = nullptr, *ah2 = nullptr, *jh2 = nullptr;   // sigma', sigma_a' h^2, j h^2
     float *phi = nullptr, *phlo = nullptr, *D = nullptr;   // phi (hi), phi (lo), D
     float *Df = nullptr;                                   // scratch: fresh D for the residual
+    // bfloat16 copies of sigma' and sigma_a' (bit patterns; allocated on the
+    // first solve with medium_bf16) read by the single-precision and hi/lo
+    // sweeps; sp and ah2 then hold the same rounded values
+    uint16_t *spb = nullptr, *sab = nullptr;
     // double-precision family (allocated on first FP64 use)
     double *sp64 = nullptr, *ah264 = nullptr, *jh264 = nullptr;
     double *phi64 = nullptr, *D64 = nullptr, *Df64 = nullptr;
@@ -39,8 +45,11 @@ struct Fields {
 };
 
 // Medium preparation (Algorithm 1: sigma floor; sigma_a', j scaled by h^2).
-cudaError_t launch_prep_f(const Layout &L, const Fields &f, float sigma_eps, float h2, cudaStream_t s);
-cudaError_t launch_prep_d(const Layout &L, const Fields &f, double sigma_eps, double h2, cudaStream_t s);
+// bf16: round sigma' and sigma_a' to bfloat16 (formed in single precision)
+// and write the bfloat16 copies too (launch_prep_f).
+cudaError_t launch_prep_f(const Layout &L, const Fields &f, float sigma_eps, float h2, bool bf16, cudaStream_t s);
+cudaError_t launch_prep_d(const Layout &L, const Fields &f, double sigma_eps, double h2, bool bf16,
+                          cudaStream_t s);
 
 // phi = phi0 / D = D0 on the unknowns, phi_b / D_b on the ghosts, 0 elsewhere.
 cudaError_t launch_init_f(const Layout &L, float *phi, float *phlo, float *D, double phi0, double D0,

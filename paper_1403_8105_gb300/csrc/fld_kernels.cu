@@ -12,9 +12,12 @@
 //     a transmittance march (Eq. 3).
 //
 // The stencil is memory-bound: no tensor-core formulation applies.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
+
+#include <type_traits>
 
 #include "fld_device.cuh"
 #include "fld_internal.h"
@@ -68,21 +71,37 @@ __global__ void __launch_bounds__(kRedThreads) k_finalize(const double *__restri
 // ---------------------------------------------------------------------------
 // Preparation
 // ---------------------------------------------------------------------------
+// sigma' = max(sigma_t, sigma_eps) and sigma_a' = (1 - albedo) sigma' in
+// single precision; with BF both are rounded to bfloat16 (nearest, ties to
+// even), the bit patterns kept for the sweeps that read bfloat16 and the
+// rounded values, upcast exactly, stored in sp / ah2 for all other kernels.
+template <bool BF>
 __global__ void k_prep_f(Layout L, const float *__restrict__ st, const float *__restrict__ alb,
                          const float *__restrict__ js, float *__restrict__ sp, float *__restrict__ ah2,
-                         float *__restrict__ jh2, float seps, float h2) {
+                         float *__restrict__ jh2, uint16_t *__restrict__ spb, uint16_t *__restrict__ sab, float seps,
+                         float h2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y * blockDim.y + threadIdx.y;
     const int k = blockIdx.z;
     if (i >= L.nx || j >= L.ny) return;
     const long long v = ((long long)k * L.ny + j) * L.nx + i;
     const int q = L.at(i, j, k);
-    const float s = fmaxf(st[v], seps);                           // Algorithm 1: sigma floor
+    float s = fmaxf(st[v], seps);                                 // Algorithm 1: sigma floor
+    float a = __fmul_rn(__fsub_rn(1.0f, alb[v]), s);              // (1 - albedo) sigma'
+    if (BF) {
+        const uint16_t sb = __bfloat16_as_ushort(__float2bfloat16_rn(s));
+        const uint16_t ab = __bfloat16_as_ushort(__float2bfloat16_rn(a));
+        spb[q] = sb;
+        sab[q] = ab;
+        s = bf16_bits_to_f(sb);
+        a = bf16_bits_to_f(ab);
+    }
     sp[q] = s;
-    ah2[q] = __fmul_rn(__fmul_rn(__fsub_rn(1.0f, alb[v]), s), h2);  // (1 - albedo) sigma' dl^2
+    ah2[q] = __fmul_rn(a, h2);                                    // sigma_a' dl^2
     jh2[q] = __fmul_rn(js[v], h2);
 }
 
+template <bool BF>
 __global__ void k_prep_d(Layout L, const float *__restrict__ st, const float *__restrict__ alb,
                          const float *__restrict__ js, double *__restrict__ sp, double *__restrict__ ah2,
                          double *__restrict__ jh2, double seps, double h2) {
@@ -92,9 +111,18 @@ __global__ void k_prep_d(Layout L, const float *__restrict__ st, const float *__
     if (i >= L.nx || j >= L.ny) return;
     const long long v = ((long long)k * L.ny + j) * L.nx + i;
     const int q = L.at(i, j, k);
-    const double s = fmax((double)st[v], seps);
+    double s, a;
+    if (BF) {   // the rounded medium of k_prep_f<true>, exactly
+        const float s32 = fmaxf(st[v], (float)seps);
+        const float a32 = __fmul_rn(__fsub_rn(1.0f, alb[v]), s32);
+        s = (double)bf16_bits_to_f(__bfloat16_as_ushort(__float2bfloat16_rn(s32)));
+        a = (double)bf16_bits_to_f(__bfloat16_as_ushort(__float2bfloat16_rn(a32)));
+    } else {
+        s = fmax((double)st[v], seps);
+        a = __dmul_rn(1.0 - (double)alb[v], s);
+    }
     sp[q] = s;
-    ah2[q] = __dmul_rn(__dmul_rn(1.0 - (double)alb[v], s), h2);
+    ah2[q] = __dmul_rn(a, h2);
     jh2[q] = __dmul_rn((double)js[v], h2);
 }
 
@@ -385,11 +413,31 @@ __device__ __forceinline__ void pdl_launch_dependents() {
 }
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
+// sigma' and sigma_a' h^2 of the two cells of a pair: the single-precision
+// fields, or the bfloat16 copies (one 32-bit load each; the first cell is the
+// low half) with sigma_a' scaled by h^2 as k_prep_f scales it.
+template <bool BF>
+__device__ __forceinline__ void medium_pair(const float *__restrict__ sp, const float *__restrict__ ah2,
+                                            const uint16_t *__restrict__ spb, const uint16_t *__restrict__ sab,
+                                            float h2, int off, float2 &s2, float2 &a2) {
+    if (BF) {
+        const uint32_t us = *reinterpret_cast<const uint32_t *>(spb + off);
+        const uint32_t ua = *reinterpret_cast<const uint32_t *>(sab + off);
+        s2 = make_float2(__uint_as_float(us << 16), __uint_as_float(us & 0xFFFF0000u));
+        a2 = make_float2(__fmul_rn(__uint_as_float(ua << 16), h2), __fmul_rn(__uint_as_float(ua & 0xFFFF0000u), h2));
+    } else {
+        s2 = ld2(sp, off);
+        a2 = ld2(ah2, off);
+    }
+}
+
 // Single-precision pass (the bulk sweeps), two unknowns per thread (40
 // registers: six CTAs per SM).
-template <int LIM, int ROUNDS>
+template <int LIM, int ROUNDS, bool BF>
 __global__ void __launch_bounds__(256, 6) k_pass2_f32(Layout L, const float *__restrict__ sp,
                                                    const float *__restrict__ ah2, const float *__restrict__ jh2,
+                                                   const uint16_t *__restrict__ spb,
+                                                   const uint16_t *__restrict__ sab, float h2,
                                                    float *__restrict__ phi, float *__restrict__ D, int colour,
                                                    int lim_rt, float larsen_n, float omega, float inv2h,
                                                    float floor_, int rounds_rt) {
@@ -400,7 +448,9 @@ __global__ void __launch_bounds__(256, 6) k_pass2_f32(Layout L, const float *__r
     Pair q;
     pair_cells(L, colour, t, J, K, q);
     if (!q.first) return;
-    const float2 s2 = ld2(sp, q.own), a2 = ld2(ah2, q.own), j2 = ld2(jh2, q.own);
+    float2 s2, a2;
+    medium_pair<BF>(sp, ah2, spb, sab, h2, q.own, s2, a2);
+    const float2 j2 = ld2(jh2, q.own);
     pdl_wait();
     float ps0[6], ps1[6], Ds0[6], Ds1[6];
     gather_pair(phi, q, ps0, ps1);
@@ -463,9 +513,11 @@ __device__ __forceinline__ void cell_fh(float p0, float p0lo, const float ps[6],
     D_new = Dp;
 }
 
-template <int LIM, int ROUNDS>
+template <int LIM, int ROUNDS, bool BF>
 __global__ void __launch_bounds__(256, 5) k_pass2_fh(Layout L, const float *__restrict__ sp,
                                                   const float *__restrict__ ah2, const float *__restrict__ jh2,
+                                                  const uint16_t *__restrict__ spb,
+                                                  const uint16_t *__restrict__ sab, float h2,
                                                   float *__restrict__ phi, float *__restrict__ phlo,
                                                   float *__restrict__ D, int colour, int lim_rt, float larsen_n,
                                                   float omega, float inv2h, float floor_, int rounds_rt) {
@@ -476,7 +528,9 @@ __global__ void __launch_bounds__(256, 5) k_pass2_fh(Layout L, const float *__re
     Pair q;
     pair_cells(L, colour, t, J, K, q);
     if (!q.first) return;
-    const float2 s2 = ld2(sp, q.own), a2 = ld2(ah2, q.own), j2 = ld2(jh2, q.own);
+    float2 s2, a2;
+    medium_pair<BF>(sp, ah2, spb, sab, h2, q.own, s2, a2);
+    const float2 j2 = ld2(jh2, q.own);
     pdl_wait();
     float ps0[6], ps1[6], ls0[6], ls1[6], Ds0[6], Ds1[6];
     gather_pair(phi, q, ps0, ps1);
@@ -963,14 +1017,17 @@ inline dim3 vox_grid(const Layout &L) {
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-cudaError_t launch_prep_f(const Layout &L, const Fields &f, float sigma_eps, float h2, cudaStream_t s) {
-    k_prep_f<<<vox_grid(L), vox_block(), 0, s>>>(L, f.sigma_t, f.albedo, f.jsrc, f.sp, f.ah2, f.jh2, sigma_eps, h2);
+cudaError_t launch_prep_f(const Layout &L, const Fields &f, float sigma_eps, float h2, bool bf16, cudaStream_t s) {
+    auto k = bf16 ? k_prep_f<true> : k_prep_f<false>;
+    k<<<vox_grid(L), vox_block(), 0, s>>>(L, f.sigma_t, f.albedo, f.jsrc, f.sp, f.ah2, f.jh2, f.spb, f.sab, sigma_eps,
+                                          h2);
     return cudaGetLastError();
 }
 
-cudaError_t launch_prep_d(const Layout &L, const Fields &f, double sigma_eps, double h2, cudaStream_t s) {
-    k_prep_d<<<vox_grid(L), vox_block(), 0, s>>>(L, f.sigma_t, f.albedo, f.jsrc, f.sp64, f.ah264, f.jh264,
-                                                  sigma_eps, h2);
+cudaError_t launch_prep_d(const Layout &L, const Fields &f, double sigma_eps, double h2, bool bf16,
+                          cudaStream_t s) {
+    auto k = bf16 ? k_prep_d<true> : k_prep_d<false>;
+    k<<<vox_grid(L), vox_block(), 0, s>>>(L, f.sigma_t, f.albedo, f.jsrc, f.sp64, f.ah264, f.jh264, sigma_eps, h2);
     return cudaGetLastError();
 }
 
@@ -1041,12 +1098,17 @@ cudaError_t launch_pass(Family fam, const Layout &L, const Fields &f, const Pass
     const dim3 grd2 = pass2_grid(L, blk);
     switch (fam) {
     case FAM_F32: {
-        auto k = k_pass2_f32<-1, 0>;
-        if (p.local_iters == 2 && p.lim == LIM_LP) k = k_pass2_f32<LIM_LP, 2>;
-        else if (p.local_iters == 2 && p.lim == LIM_KERSHAW) k = k_pass2_f32<LIM_KERSHAW, 2>;
-        else if (p.local_iters == 2 && p.lim == LIM_LARSEN) k = k_pass2_f32<LIM_LARSEN, 2>;
-        return launch_pdl(k, grd2, blk, s, L, f.sp, f.ah2, f.jh2, f.phi, f.D, colour, p.lim, (float)p.larsen_n,
-                          (float)p.omega, (float)p.inv2h, (float)p.floor_, p.local_iters);
+        auto pick = [&](auto bf) {
+            constexpr bool B = decltype(bf)::value;
+            auto k = k_pass2_f32<-1, 0, B>;
+            if (p.local_iters == 2 && p.lim == LIM_LP) k = k_pass2_f32<LIM_LP, 2, B>;
+            else if (p.local_iters == 2 && p.lim == LIM_KERSHAW) k = k_pass2_f32<LIM_KERSHAW, 2, B>;
+            else if (p.local_iters == 2 && p.lim == LIM_LARSEN) k = k_pass2_f32<LIM_LARSEN, 2, B>;
+            return launch_pdl(k, grd2, blk, s, L, f.sp, f.ah2, f.jh2, f.spb, f.sab, (float)p.h2, f.phi, f.D, colour,
+                              p.lim, (float)p.larsen_n, (float)p.omega, (float)p.inv2h, (float)p.floor_,
+                              p.local_iters);
+        };
+        return p.bf16 ? pick(std::true_type{}) : pick(std::false_type{});
     }
     case FAM_FF: {
         auto k = k_pass_ff<-1, 0>;
@@ -1057,12 +1119,17 @@ cudaError_t launch_pass(Family fam, const Layout &L, const Fields &f, const Pass
                           (float)p.larsen_n, (float)p.omega, (float)p.inv2h, (float)p.floor_, p.local_iters);
     }
     case FAM_FH: {
-        auto k = k_pass2_fh<-1, 0>;
-        if (p.local_iters == 2 && p.lim == LIM_LP) k = k_pass2_fh<LIM_LP, 2>;
-        else if (p.local_iters == 2 && p.lim == LIM_KERSHAW) k = k_pass2_fh<LIM_KERSHAW, 2>;
-        else if (p.local_iters == 2 && p.lim == LIM_LARSEN) k = k_pass2_fh<LIM_LARSEN, 2>;
-        return launch_pdl(k, grd2, blk, s, L, f.sp, f.ah2, f.jh2, f.phi, f.phlo, f.D, colour, p.lim,
-                          (float)p.larsen_n, (float)p.omega, (float)p.inv2h, (float)p.floor_, p.local_iters);
+        auto pick = [&](auto bf) {
+            constexpr bool B = decltype(bf)::value;
+            auto k = k_pass2_fh<-1, 0, B>;
+            if (p.local_iters == 2 && p.lim == LIM_LP) k = k_pass2_fh<LIM_LP, 2, B>;
+            else if (p.local_iters == 2 && p.lim == LIM_KERSHAW) k = k_pass2_fh<LIM_KERSHAW, 2, B>;
+            else if (p.local_iters == 2 && p.lim == LIM_LARSEN) k = k_pass2_fh<LIM_LARSEN, 2, B>;
+            return launch_pdl(k, grd2, blk, s, L, f.sp, f.ah2, f.jh2, f.spb, f.sab, (float)p.h2, f.phi, f.phlo,
+                              f.D, colour, p.lim, (float)p.larsen_n, (float)p.omega, (float)p.inv2h,
+                              (float)p.floor_, p.local_iters);
+        };
+        return p.bf16 ? pick(std::true_type{}) : pick(std::false_type{});
     }
     case FAM_F64:
         k_pass_d<<<grd, blk, 0, s>>>(L, f.sp64, f.ah264, f.jh264, f.phi64, f.D64, colour, p.lim, p.larsen_n,
