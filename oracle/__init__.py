@@ -76,6 +76,8 @@ def _load():
             lib.fldo_rms.argtypes = [ctypes.c_long, _dp]
             lib.fldo_rb_iteration.restype = None
             lib.fldo_rb_iteration.argtypes = [ctypes.POINTER(_Cfg), _dp, _dp, _dp, _dp, _dp]
+            lib.fldo_jacobi_iteration.restype = None
+            lib.fldo_jacobi_iteration.argtypes = [ctypes.POINTER(_Cfg), _dp, _dp, _dp, _dp, _dp, _dp]
             lib.fldo_pass.restype = None
             lib.fldo_pass.argtypes = [ctypes.POINTER(_Cfg), _dp, _dp, _dp, _dp, _dp, ctypes.c_int]
             lib.fldo_residual.restype = ctypes.c_double
@@ -227,6 +229,17 @@ def colour_pass(p: Problem, colour: int) -> None:
     lib = _load()
     c = p.cfg()
     lib.fldo_pass(ctypes.byref(c), _d(p.sp), _d(p.sa), _d(p.j), _d(p.phi), _d(p.D), int(colour))
+
+
+def jacobi_iteration(p: Problem, iters: int = 1):
+    """Jacobi iterations (D^k from phi^k everywhere, then phi^{k+1} from
+    phi^k and D^k, damped by p.omega); p.phi and p.D are updated."""
+    lib = _load()
+    c = p.cfg()
+    nxt = np.empty_like(p.phi)
+    for _ in range(iters):
+        lib.fldo_jacobi_iteration(ctypes.byref(c), _d(p.sp), _d(p.sa), _d(p.j), _d(p.phi), _d(p.D), _d(nxt))
+        p.phi, nxt = nxt, p.phi
 
 
 def residual(p: Problem, phi: np.ndarray | None = None, margin: int = 0, field: bool = False):

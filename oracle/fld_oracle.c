@@ -313,6 +313,70 @@ void fldo_pass(const fldo_cfg *c, const double *sp, const double *sa, const doub
 }
 
 /* ------------------------------------------------------------------------ */
+/* Jacobi iteration: the order-free alternative to Algorithm 1's red-black   */
+/* sweep.  Every quantity on the right of Eq. 32 comes from iteration k.     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    const fldo_cfg *c;
+    const double *sp, *sa, *j, *phi;
+    double *D, *phi_next;
+} jac_ctx;
+
+static void jacobi_D_planes(void *vctx, int k0, int k1, int worker)
+{
+    (void)worker;
+    jac_ctx *x = (jac_ctx *)vctx;
+    const fldo_cfg *c = x->c;
+    for (int k = k0; k < k1; ++k)
+        for (int j = 0; j < c->ny; ++j)
+            for (int i = 0; i < c->nx; ++i) {
+                long v = ((long)k * c->ny + j) * c->nx + i;
+                long q = pidx(c, i + 1, j + 1, k + 1);
+                x->D[q] = fresh_D(c, x->phi, x->sp[v], q);         /* D^k, Eq. 33-35 */
+            }
+}
+
+static void jacobi_phi_planes(void *vctx, int k0, int k1, int worker)
+{
+    (void)worker;
+    jac_ctx *x = (jac_ctx *)vctx;
+    const fldo_cfg *c = x->c;
+    const long sx = 1, sy = c->nx + 2, sz = (long)(c->nx + 2) * (c->ny + 2);
+    const double h2 = c->h * c->h;
+    for (int k = k0; k < k1; ++k)
+        for (int j = 0; j < c->ny; ++j)
+            for (int i = 0; i < c->nx; ++i) {
+                long v = ((long)k * c->ny + j) * c->nx + i;
+                long q = pidx(c, i + 1, j + 1, k + 1);
+                const long nb[6] = {q - sx, q + sx, q - sy, q + sy, q - sz, q + sz};
+                double num = x->j[v] * h2, den = x->sa[v] * h2;
+                for (int s = 0; s < 6; ++s) {
+                    double Dps = 0.5 * (x->D[q] + x->D[nb[s]]);
+                    num += Dps * x->phi[nb[s]];
+                    den += Dps;
+                }
+                /* Eq. 32, then the damped blend of Eq. 36 */
+                x->phi_next[q] = c->omega * (num / den) + (1.0 - c->omega) * x->phi[q];
+            }
+}
+
+/* One Jacobi iteration: D^k = F(R(phi^k))/sigma' at every unknown, then
+ * phi^{k+1}_p = (1 - omega) phi^k_p + omega num/den with num and den of
+ * Eq. 32 from phi^k and D^k only.  D (padded) is overwritten at the unknowns
+ * (ghost D untouched); phi_next (padded) receives phi^{k+1} at the unknowns
+ * and a copy of phi's ghosts. */
+void fldo_jacobi_iteration(const fldo_cfg *c, const double *sp, const double *sa, const double *j,
+                           const double *phi, double *D, double *phi_next)
+{
+    const long np = (long)(c->nx + 2) * (c->ny + 2) * (c->nz + 2);
+    memcpy(phi_next, phi, sizeof(double) * (size_t)np);
+    jac_ctx x = {c, sp, sa, j, phi, D, phi_next};
+    parallel_planes(c->nz, c->nthreads, jacobi_D_planes, &x);
+    parallel_planes(c->nz, c->nthreads, jacobi_phi_planes, &x);
+}
+
+/* ------------------------------------------------------------------------ */
 /* Residual, Eq. 37, with D recomputed from the current phi.                 */
 /* ------------------------------------------------------------------------ */
 
