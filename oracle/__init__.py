@@ -41,6 +41,12 @@ _dp = ctypes.POINTER(ctypes.c_double)
 _fp = ctypes.POINTER(ctypes.c_float)
 
 
+class _Camera(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_double * 3), ("target", ctypes.c_double * 3), ("up", ctypes.c_double * 3),
+                ("fov_deg", ctypes.c_double), ("width", ctypes.c_int), ("height", ctypes.c_int),
+                ("step", ctypes.c_double), ("background", ctypes.c_double), ("t_min", ctypes.c_double)]
+
+
 class _Cfg(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("h", ctypes.c_double), ("limiter", ctypes.c_int), ("larsen_n", ctypes.c_double),
@@ -76,6 +82,9 @@ def _load():
             lib.fldo_rms.argtypes = [ctypes.c_long, _dp]
             lib.fldo_rb_iteration.restype = None
             lib.fldo_rb_iteration.argtypes = [ctypes.POINTER(_Cfg), _dp, _dp, _dp, _dp, _dp]
+            lib.fldo_render.restype = None
+            lib.fldo_render.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp,
+                                        _dp, ctypes.POINTER(_Camera), _dp, ctypes.c_int]
             lib.fldo_jacobi_iteration.restype = None
             lib.fldo_jacobi_iteration.argtypes = [ctypes.POINTER(_Cfg), _dp, _dp, _dp, _dp, _dp, _dp]
             lib.fldo_pass.restype = None
@@ -240,6 +249,42 @@ def jacobi_iteration(p: Problem, iters: int = 1):
     for _ in range(iters):
         lib.fldo_jacobi_iteration(ctypes.byref(c), _d(p.sp), _d(p.sa), _d(p.j), _d(p.phi), _d(p.D), _d(nxt))
         p.phi, nxt = nxt, p.phi
+
+
+def render(sigma_t: np.ndarray, albedo: np.ndarray, q: np.ndarray, phi: np.ndarray, h: float, *,
+           eye, target, up=(0.0, 1.0, 0.0), fov_deg: float = 40.0, width: int = 64, height: int = 64,
+           step: float | None = None, background: float = 0.0, t_min: float = 1e-6,
+           nthreads: int | None = None) -> np.ndarray:
+    """Primary ray march (Sec. 3): radiance per pixel, shape (height, width),
+    row 0 at the top.  sigma_t, albedo, q (the solver's source: q_ri + j) are
+    unpadded; phi is unpadded or padded (the ghost layer is dropped)."""
+    lib = _load()
+    sigma_t = np.asarray(sigma_t, dtype=np.float32)
+    nz, ny, nx = sigma_t.shape
+    st = np.ascontiguousarray(sigma_t, dtype=np.float64)
+    ss = np.ascontiguousarray(np.asarray(albedo, dtype=np.float32).astype(np.float64) * st)
+    qd = np.ascontiguousarray(q, dtype=np.float64)
+    ph = np.asarray(phi, dtype=np.float64)
+    if ph.shape == (nz + 2, ny + 2, nx + 2):
+        ph = ph[1:-1, 1:-1, 1:-1]
+    ph = np.ascontiguousarray(ph)
+    cam = _Camera()
+    cam.eye[:] = [float(v) for v in eye]
+    cam.target[:] = [float(v) for v in target]
+    cam.up[:] = [float(v) for v in up]
+    cam.fov_deg, cam.width, cam.height = float(fov_deg), int(width), int(height)
+    cam.step = float(step) if step else 0.5 * h
+    cam.background, cam.t_min = float(background), float(t_min)
+    img = np.zeros((height, width), dtype=np.float64)
+    lib.fldo_render(nx, ny, nz, float(h), _d(st), _d(ss), _d(qd), _d(ph), ctypes.byref(cam), _d(img),
+                    int(nthreads or default_threads()))
+    return img
+
+
+def tonemap(radiance: np.ndarray, exposure: float = 1.0, gamma: float = 2.2) -> np.ndarray:
+    """Gamma compression to 8 bits (Sec. 7): round(255 clamp((e L)^(1/gamma), 0, 1))."""
+    v = np.clip(exposure * np.asarray(radiance, dtype=np.float64), 0.0, None) ** (1.0 / gamma)
+    return np.floor(255.0 * np.clip(v, 0.0, 1.0) + 0.5).astype(np.uint8)
 
 
 def residual(p: Problem, phi: np.ndarray | None = None, margin: int = 0, field: bool = False):

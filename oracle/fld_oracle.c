@@ -656,6 +656,152 @@ void fldo_bake_point(int nx, int ny, int nz, double h, const float *sigma_t, con
 }
 
 /* F(R) for an array of R values (Table 2). */
+/* ------------------------------------------------------------------------ */
+/* Primary ray march (Sec. 3, the equation after Eq. 2): the radiance that   */
+/* reaches the camera along a pixel's ray is the background attenuated over  */
+/* the whole chord plus, over the march segments, the transmittance from     */
+/* each segment to the camera times its source Q times the segment length.  */
+/* 4 pi Q = q_ri + sigma_s phi + j (the source in terms of phi, Sec. 3): the  */
+/* solver's source field already holds q_ri + j.  Fields are sampled        */
+/* trilinearly between voxel centres (clamped to the outermost centres) at   */
+/* the midpoint of each segment; segments of length `step` start where the   */
+/* ray enters the box [0, nx h] x [0, ny h] x [0, nz h] (or at the eye, if    */
+/* inside) and the last one ends at the exit.  The transmittance from a      */
+/* segment to the camera covers the segments between them (not its own), so */
+/* that over the whole chord it is exp(-sum sigma_t step) as in Sec. 3.  The */
+/* march stops once that transmittance is below `t_min` (the rest of the     */
+/* ray can add at most t_min times its unattenuated source).                 */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    double eye[3], target[3], up[3];
+    double fov_deg;        /* vertical field of view */
+    int width, height;
+    double step;           /* segment length (> 0) */
+    double background;     /* radiance entering the far end of every ray */
+    double t_min;          /* transmittance below which the march stops */
+} fldo_camera;
+
+static double field_trilinear(int nx, int ny, int nz, double h, const double *f, const double x[3])
+{
+    const int n[3] = {nx, ny, nz};
+    int i0[3], i1[3];
+    double w[3];
+    for (int a = 0; a < 3; ++a) {
+        double u = x[a] / h - 0.5;
+        if (u < 0.0) u = 0.0;
+        if (u > (double)(n[a] - 1)) u = (double)(n[a] - 1);
+        int b = (int)floor(u);
+        if (b > n[a] - 2) b = n[a] - 2;
+        if (b < 0) b = 0;
+        i0[a] = b;
+        i1[a] = b + 1 < n[a] ? b + 1 : b;
+        w[a] = (n[a] == 1) ? 0.0 : u - (double)b;
+    }
+    double acc = 0.0;
+    for (int cz = 0; cz < 2; ++cz)
+        for (int cy = 0; cy < 2; ++cy)
+            for (int cx = 0; cx < 2; ++cx) {
+                const int i = cx ? i1[0] : i0[0], j = cy ? i1[1] : i0[1], k = cz ? i1[2] : i0[2];
+                const double wt = (cx ? w[0] : 1.0 - w[0]) * (cy ? w[1] : 1.0 - w[1]) * (cz ? w[2] : 1.0 - w[2]);
+                acc += wt * f[((long)k * ny + j) * nx + i];
+            }
+    return acc;
+}
+
+typedef struct {
+    int nx, ny, nz;
+    double h;
+    const double *st, *ss, *q, *phi;
+    const fldo_camera *cam;
+    double *image;
+    double f[3], r[3], u[3], tan_half, aspect;
+} render_ctx;
+
+static void render_rows(void *vctx, int y0, int y1, int worker)
+{
+    (void)worker;
+    render_ctx *x = (render_ctx *)vctx;
+    const fldo_camera *c = x->cam;
+    const double box[3] = {x->nx * x->h, x->ny * x->h, x->nz * x->h};
+    for (int py = y0; py < y1; ++py)
+        for (int px = 0; px < c->width; ++px) {
+            const double sx = (2.0 * (px + 0.5) / c->width - 1.0) * x->tan_half * x->aspect;
+            const double sy = (1.0 - 2.0 * (py + 0.5) / c->height) * x->tan_half;
+            double d[3], norm = 0.0;
+            for (int a = 0; a < 3; ++a) {
+                d[a] = x->f[a] + sx * x->r[a] + sy * x->u[a];
+                norm += d[a] * d[a];
+            }
+            norm = sqrt(norm);
+            for (int a = 0; a < 3; ++a) d[a] /= norm;
+            /* chord through the box (slab test) */
+            double t0 = 0.0, t1 = INFINITY;
+            int hit = 1;
+            for (int a = 0; a < 3; ++a) {
+                if (d[a] == 0.0) {
+                    if (c->eye[a] < 0.0 || c->eye[a] > box[a]) hit = 0;
+                    continue;
+                }
+                double ta = (0.0 - c->eye[a]) / d[a], tb = (box[a] - c->eye[a]) / d[a];
+                if (ta > tb) { double tt = ta; ta = tb; tb = tt; }
+                if (ta > t0) t0 = ta;
+                if (tb < t1) t1 = tb;
+            }
+            double L = 0.0, T = 1.0;
+            if (hit && t1 > t0) {
+                const long nseg = (long)ceil((t1 - t0) / c->step);
+                for (long m = 0; m < nseg && T >= c->t_min; ++m) {
+                    const double a = t0 + m * c->step;
+                    const double b = fmin(a + c->step, t1);
+                    const double len = b - a, tm = 0.5 * (a + b);
+                    double pos[3];
+                    for (int k = 0; k < 3; ++k) pos[k] = c->eye[k] + tm * d[k];
+                    const double st = field_trilinear(x->nx, x->ny, x->nz, x->h, x->st, pos);
+                    const double ss = field_trilinear(x->nx, x->ny, x->nz, x->h, x->ss, pos);
+                    const double q = field_trilinear(x->nx, x->ny, x->nz, x->h, x->q, pos);
+                    const double ph = field_trilinear(x->nx, x->ny, x->nz, x->h, x->phi, pos);
+                    const double Q = (q + ss * ph) / (4.0 * M_PI);   /* Sec. 3, 4 pi Q */
+                    L += T * Q * len;
+                    T *= exp(-st * len);
+                }
+            }
+            x->image[(long)py * c->width + px] = L + c->background * T;
+        }
+}
+
+/* Render the volume: sigma_t, sigma_s, q (= q_ri + j) and phi unpadded
+ * (nx*ny*nz, x fastest); image (width*height, row 0 at the top) receives
+ * the radiance of each pixel. */
+void fldo_render(int nx, int ny, int nz, double h, const double *sigma_t, const double *sigma_s, const double *q,
+                 const double *phi, const fldo_camera *cam, double *image, int nthreads)
+{
+    render_ctx x;
+    x.nx = nx; x.ny = ny; x.nz = nz; x.h = h;
+    x.st = sigma_t; x.ss = sigma_s; x.q = q; x.phi = phi;
+    x.cam = cam;
+    x.image = image;
+    double nf = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        x.f[a] = cam->target[a] - cam->eye[a];
+        nf += x.f[a] * x.f[a];
+    }
+    nf = sqrt(nf);
+    for (int a = 0; a < 3; ++a) x.f[a] /= nf;
+    /* r = f x up, u = r x f */
+    x.r[0] = x.f[1] * cam->up[2] - x.f[2] * cam->up[1];
+    x.r[1] = x.f[2] * cam->up[0] - x.f[0] * cam->up[2];
+    x.r[2] = x.f[0] * cam->up[1] - x.f[1] * cam->up[0];
+    double nr = sqrt(x.r[0] * x.r[0] + x.r[1] * x.r[1] + x.r[2] * x.r[2]);
+    for (int a = 0; a < 3; ++a) x.r[a] /= nr;
+    x.u[0] = x.r[1] * x.f[2] - x.r[2] * x.f[1];
+    x.u[1] = x.r[2] * x.f[0] - x.r[0] * x.f[2];
+    x.u[2] = x.r[0] * x.f[1] - x.r[1] * x.f[0];
+    x.tan_half = tan(0.5 * cam->fov_deg * M_PI / 180.0);
+    x.aspect = (double)cam->width / (double)cam->height;
+    parallel_planes(cam->height, nthreads, render_rows, &x);
+}
+
 void fldo_limiter_array(int kind, double larsen_n, const double *R, double *F, long count)
 {
     for (long v = 0; v < count; ++v) F[v] = fldo_limiter(kind, larsen_n, R[v]);
