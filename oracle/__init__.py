@@ -39,6 +39,7 @@ LIMITERS = {"cda": 0, "sum": 1, "max": 2, "kershaw": 3, "larsen": 4, "lp": 5}
 EPS = 1e-20          # epsilon of Eq. 35
 _dp = ctypes.POINTER(ctypes.c_double)
 _fp = ctypes.POINTER(ctypes.c_float)
+_ip = ctypes.POINTER(ctypes.c_int)
 
 
 class _Camera(ctypes.Structure):
@@ -85,6 +86,15 @@ def _load():
             lib.fldo_render.restype = None
             lib.fldo_render.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp, _dp,
                                         _dp, ctypes.POINTER(_Camera), _dp, ctypes.c_int]
+            lib.fldo_render_pixels.restype = None
+            lib.fldo_render_pixels.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, _dp, _dp,
+                                               _dp, _dp, ctypes.POINTER(_Camera), _ip, _ip, ctypes.c_long, _dp]
+            lib.fldo_downsample.restype = None
+            lib.fldo_downsample.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, _fp, _fp, _dp,
+                                            _dp, _dp, _dp]
+            lib.fldo_upsample.restype = None
+            lib.fldo_upsample.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                          _dp, _dp]
             lib.fldo_jacobi_iteration.restype = None
             lib.fldo_jacobi_iteration.argtypes = [ctypes.POINTER(_Cfg), _dp, _dp, _dp, _dp, _dp, _dp]
             lib.fldo_pass.restype = None
@@ -254,10 +264,11 @@ def jacobi_iteration(p: Problem, iters: int = 1):
 def render(sigma_t: np.ndarray, albedo: np.ndarray, q: np.ndarray, phi: np.ndarray, h: float, *,
            eye, target, up=(0.0, 1.0, 0.0), fov_deg: float = 40.0, width: int = 64, height: int = 64,
            step: float | None = None, background: float = 0.0, t_min: float = 1e-6,
-           nthreads: int | None = None) -> np.ndarray:
+           nthreads: int | None = None, pixels=None) -> np.ndarray:
     """Primary ray march (Sec. 3): radiance per pixel, shape (height, width),
-    row 0 at the top.  sigma_t, albedo, q (the solver's source: q_ri + j) are
-    unpadded; phi is unpadded or padded (the ghost layer is dropped)."""
+    row 0 at the top (or, with pixels = [(px, py), ...], of those pixels
+    only).  sigma_t, albedo, q (the solver's source: q_ri + j) are unpadded;
+    phi is unpadded or padded (the ghost layer is dropped)."""
     lib = _load()
     sigma_t = np.asarray(sigma_t, dtype=np.float32)
     nz, ny, nx = sigma_t.shape
@@ -275,10 +286,47 @@ def render(sigma_t: np.ndarray, albedo: np.ndarray, q: np.ndarray, phi: np.ndarr
     cam.fov_deg, cam.width, cam.height = float(fov_deg), int(width), int(height)
     cam.step = float(step) if step else 0.5 * h
     cam.background, cam.t_min = float(background), float(t_min)
+    if pixels is not None:
+        pxs = np.ascontiguousarray([p[0] for p in pixels], dtype=np.int32)
+        pys = np.ascontiguousarray([p[1] for p in pixels], dtype=np.int32)
+        out = np.zeros(len(pxs), dtype=np.float64)
+        lib.fldo_render_pixels(nx, ny, nz, float(h), _d(st), _d(ss), _d(qd), _d(ph), ctypes.byref(cam),
+                               pxs.ctypes.data_as(_ip), pys.ctypes.data_as(_ip), len(pxs), _d(out))
+        return out
     img = np.zeros((height, width), dtype=np.float64)
     lib.fldo_render(nx, ny, nz, float(h), _d(st), _d(ss), _d(qd), _d(ph), ctypes.byref(cam), _d(img),
                     int(nthreads or default_threads()))
     return img
+
+
+def downsample(sigma_t: np.ndarray, albedo: np.ndarray, q: np.ndarray, factor: int = 4):
+    """Box averages over factor^3 blocks (Sec. 7's quarter-resolution solve):
+    returns (sigma_t_c, albedo_c, q_c) on the ceil(n / factor) grid."""
+    lib = _load()
+    sigma_t = np.ascontiguousarray(sigma_t, dtype=np.float32)
+    albedo = np.ascontiguousarray(albedo, dtype=np.float32)
+    qd = np.ascontiguousarray(q, dtype=np.float64)
+    nz, ny, nx = sigma_t.shape
+    f = int(factor)
+    shp = ((nz + f - 1) // f, (ny + f - 1) // f, (nx + f - 1) // f)
+    st, al, qc = (np.zeros(shp), np.zeros(shp), np.zeros(shp))
+    lib.fldo_downsample(nx, ny, nz, f, _f(sigma_t), _f(albedo), _d(qd), _d(st), _d(al), _d(qc))
+    return st, al, qc
+
+
+def upsample(phi_c: np.ndarray, fine_shape, h: float, factor: int = 4) -> np.ndarray:
+    """phi of the coarse grid (unpadded or padded) at the fine voxel centres."""
+    lib = _load()
+    nz, ny, nx = fine_shape
+    f = int(factor)
+    shp = ((nz + f - 1) // f, (ny + f - 1) // f, (nx + f - 1) // f)
+    pc = np.asarray(phi_c, dtype=np.float64)
+    if pc.shape == tuple(s + 2 for s in shp):
+        pc = pc[1:-1, 1:-1, 1:-1]
+    pc = np.ascontiguousarray(pc)
+    out = np.zeros((nz, ny, nx))
+    lib.fldo_upsample(nx, ny, nz, float(h), f, _d(pc), _d(out))
+    return out
 
 
 def tonemap(radiance: np.ndarray, exposure: float = 1.0, gamma: float = 2.2) -> np.ndarray:

@@ -718,56 +718,81 @@ typedef struct {
     double f[3], r[3], u[3], tan_half, aspect;
 } render_ctx;
 
+static double render_pixel(const render_ctx *x, int px, int py)
+{
+    const fldo_camera *c = x->cam;
+    const double box[3] = {x->nx * x->h, x->ny * x->h, x->nz * x->h};
+    const double sx = (2.0 * (px + 0.5) / c->width - 1.0) * x->tan_half * x->aspect;
+    const double sy = (1.0 - 2.0 * (py + 0.5) / c->height) * x->tan_half;
+    double d[3], norm = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        d[a] = x->f[a] + sx * x->r[a] + sy * x->u[a];
+        norm += d[a] * d[a];
+    }
+    norm = sqrt(norm);
+    for (int a = 0; a < 3; ++a) d[a] /= norm;
+    /* chord through the box (slab test) */
+    double t0 = 0.0, t1 = INFINITY;
+    int hit = 1;
+    for (int a = 0; a < 3; ++a) {
+        if (d[a] == 0.0) {
+            if (c->eye[a] < 0.0 || c->eye[a] > box[a]) hit = 0;
+            continue;
+        }
+        double ta = (0.0 - c->eye[a]) / d[a], tb = (box[a] - c->eye[a]) / d[a];
+        if (ta > tb) { double tt = ta; ta = tb; tb = tt; }
+        if (ta > t0) t0 = ta;
+        if (tb < t1) t1 = tb;
+    }
+    double L = 0.0, T = 1.0;
+    if (hit && t1 > t0) {
+        const long nseg = (long)ceil((t1 - t0) / c->step);
+        for (long m = 0; m < nseg && T >= c->t_min; ++m) {
+            const double a = t0 + m * c->step;
+            const double b = fmin(a + c->step, t1);
+            const double len = b - a, tm = 0.5 * (a + b);
+            double pos[3];
+            for (int k = 0; k < 3; ++k) pos[k] = c->eye[k] + tm * d[k];
+            const double st = field_trilinear(x->nx, x->ny, x->nz, x->h, x->st, pos);
+            const double ss = field_trilinear(x->nx, x->ny, x->nz, x->h, x->ss, pos);
+            const double q = field_trilinear(x->nx, x->ny, x->nz, x->h, x->q, pos);
+            const double ph = field_trilinear(x->nx, x->ny, x->nz, x->h, x->phi, pos);
+            const double Q = (q + ss * ph) / (4.0 * M_PI);   /* Sec. 3, 4 pi Q */
+            L += T * Q * len;
+            T *= exp(-st * len);
+        }
+    }
+    return L + c->background * T;
+}
+
 static void render_rows(void *vctx, int y0, int y1, int worker)
 {
     (void)worker;
     render_ctx *x = (render_ctx *)vctx;
-    const fldo_camera *c = x->cam;
-    const double box[3] = {x->nx * x->h, x->ny * x->h, x->nz * x->h};
     for (int py = y0; py < y1; ++py)
-        for (int px = 0; px < c->width; ++px) {
-            const double sx = (2.0 * (px + 0.5) / c->width - 1.0) * x->tan_half * x->aspect;
-            const double sy = (1.0 - 2.0 * (py + 0.5) / c->height) * x->tan_half;
-            double d[3], norm = 0.0;
-            for (int a = 0; a < 3; ++a) {
-                d[a] = x->f[a] + sx * x->r[a] + sy * x->u[a];
-                norm += d[a] * d[a];
-            }
-            norm = sqrt(norm);
-            for (int a = 0; a < 3; ++a) d[a] /= norm;
-            /* chord through the box (slab test) */
-            double t0 = 0.0, t1 = INFINITY;
-            int hit = 1;
-            for (int a = 0; a < 3; ++a) {
-                if (d[a] == 0.0) {
-                    if (c->eye[a] < 0.0 || c->eye[a] > box[a]) hit = 0;
-                    continue;
-                }
-                double ta = (0.0 - c->eye[a]) / d[a], tb = (box[a] - c->eye[a]) / d[a];
-                if (ta > tb) { double tt = ta; ta = tb; tb = tt; }
-                if (ta > t0) t0 = ta;
-                if (tb < t1) t1 = tb;
-            }
-            double L = 0.0, T = 1.0;
-            if (hit && t1 > t0) {
-                const long nseg = (long)ceil((t1 - t0) / c->step);
-                for (long m = 0; m < nseg && T >= c->t_min; ++m) {
-                    const double a = t0 + m * c->step;
-                    const double b = fmin(a + c->step, t1);
-                    const double len = b - a, tm = 0.5 * (a + b);
-                    double pos[3];
-                    for (int k = 0; k < 3; ++k) pos[k] = c->eye[k] + tm * d[k];
-                    const double st = field_trilinear(x->nx, x->ny, x->nz, x->h, x->st, pos);
-                    const double ss = field_trilinear(x->nx, x->ny, x->nz, x->h, x->ss, pos);
-                    const double q = field_trilinear(x->nx, x->ny, x->nz, x->h, x->q, pos);
-                    const double ph = field_trilinear(x->nx, x->ny, x->nz, x->h, x->phi, pos);
-                    const double Q = (q + ss * ph) / (4.0 * M_PI);   /* Sec. 3, 4 pi Q */
-                    L += T * Q * len;
-                    T *= exp(-st * len);
-                }
-            }
-            x->image[(long)py * c->width + px] = L + c->background * T;
-        }
+        for (int px = 0; px < x->cam->width; ++px) x->image[(long)py * x->cam->width + px] = render_pixel(x, px, py);
+}
+
+static void setup_camera(render_ctx *x, const fldo_camera *cam)
+{
+    double nf = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        x->f[a] = cam->target[a] - cam->eye[a];
+        nf += x->f[a] * x->f[a];
+    }
+    nf = sqrt(nf);
+    for (int a = 0; a < 3; ++a) x->f[a] /= nf;
+    /* r = f x up, u = r x f */
+    x->r[0] = x->f[1] * cam->up[2] - x->f[2] * cam->up[1];
+    x->r[1] = x->f[2] * cam->up[0] - x->f[0] * cam->up[2];
+    x->r[2] = x->f[0] * cam->up[1] - x->f[1] * cam->up[0];
+    double nr = sqrt(x->r[0] * x->r[0] + x->r[1] * x->r[1] + x->r[2] * x->r[2]);
+    for (int a = 0; a < 3; ++a) x->r[a] /= nr;
+    x->u[0] = x->r[1] * x->f[2] - x->r[2] * x->f[1];
+    x->u[1] = x->r[2] * x->f[0] - x->r[0] * x->f[2];
+    x->u[2] = x->r[0] * x->f[1] - x->r[1] * x->f[0];
+    x->tan_half = tan(0.5 * cam->fov_deg * M_PI / 180.0);
+    x->aspect = (double)cam->width / (double)cam->height;
 }
 
 /* Render the volume: sigma_t, sigma_s, q (= q_ri + j) and phi unpadded
@@ -781,25 +806,70 @@ void fldo_render(int nx, int ny, int nz, double h, const double *sigma_t, const 
     x.st = sigma_t; x.ss = sigma_s; x.q = q; x.phi = phi;
     x.cam = cam;
     x.image = image;
-    double nf = 0.0;
-    for (int a = 0; a < 3; ++a) {
-        x.f[a] = cam->target[a] - cam->eye[a];
-        nf += x.f[a] * x.f[a];
-    }
-    nf = sqrt(nf);
-    for (int a = 0; a < 3; ++a) x.f[a] /= nf;
-    /* r = f x up, u = r x f */
-    x.r[0] = x.f[1] * cam->up[2] - x.f[2] * cam->up[1];
-    x.r[1] = x.f[2] * cam->up[0] - x.f[0] * cam->up[2];
-    x.r[2] = x.f[0] * cam->up[1] - x.f[1] * cam->up[0];
-    double nr = sqrt(x.r[0] * x.r[0] + x.r[1] * x.r[1] + x.r[2] * x.r[2]);
-    for (int a = 0; a < 3; ++a) x.r[a] /= nr;
-    x.u[0] = x.r[1] * x.f[2] - x.r[2] * x.f[1];
-    x.u[1] = x.r[2] * x.f[0] - x.r[0] * x.f[2];
-    x.u[2] = x.r[0] * x.f[1] - x.r[1] * x.f[0];
-    x.tan_half = tan(0.5 * cam->fov_deg * M_PI / 180.0);
-    x.aspect = (double)cam->width / (double)cam->height;
+    setup_camera(&x, cam);
     parallel_planes(cam->height, nthreads, render_rows, &x);
+}
+
+/* The same for `count` single pixels (px[i], py[i]) of the camera's image. */
+void fldo_render_pixels(int nx, int ny, int nz, double h, const double *sigma_t, const double *sigma_s,
+                        const double *q, const double *phi, const fldo_camera *cam, const int *px, const int *py,
+                        long count, double *out)
+{
+    render_ctx x;
+    x.nx = nx; x.ny = ny; x.nz = nz; x.h = h;
+    x.st = sigma_t; x.ss = sigma_s; x.q = q; x.phi = phi;
+    x.cam = cam;
+    x.image = NULL;
+    setup_camera(&x, cam);
+    for (long i = 0; i < count; ++i) out[i] = render_pixel(&x, px[i], py[i]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Quarter-resolution solve (Sec. 7: phi is solved on a grid with a quarter  */
+/* of the data's resolution per axis, then used at full resolution in the    */
+/* ray march).  Downsampling: the coarse voxel (I,J,K) covers the fine       */
+/* voxels f I .. f I + f - 1 per axis (those that exist); sigma_t, sigma_s =  */
+/* albedo sigma_t and the source are averaged over them, and the coarse     */
+/* albedo is mean sigma_s / mean sigma_t (0 where mean sigma_t is 0).        */
+/* Upsampling: phi at each fine voxel centre, blended trilinearly between    */
+/* the coarse voxel centres (clamped to the outermost), the coarse grid's    */
+/* spacing being f h.                                                        */
+/* ------------------------------------------------------------------------ */
+
+void fldo_downsample(int nx, int ny, int nz, int f, const float *sigma_t, const float *albedo, const double *q,
+                     double *sigma_t_c, double *albedo_c, double *q_c)
+{
+    const int cx = (nx + f - 1) / f, cy = (ny + f - 1) / f, cz = (nz + f - 1) / f;
+    for (int K = 0; K < cz; ++K)
+        for (int J = 0; J < cy; ++J)
+            for (int I = 0; I < cx; ++I) {
+                double st = 0.0, ss = 0.0, qq = 0.0;
+                long cnt = 0;
+                for (int k = K * f; k < K * f + f && k < nz; ++k)
+                    for (int j = J * f; j < J * f + f && j < ny; ++j)
+                        for (int i = I * f; i < I * f + f && i < nx; ++i) {
+                            const long v = ((long)k * ny + j) * nx + i;
+                            st += (double)sigma_t[v];
+                            ss += (double)albedo[v] * (double)sigma_t[v];
+                            qq += q[v];
+                            ++cnt;
+                        }
+                const long c = ((long)K * cy + J) * cx + I;
+                sigma_t_c[c] = st / (double)cnt;
+                albedo_c[c] = st > 0.0 ? ss / st : 0.0;
+                q_c[c] = qq / (double)cnt;
+            }
+}
+
+void fldo_upsample(int nx, int ny, int nz, double h, int f, const double *phi_c, double *phi)
+{
+    const int cx = (nx + f - 1) / f, cy = (ny + f - 1) / f, cz = (nz + f - 1) / f;
+    for (int k = 0; k < nz; ++k)
+        for (int j = 0; j < ny; ++j)
+            for (int i = 0; i < nx; ++i) {
+                const double x[3] = {(i + 0.5) * h, (j + 0.5) * h, (k + 0.5) * h};
+                phi[((long)k * ny + j) * nx + i] = field_trilinear(cx, cy, cz, f * h, phi_c, x);
+            }
 }
 
 void fldo_limiter_array(int kind, double larsen_n, const double *R, double *F, long count)
