@@ -73,7 +73,9 @@ def parse_args():
     ap.add_argument("--c3-limiters", default="lp,kershaw,larsen", help="c3 workload: limiters (comma list)")
     ap.add_argument("--c3-oracle-n", type=int, default=32,
                     help="c3 workload: edge of the same-recipe solves compared with the FP64 oracle's fixed point")
-    ap.add_argument("--workload", choices=["cloud", "batch", "serve", "c3"], default="cloud",
+    ap.add_argument("--scenes", default="nebulae,manix,explosion", help="pipeline workload: scenes")
+    ap.add_argument("--factor", type=int, default=4, help="pipeline workload: coarsening of the phi grid")
+    ap.add_argument("--workload", choices=["cloud", "batch", "serve", "c3", "pipeline"], default="cloud",
                     help="cloud: the 128^3 solve (default); batch: independent solves of uneven size, "
                          "batched in shared launches vs one after another")
     ap.add_argument("--count", type=int, default=16, help="batch workload: number of solves")
@@ -328,6 +330,7 @@ def run_gpu(args):
     extras = {}
     if ranks.rank == 0 and not args.no_extras:
         extras["roofline_hbm_resident"] = roofline_256(fld, torch, dev, sig_np, alb_np, roof)
+        extras["roofline_jacobi"] = roofline_jacobi(fld, torch, dev, sig_np, alb_np, peak, peak_src)
         extras["e2e"] = e2e_measure(fld, g, sig_np, alb_np, p, n, args)
         extras["cpu_baseline"] = cpu_baseline(sig_np, alb_np, n, args.cpu_seconds)
     g.close()
@@ -382,6 +385,41 @@ def roofline_256(fld, torch, dev, sig_np, alb_np, roof):
             out[fam] = roof(fam, ms, it, n ** 3, f"cloud{n}", False)
     finally:
         g.close()
+    return out
+
+
+def roofline_jacobi(fld, torch, dev, sig_np, alb_np, peak, peak_src):
+    """Throughput of the Jacobi variant (FP32): per iteration one fresh-D pass
+    (reads phi, sigma'; writes D: 12 B per voxel) and one update pass (reads
+    phi, D, sigma_a' dl^2, j dl^2; writes phi': 20 B per voxel) over every
+    unknown, at 128^3 and at 256^3 (the medium tiled 2x2x2)."""
+    import numpy as np
+    out = {}
+    stream = torch.cuda.Stream(device=dev)
+    for rep in (1, 2):
+        n = rep * sig_np.shape[0]
+        sig = torch.from_numpy(np.tile(sig_np, (rep,) * 3)).to(dev)
+        alb = torch.from_numpy(np.tile(alb_np, (rep,) * 3)).to(dev)
+        torch.cuda.synchronize()
+        g = fld.Grid(n, n, n, 1.0 / n, stream=stream.cuda_stream)
+        try:
+            g.set_medium(sig, alb)
+            g.bake_directional((0.0, 0.0, -1.0), 1.0)
+            p = fld.params(limiter="lp", precision="fp32", scheme="jacobi", tol=0.0, check_every=64, max_iters=64)
+            g.solve(p, check=False)
+            p.warm_start = 1
+            r = g.solve(p, check=False)
+            it_s = r.ms_sweep_fp32 / 1e3 / r.iterations_fp32
+            alg = 32 * n ** 3
+            ach = alg / it_s / 1e9
+            out[f"cloud{n}"] = {"bound": "hbm", "kernel": "k_fresh_D_f + k_jacobi<float> (one Jacobi iteration)",
+                                "achieved": round(ach, 1), "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                                "traffic": None, "algorithmic_bytes_per_iteration": alg,
+                                "iteration_us": round(it_s * 1e6, 3), "iterations_measured": r.iterations_fp32,
+                                "voxel_updates_per_s": n ** 3 / it_s, "peak_source": peak_src,
+                                "l2_resident": n <= 128}
+        finally:
+            g.close()
     return out
 
 
@@ -747,10 +785,12 @@ def run_c3(args):
             g.close()
             ref, ref_rel = {}, {}
             for bf in (True, False):
+                # the fixed point does not depend on omega: a conservative one
+                # keeps the FP64 reference solve from cycling
                 prob = oracle.make_problem(sig, alb, j, 1.0 / m, limiter=lim, larsen_n=2.0, local_iters=2,
-                                           medium_bf16=bf)
+                                           omega=1.5, medium_bf16=bf)
                 oracle.init_state(prob)
-                _, ref_rel[bf], _ = oracle.solve(prob, tol=1e-10, max_iters=400000, check_every=50)
+                _, ref_rel[bf], _ = oracle.solve(prob, tol=1e-10, max_iters=100000, check_every=50)
                 ref[bf] = prob.phi[1:-1, 1:-1, 1:-1]
             inner = phi[1:-1, 1:-1, 1:-1]
             l2 = float(np.linalg.norm(inner - ref[True]) / np.linalg.norm(ref[True]))
@@ -781,6 +821,93 @@ def run_c3(args):
     print(json.dumps(line), flush=True)
 
 
+# The paper's end-to-end render times (GTX TITAN, single precision, solve to
+# Rbar/jbar = 1e-4 on a grid of a quarter of the data's resolution, light bake
+# and 1024^2 primary ray march included; Sec. 7, Figs. 1, 8, 9): context only.
+PAPER_RENDER_S = {"nebulae": 0.6, "manix": 1.8, "explosion": 0.7}
+
+
+def run_pipeline(args):
+    """The paper's timed workload, end to end, on synthetic stand-ins of its
+    three scenes (fld_inputs.paper_scene): per colour channel the light bake
+    (plus emission) at full resolution, the box-averaged medium and source on
+    a grid of 1/factor the resolution, the FLD solve there (to the paper's
+    1e-4 and to 1e-6; three channels solved as one batch), and the 1024^2
+    primary ray march at full resolution with phi upsampled.  Stages timed
+    with CUDA events on one stream, inputs resident on the device; the median
+    of --steps runs after --warmup."""
+    import numpy as np
+    import torch
+
+    import fld_inputs
+    import paper_1403_8105_gb300 as fld
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    fld.load(build_if_missing=True)
+    stream = torch.cuda.Stream(device=dev)
+    f = args.factor
+    rows = []
+    for name in [x for x in args.scenes.split(",") if x]:
+        sc = fld_inputs.paper_scene(name)
+        nz, ny, nx = sc.sigma_t.shape
+        cx, cy, cz = (nx + f - 1) // f, (ny + f - 1) // f, (nz + f - 1) // f
+        sig = torch.from_numpy(sc.sigma_t).to(dev)
+        albs = [torch.from_numpy(a).to(dev) for a in sc.albedos]
+        emis = torch.from_numpy(sc.emission).to(dev) if sc.emission is not None else None
+        torch.cuda.synchronize()
+        fine = [fld.Grid(nx, ny, nz, sc.h, stream=stream.cuda_stream) for _ in albs]
+        coarse = [fld.Grid(cx, cy, cz, f * sc.h, stream=stream.cuda_stream) for _ in albs]
+        box = (nx * sc.h, ny * sc.h, nz * sc.h)
+        ctr = tuple(0.5 * b for b in box)
+        cam = fld.camera(eye=(ctr[0] + 0.35 * box[1], ctr[1] + 0.45 * box[1], ctr[2] - 2.1 * box[1]), target=ctr,
+                         fov_deg=40.0, width=1024, height=1024, background=0.05)
+        images = [torch.empty((1024, 1024), dtype=torch.float32, device=dev) for _ in albs]
+        for tol in (1e-4, 1e-6):
+            p = fld.params(limiter="lp", precision="mixed", tol=tol, check_every=64, max_iters=args.max_iters)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+            runs = []
+            for it in range(args.warmup + args.steps):
+                with torch.cuda.stream(stream):
+                    stream.synchronize()
+                    ev[0].record(stream)
+                    for g, a in zip(fine, albs):
+                        g.set_medium(sig, a)
+                        if emis is not None:
+                            g.set_source(emis)
+                        g.bake_directional(sc.light_dir, sc.light_radiance, accumulate=1 if emis is not None else 0)
+                    ev[1].record(stream)
+                    for g, c in zip(fine, coarse):
+                        g.downsample_to(c, f)
+                    ev[2].record(stream)
+                    if len(coarse) == 1:
+                        rs = [coarse[0].solve(p)]
+                    else:
+                        st, rs = fld.fld_solve_batch(coarse, p)
+                    ev[3].record(stream)
+                    for g, c, img in zip(fine, coarse, images):
+                        fld.fld_render(g.handle, c.handle, cam, img, None, 1.0, 2.2)
+                    ev[4].record(stream)
+                    ev[4].synchronize()
+                if it >= args.warmup:
+                    ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(4)]
+                    runs.append({"bake_ms": ms[0], "downsample_ms": ms[1], "solve_ms": ms[2], "render_ms": ms[3],
+                                 "total_ms": sum(ms), "iterations": [r.iterations for r in rs],
+                                 "rel_residual": [r.rel_residual for r in rs],
+                                 "status": [fld.fld_status_string(r.status) for r in rs]})
+            med = sorted(runs, key=lambda r: r["total_ms"])[len(runs) // 2]
+            rows.append({"scene": name, "grid": [nx, ny, nz], "phi_grid": [cx, cy, cz], "channels": len(albs),
+                         "tol": tol, **med, "paper_s_gtx_titan_tol_1e-4": PAPER_RENDER_S.get(name),
+                         "image_mean_radiance": [float(img.mean()) for img in images]})
+            print(json.dumps({"pipeline_case": rows[-1]}), flush=True)
+        for g in fine + coarse:
+            g.close()
+    line = {"metric": "end-to-end render time (light bake + FLD solve at 1/%d resolution + 1024^2 ray march)" % f,
+            "unit": "ms", "higher_is_better": False, "n_gpus": 1, "data": "synthetic stand-ins of the paper's scenes",
+            "steps": args.steps, "warmup": args.warmup, "cases": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -791,6 +918,8 @@ def main():
         run_serve(args)
     elif args.workload == "c3":
         run_c3(args)
+    elif args.workload == "pipeline":
+        run_pipeline(args)
     else:
         run_gpu(args)
 
