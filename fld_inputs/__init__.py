@@ -213,3 +213,44 @@ def batch_cases(count: int = 64, seed: int = 1234,
             light = Light(kind="point", pos=p, power=4.0 * np.pi * float(np.sum((np.array(p) - 0.5) ** 2)))
         specs.append(dict(n=n, seed=s, albedo=a, light=light))
     return specs
+
+
+@dataclasses.dataclass
+class Scene:
+    """A synthetic stand-in for one of the paper's rendered datasets."""
+    name: str
+    sigma_t: np.ndarray           # (nz, ny, nx) float32
+    albedos: list                 # one (nz, ny, nx) float32 albedo per colour channel
+    emission: np.ndarray | None   # (nz, ny, nx) float32 self-emission j, or None
+    h: float
+    light_dir: tuple              # direction the light travels
+    light_radiance: float
+
+
+def paper_scene(name: str) -> Scene:
+    """Stand-ins for the paper's three rendered datasets, with their grid
+    shapes (Sec. 7): "nebulae" -- 200^3, albedo 0.9, one directional light;
+    "manix" -- 256 x 329 x 256 (x, y, z), extinction and a per-channel (RGB)
+    albedo from one density via a transfer function; "explosion" -- 201 x
+    272 x 230, albedo 1, a black-body-like emission field from a second noise
+    field ("temperature", j ~ T^4 where hot) plus the light.  The densities
+    are fBm sphere clouds (cloud_medium); the light comes from above."""
+    light = (0.25, -1.0, -0.35)
+    if name == "nebulae":
+        sig, alb = cloud_medium(200, seed=11, albedo=0.9)
+        return Scene(name, sig, [alb], None, 1.0 / 200, light, 1.0)
+    if name == "manix":
+        nx, ny, nz = 256, 329, 256
+        sig, _ = cloud_medium(nx, seed=12, albedo=1.0, ny=ny, nz=nz)
+        d = sig / max(float(sig.max()), 1e-30)                 # density in [0, 1]
+        # transfer function: dense "bone" scatters white, thin "tissue" reddish
+        base = ((0.97, 0.25), (0.85, 0.45), (0.75, 0.6))         # (albedo at d = 0, drop to d = 1) per channel
+        albs = [np.clip(a0 - drop * (1.0 - d) * (d > 0), 0.0, 1.0).astype(np.float32) for a0, drop in base]
+        return Scene(name, sig, albs, None, 1.0 / ny, light, 1.0)
+    if name == "explosion":
+        nx, ny, nz = 201, 272, 230
+        sig, alb = cloud_medium(nx, seed=13, albedo=1.0, ny=ny, nz=nz)
+        temp = fbm_noise(nx, ny, nz, 1.0 / ny, seed=14)
+        j = (40.0 * np.maximum(0.0, temp - 0.55) ** 4 / 0.45 ** 4) * (sig > 0)
+        return Scene(name, sig, [alb], j.astype(np.float32), 1.0 / ny, light, 1.0)
+    raise ValueError(f"unknown scene {name!r}")

@@ -88,6 +88,15 @@ typedef enum { FLD_MEM_HOST = 0, FLD_MEM_DEVICE = 1 } fld_mem;
  *         updates summed in FP32 with the approximate D of the bulk sweeps. */
 typedef enum { FLD_PREC_FP64 = 0, FLD_PREC_FP32 = 1, FLD_PREC_MIXED = 2, FLD_PREC_PAIR = 3 } fld_precision;
 
+/* Iteration scheme.  RED_BLACK: Algorithm 1, the red unknowns (i+j+k even)
+ * then the black ones, each update using the newest neighbours and D
+ * (Gauss-Seidel order), over-relaxed by omega (Eq. 36).  JACOBI: every
+ * unknown from the previous iterate only -- D^k = F(R(phi^k))/sigma' at all
+ * unknowns (Eq. 33-35), then phi^{k+1} from phi^k and D^k (Eq. 32) into a
+ * second buffer, damped by omega <= 1.  Both have the same fixed point (Eq.
+ * 31); Jacobi needs many more iterations and runs in FP32 or FP64 only. */
+typedef enum { FLD_SCHEME_RED_BLACK = 0, FLD_SCHEME_JACOBI = 1 } fld_scheme;
+
 typedef struct {
     int limiter;          /* fld_limiter                                             */
     double larsen_n;      /* n of Larsen-n, > 0 (default 2)                          */
@@ -136,6 +145,9 @@ typedef struct {
                              is that of the rounded medium.  The rounding moves
                              the medium by at most 2^-8 relative.  0 (default):
                              the single-precision medium.  Not in the paper.  */
+    int scheme;           /* fld_scheme (default RED_BLACK).  JACOBI: precision
+                             FP32 or FP64, 0 < omega <= 1 (<= 0 selects 1), no
+                             warm-up; local_iters does not apply               */
 } fld_solve_params;
 
 typedef struct {
@@ -313,6 +325,55 @@ fld_status fld_residual(fld_grid g, const fld_solve_params *p, double *rel);
 fld_status fld_residual_noalloc(int nx, int ny, int nz, double h, const fld_solve_params *p,
                                 const float *sigma_t, const float *albedo, const float *j,
                                 const double *phi, const double *D, double *rel, void *stream);
+
+/* Primary ray march of the rendered image (Sec. 3): each pixel's radiance is
+ * the background attenuated over the ray's chord through the grid's box
+ * [0, nx h] x [0, ny h] x [0, nz h] plus, over march segments of length
+ * `step`, the transmittance between the segment and the camera times
+ * Q x step, with 4 pi Q = q + sigma_s phi (Sec. 3: q = the grid's source
+ * field, i.e. q_ri + j after a bake; sigma_s = albedo sigma_t, raw; phi =
+ * the grid's current fluence).  Fields are blended trilinearly between voxel
+ * centres (clamped to the outermost centres) at each segment's midpoint; the
+ * last segment ends at the exit; the transmittance to a segment covers the
+ * segments before it.  The march stops where the transmittance falls below
+ * t_min.  The camera is a pinhole at `eye` looking at `target`; `up` fixes
+ * the roll; rows run top to bottom.  Not fixed by the paper: the camera
+ * model, the trilinear sampling and the segment placement. */
+typedef struct {
+    double eye[3], target[3], up[3];
+    double fov_deg;        /* vertical field of view, in (0, 180) degrees        */
+    int width, height;     /* pixels, 1 .. 16384 each                            */
+    double step;           /* segment length; <= 0 selects h / 2                 */
+    double background;     /* radiance entering the far end of every ray, >= 0   */
+    double t_min;          /* stop below this transmittance; < 0 selects 1e-6    */
+} fld_camera;
+
+/* Render the grid (needs a medium, a source and a state, e.g. after
+ * fld_solve).  phi_grid: NULL to take phi from g itself, or a coarser grid
+ * covering g's box whose solved phi is blended trilinearly (between its
+ * voxel centres) to g's voxel centres before the march -- the
+ * quarter-resolution solve of Sec. 7 (see fld_downsample).  radiance:
+ * width*height floats, row-major, or NULL; codes:
+ * width*height bytes of round(255 min(1, (exposure L)^(1/gamma))), the gamma
+ * compression of Sec. 7, or NULL (one of the two must be given).  `where`
+ * (fld_mem) applies to both outputs; with host outputs the call returns when
+ * they are written.  Keeps a 16-byte-per-voxel sampling volume with the
+ * grid.  Errors: FLD_ERR_INVALID_ARG for a bad camera, exposure <= 0 or
+ * gamma <= 0; FLD_ERR_STATE without a medium or a state. */
+fld_status fld_render(fld_grid g, fld_grid phi_grid, const fld_camera *cam, float *radiance, unsigned char *codes,
+                      double exposure, double gamma, int where);
+
+/* Quarter-resolution solve (Sec. 7: phi is solved on a grid with a quarter
+ * of the data's resolution per axis, the multiply scattered light being much
+ * smoother than the medium): set the coarse grid's medium and source from
+ * the fine grid's by box averages over factor^3 blocks -- sigma_t and the
+ * source averaged, the albedo as mean(albedo sigma_t) / mean(sigma_t) (0 in
+ * vacuum); partial blocks at the far faces average the voxels that exist.
+ * coarse must have ceil(n / factor) voxels per axis and spacing factor * h.
+ * The paper gives no averaging rule: the box average is this library's.
+ * Errors: FLD_ERR_INVALID_ARG for mismatched grids, FLD_ERR_STATE without a
+ * fine medium. */
+fld_status fld_downsample(fld_grid fine, fld_grid coarse, int factor);
 
 /* Free the grid and everything it owns (NULL is ignored). */
 void fld_destroy(fld_grid g);

@@ -37,6 +37,7 @@ FLD_ERR_NOT_CONVERGED, FLD_ERR_DIVERGED, FLD_ERR_NO_DEVICE = 5, 6, 7
 FLD_MEM_HOST, FLD_MEM_DEVICE = 0, 1
 LIMITERS = {"cda": 0, "sum": 1, "max": 2, "kershaw": 3, "larsen": 4, "lp": 5}
 PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2, "pair": 3}
+SCHEMES = {"red_black": 0, "rb": 0, "jacobi": 1}
 
 
 class SolveParams(ctypes.Structure):
@@ -48,7 +49,7 @@ class SolveParams(ctypes.Structure):
         ("precision", ctypes.c_int), ("fp32_switch", ctypes.c_double), ("residual_margin", ctypes.c_int),
         ("warm_start", ctypes.c_int), ("phi0", ctypes.c_double), ("D0", ctypes.c_double),
         ("phi_b", ctypes.c_double), ("D_b", ctypes.c_double), ("warmup_iters", ctypes.c_int),
-        ("medium_bf16", ctypes.c_int),
+        ("medium_bf16", ctypes.c_int), ("scheme", ctypes.c_int),
     ]
 
 
@@ -64,6 +65,26 @@ class SolveResult(ctypes.Structure):
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class Camera(ctypes.Structure):
+    """Mirror of fld_camera (fld.h)."""
+    _fields_ = [
+        ("eye", ctypes.c_double * 3), ("target", ctypes.c_double * 3), ("up", ctypes.c_double * 3),
+        ("fov_deg", ctypes.c_double), ("width", ctypes.c_int), ("height", ctypes.c_int),
+        ("step", ctypes.c_double), ("background", ctypes.c_double), ("t_min", ctypes.c_double),
+    ]
+
+
+def camera(eye, target, up=(0.0, 1.0, 0.0), fov_deg=40.0, width=1024, height=1024, step=0.0, background=0.0,
+           t_min=-1.0) -> Camera:
+    c = Camera()
+    c.eye[:] = [float(v) for v in eye]
+    c.target[:] = [float(v) for v in target]
+    c.up[:] = [float(v) for v in up]
+    c.fov_deg, c.width, c.height = float(fov_deg), int(width), int(height)
+    c.step, c.background, c.t_min = float(step), float(background), float(t_min)
+    return c
 
 
 class FldError(RuntimeError):
@@ -121,6 +142,8 @@ def load(build_if_missing: bool = True):
             "fld_residual": (c_int, [_vp, P, ctypes.POINTER(c_double)]),
             "fld_residual_noalloc": (c_int, [c_int, c_int, c_int, c_double, P, _vp, _vp, _vp, _vp, _vp,
                                              ctypes.POINTER(c_double), _vp]),
+            "fld_render": (c_int, [_vp, _vp, ctypes.POINTER(Camera), _vp, _vp, c_double, c_double, c_int]),
+            "fld_downsample": (c_int, [_vp, _vp, c_int]),
             "fld_destroy": (None, [_vp]),
             "fld_status_string": (ctypes.c_char_p, [c_int]),
             "fld_last_error": (ctypes.c_char_p, []),
@@ -148,7 +171,7 @@ def _ptr(a, dtype):
         is_tensor = False
     if is_tensor:
         import torch
-        want = {np.float32: torch.float32, np.float64: torch.float64}[dtype]
+        want = {np.float32: torch.float32, np.float64: torch.float64, np.uint8: torch.uint8}[dtype]
         if a.dtype != want or not a.is_contiguous():
             raise TypeError(f"expected a contiguous {want} tensor")
         return ctypes.c_void_p(a.data_ptr()), (FLD_MEM_DEVICE if a.is_cuda else FLD_MEM_HOST), a
@@ -197,6 +220,21 @@ def fld_set_source(g, j) -> None:
 def fld_get_source(g, out) -> None:
     pj, w, k = _ptr(out, np.float32)
     _check(load().fld_get_source(g, pj, w), "fld_get_source")
+
+
+def fld_downsample(fine, coarse, factor: int = 4) -> None:
+    _check(load().fld_downsample(fine, coarse, int(factor)), "fld_downsample")
+
+
+def fld_render(g, phi_grid, cam: Camera, radiance=None, codes=None, exposure: float = 1.0,
+               gamma: float = 2.2) -> None:
+    pr, w1, k1 = _ptr(radiance, np.float32) if radiance is not None else (None, None, None)
+    pc, w2, k2 = _ptr(codes, np.uint8) if codes is not None else (None, None, None)
+    ws = {w for w in (w1, w2) if w is not None}
+    if len(ws) > 1:
+        raise ValueError("radiance and codes must live in the same kind of memory")
+    _check(load().fld_render(g, phi_grid, ctypes.byref(cam), pr, pc, float(exposure), float(gamma),
+                             ws.pop() if ws else FLD_MEM_HOST), "fld_render")
 
 
 def fld_bake_directional(g, direction, radiance: float = 1.0, step: float = 0.0, accumulate: int = 0) -> None:
@@ -363,6 +401,8 @@ def params(**kw) -> SolveParams:
             v = LIMITERS[v]
         if k == "precision" and isinstance(v, str):
             v = PRECISIONS[v]
+        if k == "scheme" and isinstance(v, str):
+            v = SCHEMES[v]
         if not hasattr(p, k):
             raise AttributeError(f"SolveParams has no field {k!r}")
         setattr(p, k, v)
@@ -415,6 +455,18 @@ class Grid:
 
     def bake_point(self, pos, power=1.0, step=0.0, accumulate=0):
         fld_bake_point(self.handle, pos, power, step, accumulate)
+
+    def render(self, cam: Camera, exposure=1.0, gamma=2.2, codes=False, phi_grid=None):
+        """(radiance, codes or None) as host arrays of shape (height, width);
+        phi_grid: a coarser solved Grid to take phi from (upsampled)."""
+        rad = np.empty((cam.height, cam.width), np.float32)
+        cod = np.empty((cam.height, cam.width), np.uint8) if codes else None
+        fld_render(self.handle, phi_grid.handle if phi_grid is not None else None, cam, rad, cod, exposure, gamma)
+        return rad, cod
+
+    def downsample_to(self, coarse: "Grid", factor: int = 4):
+        """Set coarse's medium and source from this grid's (box averages)."""
+        fld_downsample(self.handle, coarse.handle, factor)
 
     def set_state(self, phi=None, D=None):
         fld_set_state(self.handle, phi, D)

@@ -63,7 +63,7 @@ struct GraphEntry {
 
 bool same_params(const PassParams &a, const PassParams &b) {
     return a.lim == b.lim && a.local_iters == b.local_iters && a.larsen_n == b.larsen_n && a.omega == b.omega &&
-           a.inv2h == b.inv2h && a.floor_ == b.floor_ && a.bf16 == b.bf16 && a.h2 == b.h2;
+           a.inv2h == b.inv2h && a.floor_ == b.floor_ && a.bf16 == b.bf16 && a.h2 == b.h2 && a.scheme == b.scheme;
 }
 
 }  // namespace
@@ -130,6 +130,19 @@ fld_status ensure_bf16(fld_grid_s *g) {
     return FLD_OK;
 }
 
+// Second phi buffer of the Jacobi scheme (allocated outside graph capture).
+fld_status ensure_jacobi(fld_grid_s *g, Family fam) {
+    const size_t n = (size_t)g->L.total;
+    cudaError_t e = cudaSuccess;
+    if (fam == FAM_F64 && !g->f.phi642) e = cudaMalloc((void **)&g->f.phi642, sizeof(double) * n);
+    if (fam != FAM_F64 && !g->f.phi2) e = cudaMalloc((void **)&g->f.phi2, sizeof(float) * n);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        return fail(FLD_ERR_OOM, "cudaMalloc of the Jacobi buffer failed");
+    }
+    return FLD_OK;
+}
+
 // sigma_eps = 1e-3 / L with L the largest grid extent (Sec. 5), unless given.
 double sigma_eps_of(const fld_grid_s *g, const fld_solve_params *p) {
     if (p->sigma_eps > 0.0) return p->sigma_eps;
@@ -141,6 +154,7 @@ double sigma_eps_of(const fld_grid_s *g, const fld_solve_params *p) {
 
 double omega_of(const fld_grid_s *g, const fld_solve_params *p) {
     if (p->omega > 0.0) return p->omega;
+    if (p->scheme == FLD_SCHEME_JACOBI) return 1.0;
     int n = g->nx;
     if (g->ny > n) n = g->ny;
     if (g->nz > n) n = g->nz;
@@ -157,7 +171,7 @@ double omega_of(const fld_grid_s *g, const fld_solve_params *p) {
 // it, stays stable once the first sweeps have spread the source.
 int warmup_of(const fld_grid_s *g, const fld_solve_params *p) {
     if (p->warmup_iters >= 0) return p->warmup_iters;
-    if (p->warm_start) return 0;
+    if (p->warm_start || p->scheme == FLD_SCHEME_JACOBI) return 0;
     int n = g->nx;
     if (g->ny > n) n = g->ny;
     if (g->nz > n) n = g->nz;
@@ -209,6 +223,7 @@ fld_status prepare(fld_grid_s *g, const fld_solve_params *p, Family fam) {
     if (fam == FAM_F64) {
         st = ensure_f64(g);
         if (st != FLD_OK) return st;
+        if (p->scheme == FLD_SCHEME_JACOBI && (st = ensure_jacobi(g, fam)) != FLD_OK) return st;
         if (g->prepared_d != g->version || g->prepared_seps_d != seps || g->prepared_bf16_d != bf) {
             FLD_CK(launch_prep_d(g->L, g->f, seps, h2, bf != 0, g->stream));
             g->kernels += 1;
@@ -218,6 +233,7 @@ fld_status prepare(fld_grid_s *g, const fld_solve_params *p, Family fam) {
         }
     } else {
         if (bf && (st = ensure_bf16(g)) != FLD_OK) return st;
+        if (p->scheme == FLD_SCHEME_JACOBI && (st = ensure_jacobi(g, fam)) != FLD_OK) return st;
         if (g->prepared_f != g->version || g->prepared_seps_f != seps || g->prepared_bf16_f != bf) {
             FLD_CK(launch_prep_f(g->L, g->f, (float)seps, (float)h2, bf != 0, g->stream));
             g->kernels += 1;
@@ -239,6 +255,7 @@ PassParams pass_params(const fld_grid_s *g, const fld_solve_params *p) {
     const double eps = p->eps > 0.0 ? p->eps : 1e-20;
     q.floor_ = g->jbar > 0.0 ? eps * g->jbar : kFloorNoEmission;
     q.bf16 = p->medium_bf16 ? 1 : 0;
+    q.scheme = p->scheme;
     q.h2 = g->h * g->h;
     return q;
 }
@@ -309,6 +326,19 @@ fld_status sync_family(fld_grid_s *g, Family fam) {
 }
 
 fld_status enqueue_iterations(fld_grid_s *g, Family fam, const PassParams &pp, int iters) {
+    if (pp.scheme == FLD_SCHEME_JACOBI) {
+        // ping-pong between phi and its second buffer; the second buffer first
+        // takes phi whole (its ghosts), and an odd count ends with a copy back
+        const bool d = fam == FAM_F64;
+        const size_t bytes = (d ? sizeof(double) : sizeof(float)) * (size_t)g->L.total;
+        void *a = d ? (void *)g->f.phi64 : (void *)g->f.phi;
+        void *b = d ? (void *)g->f.phi642 : (void *)g->f.phi2;
+        if (!b) return fail(FLD_ERR_STATE, "the Jacobi buffer is not allocated");
+        FLD_CK(cudaMemcpyAsync(b, a, bytes, cudaMemcpyDeviceToDevice, g->stream));
+        for (int it = 0; it < iters; ++it) FLD_CK(launch_jacobi(fam, g->L, g->f, pp, (it & 1) == 0, g->stream));
+        if (iters & 1) FLD_CK(cudaMemcpyAsync(a, b, bytes, cudaMemcpyDeviceToDevice, g->stream));
+        return FLD_OK;
+    }
     for (int it = 0; it < iters; ++it)
         for (int colour = 0; colour < 2; ++colour) FLD_CK(launch_pass(fam, g->L, g->f, pp, colour, g->stream));
     return FLD_OK;
@@ -372,6 +402,13 @@ fld_status check_params(const fld_grid_s *g, const fld_solve_params *p) {
     if (p->residual_margin < 0) return fail(FLD_ERR_INVALID_ARG, "residual_margin must be >= 0");
     if (p->medium_bf16 != 0 && p->medium_bf16 != 1) return fail(FLD_ERR_INVALID_ARG, "medium_bf16 must be 0 or 1");
     if (p->warmup_iters < -1) return fail(FLD_ERR_INVALID_ARG, "warmup_iters must be >= -1");
+    if (p->scheme != FLD_SCHEME_RED_BLACK && p->scheme != FLD_SCHEME_JACOBI)
+        return fail(FLD_ERR_INVALID_ARG, "unknown scheme");
+    if (p->scheme == FLD_SCHEME_JACOBI) {
+        if (p->precision != FLD_PREC_FP32 && p->precision != FLD_PREC_FP64)
+            return fail(FLD_ERR_INVALID_ARG, "the Jacobi scheme runs in FP32 or FP64 precision");
+        if (p->omega > 1.0) return fail(FLD_ERR_INVALID_ARG, "the Jacobi scheme needs omega <= 1");
+    }
     (void)g;
     return FLD_OK;
 }
@@ -659,7 +696,7 @@ void fld_destroy(fld_grid g) {
         if (e.exec) cudaGraphExecDestroy(e.exec);
     void *ptrs[] = {g->f.sp, g->f.ah2, g->f.jh2, g->f.phi, g->f.phlo, g->f.D, g->f.Df, g->f.sp64, g->f.ah264,
                     g->f.jh264, g->f.phi64, g->f.D64, g->f.Df64, g->f.sigma_t, g->f.albedo, g->f.jsrc,
-                    g->f.partials, g->f.result, g->f.spb, g->f.sab};
+                    g->f.partials, g->f.result, g->f.spb, g->f.sab, g->f.phi2, g->f.phi642, g->f.render_vol};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (g->ev0) cudaEventDestroy(g->ev0);
@@ -708,6 +745,120 @@ fld_status fld_get_source(fld_grid g, float *j, int where) {
     const cudaMemcpyKind kind = where == FLD_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     FLD_CK(cudaMemcpyAsync(j, g->f.jsrc, sizeof(float) * (size_t)nvox(g), kind, g->stream));
     if (where != FLD_MEM_DEVICE) FLD_CK(cudaStreamSynchronize(g->stream));
+    return FLD_OK;
+}
+
+fld_status fld_downsample(fld_grid fine, fld_grid coarse, int factor) {
+    fld_status st = enter(fine);
+    if (st != FLD_OK) return st;
+    if (!coarse || coarse == fine) return fail(FLD_ERR_INVALID_ARG, "coarse must be another grid");
+    if (coarse->device != fine->device) return fail(FLD_ERR_INVALID_ARG, "the grids live on different devices");
+    if (factor < 1) return fail(FLD_ERR_INVALID_ARG, "factor must be >= 1");
+    if (coarse->nx != (fine->nx + factor - 1) / factor || coarse->ny != (fine->ny + factor - 1) / factor ||
+        coarse->nz != (fine->nz + factor - 1) / factor)
+        return fail(FLD_ERR_INVALID_ARG, "the coarse grid must have ceil(n / factor) voxels per axis");
+    if (fabs(coarse->h - factor * fine->h) > 1e-9 * factor * fine->h)
+        return fail(FLD_ERR_INVALID_ARG, "the coarse grid's h must be factor * h");
+    if (!fine->has_medium) return fail(FLD_ERR_STATE, "the fine grid has no medium");
+    FLD_CK(cudaStreamSynchronize(fine->stream));
+    FLD_CK(launch_downsample(fine->L, fine->f, factor, coarse->L, coarse->f, coarse->stream));
+    coarse->kernels += 1;
+    coarse->has_medium = true;
+    ++coarse->version;
+    return FLD_OK;
+}
+
+fld_status fld_render(fld_grid g, fld_grid phi_grid, const fld_camera *cam, float *radiance, unsigned char *codes,
+                      double exposure, double gamma, int where) {
+    fld_status st = enter(g);
+    if (st != FLD_OK) return st;
+    fld_grid_s *pg = phi_grid ? phi_grid : g;
+    if (pg->device != g->device) return fail(FLD_ERR_INVALID_ARG, "the phi grid lives on another device");
+    if (pg != g && (pg->nx * pg->h < g->nx * g->h * (1 - 1e-9) || pg->ny * pg->h < g->ny * g->h * (1 - 1e-9) ||
+                    pg->nz * pg->h < g->nz * g->h * (1 - 1e-9)))
+        return fail(FLD_ERR_INVALID_ARG, "the phi grid must cover the rendered grid's box");
+    if (!cam) return fail(FLD_ERR_INVALID_ARG, "camera is NULL");
+    if (!radiance && !codes) return fail(FLD_ERR_INVALID_ARG, "radiance and codes are both NULL");
+    if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
+        return fail(FLD_ERR_INVALID_ARG, "image size must be 1 .. 16384 per side");
+    if (!(cam->fov_deg > 0.0 && cam->fov_deg < 180.0)) return fail(FLD_ERR_INVALID_ARG, "fov_deg must be in (0, 180)");
+    if (!(exposure > 0.0) || !(gamma > 0.0) || !isfinite(exposure) || !isfinite(gamma))
+        return fail(FLD_ERR_INVALID_ARG, "exposure and gamma must be > 0");
+    if (!(cam->background >= 0.0) || !isfinite(cam->background)) return fail(FLD_ERR_INVALID_ARG, "bad background");
+    for (int k = 0; k < 3; ++k)
+        if (!isfinite(cam->eye[k]) || !isfinite(cam->target[k]) || !isfinite(cam->up[k]))
+            return fail(FLD_ERR_INVALID_ARG, "camera vectors must be finite");
+    if (!g->has_medium) return fail(FLD_ERR_STATE, "fld_set_medium has not been called");
+    if (!pg->valid_float && !pg->valid_d) return fail(FLD_ERR_STATE, "the grid holds no state yet");
+    RenderCamera c;
+    double fn = 0.0;
+    for (int k = 0; k < 3; ++k) {
+        c.eye[k] = cam->eye[k];
+        c.f[k] = cam->target[k] - cam->eye[k];
+        fn += c.f[k] * c.f[k];
+    }
+    fn = sqrt(fn);
+    if (!(fn > 0.0)) return fail(FLD_ERR_INVALID_ARG, "eye and target coincide");
+    for (int k = 0; k < 3; ++k) c.f[k] /= fn;
+    c.r[0] = c.f[1] * cam->up[2] - c.f[2] * cam->up[1];
+    c.r[1] = c.f[2] * cam->up[0] - c.f[0] * cam->up[2];
+    c.r[2] = c.f[0] * cam->up[1] - c.f[1] * cam->up[0];
+    const double rn = sqrt(c.r[0] * c.r[0] + c.r[1] * c.r[1] + c.r[2] * c.r[2]);
+    if (!(rn > 1e-12)) return fail(FLD_ERR_INVALID_ARG, "up is parallel to the view direction");
+    for (int k = 0; k < 3; ++k) c.r[k] /= rn;
+    c.u[0] = c.r[1] * c.f[2] - c.r[2] * c.f[1];
+    c.u[1] = c.r[2] * c.f[0] - c.r[0] * c.f[2];
+    c.u[2] = c.r[0] * c.f[1] - c.r[1] * c.f[0];
+    c.tan_half = tan(0.5 * cam->fov_deg * M_PI / 180.0);
+    c.aspect = (double)cam->width / (double)cam->height;
+    c.h = g->h;
+    c.width = cam->width;
+    c.height = cam->height;
+    c.step = cam->step > 0.0 ? cam->step : 0.5 * g->h;
+    if (!isfinite(c.step)) return fail(FLD_ERR_INVALID_ARG, "bad step");
+    c.background = cam->background;
+    c.t_min = cam->t_min < 0.0 ? 1e-6 : cam->t_min;
+    if (!g->f.render_vol) {
+        if (cudaMalloc((void **)&g->f.render_vol, sizeof(float4) * (size_t)nvox(g)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(FLD_ERR_OOM, "cudaMalloc of the sampling volume failed");
+        }
+    }
+    const size_t npx = (size_t)cam->width * (size_t)cam->height;
+    float *rad = radiance;
+    unsigned char *cod = codes;
+    if (where != FLD_MEM_DEVICE) {   // device staging for host outputs
+        if (radiance && cudaMalloc((void **)&rad, sizeof(float) * npx) != cudaSuccess) rad = nullptr;
+        if (codes && cudaMalloc((void **)&cod, npx) != cudaSuccess) cod = nullptr;
+        if ((radiance && !rad) || (codes && !cod)) {
+            (void)cudaGetLastError();
+            if (rad && rad != radiance) cudaFree(rad);
+            if (cod && cod != codes) cudaFree(cod);
+            return fail(FLD_ERR_OOM, "cudaMalloc of the image staging buffers failed");
+        }
+    }
+    PhiSource ps;
+    const bool use_f = pg->valid_float;
+    ps.phi = use_f ? pg->f.phi : nullptr;
+    ps.phlo = use_f && pg->lo_live ? pg->f.phlo : nullptr;
+    ps.phi64 = use_f ? nullptr : pg->f.phi64;
+    ps.coarse = pg != g;
+    ps.C = pg->L;
+    ps.hc = pg->h;
+    cudaError_t e = pg != g ? cudaStreamSynchronize(pg->stream) : cudaSuccess;
+    if (e == cudaSuccess)
+        e = launch_render(g->L, g->f, ps, c, g->f.render_vol, rad, cod, exposure, gamma, g->stream);
+    g->kernels += 2;
+    if (e == cudaSuccess && where != FLD_MEM_DEVICE) {
+        if (radiance) e = cudaMemcpyAsync(radiance, rad, sizeof(float) * npx, cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess && codes) e = cudaMemcpyAsync(codes, cod, npx, cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+    }
+    if (where != FLD_MEM_DEVICE) {
+        if (radiance) cudaFree(rad);
+        if (codes) cudaFree(cod);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "fld_render");
     return FLD_OK;
 }
 

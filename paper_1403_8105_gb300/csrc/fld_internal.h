@@ -19,6 +19,7 @@ struct PassParams {
     double omega;
     double inv2h;
     double floor_;   // eps * jbar (or the no-emission floor)
+    int scheme = 0;  // fld_scheme: red-black SOR or Jacobi
     int bf16 = 0;    // single-precision / hi-lo sweeps read the bfloat16 medium
     double h2 = 0;   // h^2, which scales the bfloat16 sigma_a'
 };
@@ -33,6 +34,11 @@ struct Fields {
     // first solve with medium_bf16) read by the single-precision and hi/lo
     // sweeps; sp and ah2 then hold the same rounded values
     uint16_t *spb = nullptr, *sab = nullptr;
+    // sampling volume of fld_render: sigma_t, sigma_s, source, phi per voxel
+    float4 *render_vol = nullptr;
+    // second phi buffer of the Jacobi variant (allocated on first use)
+    float *phi2 = nullptr;
+    double *phi642 = nullptr;
     // double-precision family (allocated on first FP64 use)
     double *sp64 = nullptr, *ah264 = nullptr, *jh264 = nullptr;
     double *phi64 = nullptr, *D64 = nullptr, *Df64 = nullptr;
@@ -50,6 +56,41 @@ struct Fields {
 cudaError_t launch_prep_f(const Layout &L, const Fields &f, float sigma_eps, float h2, bool bf16, cudaStream_t s);
 cudaError_t launch_prep_d(const Layout &L, const Fields &f, double sigma_eps, double h2, bool bf16,
                           cudaStream_t s);
+
+// One Jacobi iteration: D^k from phi^k at every unknown, then phi^{k+1} from
+// phi^k and D^k; to_second = 1 reads phi and writes the second buffer, 0 the
+// reverse.  The destination's ghosts must already hold the ghost values.
+cudaError_t launch_jacobi(Family fam, const Layout &L, const Fields &f, const PassParams &p, int to_second,
+                          cudaStream_t s);
+
+// Primary ray march (fld_render.cu).  The camera basis is formed on the host
+// (f forward, r right, u up, unit vectors; tan_half = tan(fov/2)).
+struct RenderCamera {
+    double eye[3], f[3], r[3], u[3];
+    double tan_half, aspect, h;
+    int width, height;
+    double step, background, t_min;
+};
+// Where the renderer takes phi from: phi (+ phlo) or phi64 of the rendered
+// grid's own layout, or (coarse) of a coarser grid with layout C and spacing
+// hc, upsampled trilinearly to the rendered grid's voxel centres.
+struct PhiSource {
+    const float *phi = nullptr, *phlo = nullptr;
+    const double *phi64 = nullptr;
+    bool coarse = false;
+    Layout C{};
+    double hc = 0.0;
+};
+// Packs sigma_t, albedo sigma_t, the source and phi into vol (one float4 per
+// voxel), then renders; radiance (width*height floats) and codes (8-bit
+// gamma-compressed) may each be null.
+cudaError_t launch_render(const Layout &L, const Fields &f, const PhiSource &ps, const RenderCamera &c,
+                          float4 *vol, float *radiance, uint8_t *codes, double exposure, double gamma,
+                          cudaStream_t s);
+// Box averages of the fine grid's sigma_t, albedo (sigma_s-weighted) and
+// source over factor^3 blocks into the coarse grid's input arrays.
+cudaError_t launch_downsample(const Layout &L, const Fields &f, int factor, const Layout &C, Fields &fc,
+                              cudaStream_t s);
 
 // phi = phi0 / D = D0 on the unknowns, phi_b / D_b on the ghosts, 0 elsewhere.
 cudaError_t launch_init_f(const Layout &L, float *phi, float *phlo, float *D, double phi0, double D0,

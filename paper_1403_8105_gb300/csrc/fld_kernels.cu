@@ -606,6 +606,37 @@ __global__ void __launch_bounds__(256) k_pass_ff(Layout L, const float *__restri
                               inv2h, floor_, rounds_rt);
 }
 
+// Jacobi variant: phi^{k+1} at every unknown (both colours) from phi^k
+// (src) and D^k (written by the preceding fresh-D pass), into dst.  The update
+// is the residual form of Eq. 32 damped by omega (Eq. 36): phi' = phi_p +
+// omega S / den, S = j h^2 - sigma_a' h^2 phi_p + 1/2 (D_p sum d + sum D_s d),
+// den = sigma_a' h^2 + 3 D_p + 1/2 sum D_s, d = phi_s - phi_p.
+template <typename T>
+__global__ void __launch_bounds__(256) k_jacobi(Layout L, const T *__restrict__ ah2, const T *__restrict__ jh2,
+                                                const T *__restrict__ src, const T *__restrict__ D,
+                                                T *__restrict__ dst, T omega) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= L.nx || j >= L.ny) return;
+    const int q = L.at(i, j, k);
+    const int nb[6] = {L.at(i - 1, j, k), L.at(i + 1, j, k), L.at(i, j - 1, k),
+                       L.at(i, j + 1, k), L.at(i, j, k - 1), L.at(i, j, k + 1)};
+    const T p0 = src[q], Dp = D[q], ah = ah2[q];
+    T A = 0, B = 0, C = 0;
+#pragma unroll
+    for (int s = 0; s < 6; ++s) {
+        const T d = src[nb[s]] - p0;
+        const T Ds = D[nb[s]];
+        A += d;
+        B += Ds * d;
+        C += Ds;
+    }
+    const T S = jh2[q] - ah * p0 + T(0.5) * (Dp * A + B);
+    const T den = ah + T(3) * Dp + T(0.5) * C;
+    dst[q] = p0 + omega * (S / den);
+}
+
 // Descriptor of a batched grid, read by every thread with uniform 16-byte
 // loads (one transaction per warp, no shared-memory staging or barrier).
 __device__ __forceinline__ BatchDesc load_desc(const BatchDesc *__restrict__ p) {
@@ -1159,6 +1190,24 @@ int reduction_blocks(const Layout &L) {
     const dim3 g = vox_grid(L);
     const long long n = (long long)g.x * g.y * g.z;
     return (int)(n > 4096 ? n : 4096);
+}
+
+cudaError_t launch_jacobi(Family fam, const Layout &L, const Fields &f, const PassParams &p, int to_second,
+                          cudaStream_t s) {
+    const dim3 grd = vox_grid(L), blk = vox_block();
+    if (fam == FAM_F64) {
+        const double *src = to_second ? f.phi64 : f.phi642;
+        double *dst = to_second ? f.phi642 : f.phi64;
+        k_fresh_D_d<<<grd, blk, 0, s>>>(L, f.sp64, src, f.D64, p.lim, p.larsen_n, p.inv2h, p.floor_);
+        k_jacobi<double><<<grd, blk, 0, s>>>(L, f.ah264, f.jh264, src, f.D64, dst, p.omega);
+    } else {
+        const float *src = to_second ? f.phi : f.phi2;
+        float *dst = to_second ? f.phi2 : f.phi;
+        k_fresh_D_f<<<grd, blk, 0, s>>>(L, f.sp, src, nullptr, f.D, p.lim, (float)p.larsen_n, (float)p.inv2h,
+                                        (float)p.floor_);
+        k_jacobi<float><<<grd, blk, 0, s>>>(L, f.ah2, f.jh2, src, f.D, dst, (float)p.omega);
+    }
+    return cudaGetLastError();
 }
 
 cudaError_t launch_residual(Family fam, const Layout &L, const Fields &f, const PassParams &p, int margin,

@@ -75,3 +75,28 @@ def test_one_iteration_parity_at_full_size(c2):
     phi, D = g.get_state()
     assert np.abs(phi - ref.phi).max() <= 1e-6 * np.abs(ref.phi).max()
     assert np.abs(D - ref.D).max() <= 3e-5 * np.abs(ref.D).max()
+
+
+def test_render_at_full_size_matches_oracle_pixels(c2):
+    # the bench's 1024^2 view of the solved 128^3 cloud, sampled pixels
+    # rendered one by one by the oracle from the same fields
+    case, g, j = c2
+    p = fld.params(limiter="lp", precision="mixed", tol=1e-6, check_every=256, max_iters=600000)
+    r = g.solve(p)
+    assert r.status == fld.FLD_OK, r.as_dict()
+    cam = dict(eye=(0.5, 1.1, -1.3), target=(0.5, 0.45, 0.5), up=(0.0, 1.0, 0.0), fov_deg=40.0, width=1024,
+               height=1024, background=0.05)
+    rad, codes = g.render(fld.camera(**cam), exposure=2.0, codes=True)
+    phi, _ = g.get_state()
+    rng = np.random.default_rng(3)
+    pix = [(int(x), int(y)) for x, y in rng.integers(0, 1024, size=(300, 2))]
+    pix += [(512, 512), (0, 0), (1023, 1023), (300, 700)]
+    want = oracle.render(case.sigma_t, case.alb, j.astype(np.float64), phi, case.h, pixels=pix, t_min=1e-6, **cam)
+    got = np.array([rad[y, x] for x, y in pix], dtype=np.float64)
+    scale = float(np.abs(want).max())
+    assert np.abs(got - want).max() <= 1e-4 * scale
+    assert (rad > 1.05 * cam["background"]).mean() > 0.05     # the lit cloud covers part of the view
+    # tone map: the GPU's 8-bit codes are the gamma compression of its own radiance
+    mine = oracle.tonemap(rad.astype(np.float64), exposure=2.0)
+    assert np.abs(mine.astype(int) - codes.astype(int)).max() <= 1
+    assert (mine != codes).mean() < 1e-3
