@@ -148,6 +148,15 @@ typedef struct {
     int scheme;           /* fld_scheme (default RED_BLACK).  JACOBI: precision
                              FP32 or FP64, 0 < omega <= 1 (<= 0 selects 1), no
                              warm-up; local_iters does not apply               */
+    int nested;           /* cold fld_solve only: start from the solution of
+                             `nested` successively 2x coarser problems (medium
+                             and source box-averaged as in fld_downsample; the
+                             coarsest solved cold to 1e-4, each finer one from
+                             its coarser neighbour's phi, blended trilinearly,
+                             with D recomputed).  The fixed point is the same;
+                             the start removes the smooth error SOR is slowest
+                             on.  Coarse edges stay >= 8.  0 (default): the
+                             paper's initial state.  Not in the paper.        */
 } fld_solve_params;
 
 typedef struct {
@@ -168,6 +177,9 @@ typedef struct {
     int iterations_mid;    /* MIXED: sweeps with phi as a hi/lo pair and
                               FP32-summed updates (between the two above)       */
     double ms_sweep_mid;   /* device time inside those sweeps                     */
+    int iterations_coarse; /* nested: iterations on the coarser grids (summed)    */
+    double ms_coarse;      /* nested: their device time (included in ms)          */
+    long long updates_coarse; /* nested: their voxel updates                      */
 } fld_solve_result;
 
 /* Fill *p with the defaults: LP limiter, Larsen n = 2, omega auto,

@@ -49,7 +49,7 @@ class SolveParams(ctypes.Structure):
         ("precision", ctypes.c_int), ("fp32_switch", ctypes.c_double), ("residual_margin", ctypes.c_int),
         ("warm_start", ctypes.c_int), ("phi0", ctypes.c_double), ("D0", ctypes.c_double),
         ("phi_b", ctypes.c_double), ("D_b", ctypes.c_double), ("warmup_iters", ctypes.c_int),
-        ("medium_bf16", ctypes.c_int), ("scheme", ctypes.c_int),
+        ("medium_bf16", ctypes.c_int), ("scheme", ctypes.c_int), ("nested", ctypes.c_int),
     ]
 
 
@@ -61,6 +61,7 @@ class SolveResult(ctypes.Structure):
         ("jbar", ctypes.c_double), ("omega", ctypes.c_double), ("ms", ctypes.c_double),
         ("ms_sweep_fp32", ctypes.c_double), ("ms_sweep_corr", ctypes.c_double), ("kernels", ctypes.c_longlong),
         ("omega_backoffs", ctypes.c_int), ("iterations_mid", ctypes.c_int), ("ms_sweep_mid", ctypes.c_double),
+        ("iterations_coarse", ctypes.c_int), ("ms_coarse", ctypes.c_double), ("updates_coarse", ctypes.c_longlong),
     ]
 
     def as_dict(self):

@@ -53,6 +53,7 @@ constexpr double kFlatBelow = 0.1;            // ... below this fraction of the 
 constexpr int kMaxBackoffs = 8;               // omega reductions before reporting divergence
 constexpr double kOmegaMax = 1.98;            // upper clamp of the automatic omega
 constexpr int kWarmupPerEdge = 4;             // automatic warm-up: iterations per voxel of the largest extent
+constexpr double kNestedTol = 1e-4;           // nested solves: tolerance of the coarser levels
 
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
@@ -90,6 +91,7 @@ struct fld_grid_s {
     GraphEntry graphs[4];
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, evb0 = nullptr, evb1 = nullptr;
     long long kernels = 0;                       // kernel launches issued so far
+    fld_grid_s *coarse = nullptr;                // nested solves: the next 2x coarser grid (owned)
     // last good state of a solve (float family: phi, lo, D; FP64: phi, D)
     float *snap_phi = nullptr, *snap_lo = nullptr, *snap_D = nullptr;
     double *snap_phi64 = nullptr, *snap_D64 = nullptr;
@@ -541,12 +543,12 @@ struct Controller {
             ++since_best;
         }
         const bool no_progress = since_best >= kSwitchChecks;
-        // No new minimum for a while although the residual never fell an
-        // order of magnitude below where the over-relaxed iteration started:
-        // that is omega cycling the nonlinear iteration (seen with omega
-        // 1.97 at 128^3), not a precision floor -- return to the best state
-        // with a smaller omega.
-        if (no_progress && omega > 1.0 && rel >= kFlatBelow * initial && backoffs < kMaxBackoffs) {
+        // No new minimum for a while and the residual above where the
+        // over-relaxed iteration started: that is omega cycling the nonlinear
+        // iteration (seen with omega 1.97 at 128^3: 4-6 against a start of
+        // 0.43), not a precision floor (which a warm start may begin near) --
+        // return to the best state with a smaller omega.
+        if (no_progress && omega > 1.0 && rel >= initial && backoffs < kMaxBackoffs) {
             ++backoffs;
             since_best = 0;
             nrecent = 0;
@@ -689,6 +691,11 @@ fld_status fld_create_grid(int nx, int ny, int nz, double h, void *stream, fld_g
 }
 
 void fld_destroy(fld_grid g) {
+    if (!g) return;
+    if (g->coarse) {
+        fld_destroy(g->coarse);
+        g->coarse = nullptr;
+    }
     if (!g) return;
     cudaSetDevice(g->device);
     if (g->stream) cudaStreamSynchronize(g->stream);
@@ -1007,12 +1014,125 @@ fld_status fld_residual(fld_grid g, const fld_solve_params *p, double *rel) {
     return residual_now(g, use, pass_params(g, p), p->residual_margin, rel);
 }
 
+namespace {
+fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r);
+fld_status solve_nested(fld_grid g, const fld_solve_params *p, fld_solve_result *r);
+}  // namespace
+
 fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r) {
     fld_status st = enter(g);
     if (st != FLD_OK) return st;
     if ((st = check_params(g, p)) != FLD_OK) return st;
     if (!(p->tol >= 0.0)) return fail(FLD_ERR_INVALID_ARG, "tol must be >= 0");
     if (p->max_iters < 0 || p->check_every < 1) return fail(FLD_ERR_INVALID_ARG, "bad max_iters / check_every");
+    if (p->nested > 0 && !p->warm_start && p->scheme == FLD_SCHEME_RED_BLACK) return solve_nested(g, p, r);
+    return solve_core(g, p, r);
+}
+
+namespace {
+
+// Start from the solutions of successively coarser problems (fld_solve_params
+// .nested): box-averaged medium and source on grids of 2x, 4x, ... the
+// spacing, the coarsest solved cold to kNestedTol, each finer one from the
+// next coarser phi (blended trilinearly, D recomputed) to kNestedTol, and g
+// from its coarser neighbour to the caller's tolerance.
+fld_status solve_nested(fld_grid g, const fld_solve_params *p, fld_solve_result *r) {
+    int levels = p->nested;
+    while (levels > 0) {   // coarse edges stay >= 8
+        const int f = 1 << levels;
+        if ((g->nx + f - 1) / f >= 8 && (g->ny + f - 1) / f >= 8 && (g->nz + f - 1) / f >= 8) break;
+        --levels;
+    }
+    if (levels == 0) return solve_core(g, p, r);
+    // the chain g -> coarse -> ... (kept with the grid, rebuilt if the shape changed)
+    std::vector<fld_grid_s *> chain{g};
+    for (int l = 1; l <= levels; ++l) {
+        fld_grid_s *up = chain.back();
+        const int cx = (up->nx + 1) / 2, cy = (up->ny + 1) / 2, cz = (up->nz + 1) / 2;
+        if (up->coarse && (up->coarse->nx != cx || up->coarse->ny != cy || up->coarse->nz != cz ||
+                           up->coarse->h != 2.0 * up->h)) {
+            fld_destroy(up->coarse);
+            up->coarse = nullptr;
+        }
+        if (!up->coarse) {
+            fld_grid c = nullptr;
+            fld_status st = fld_create_grid(cx, cy, cz, 2.0 * up->h, (void *)up->stream, &c);
+            if (st != FLD_OK) return st;
+            up->coarse = c;
+        }
+        chain.push_back(up->coarse);
+    }
+    fld_status st = FLD_OK;
+    for (int l = 1; l <= levels; ++l)
+        if ((st = fld_downsample(chain[l - 1], chain[l], 2)) != FLD_OK) return st;
+    fld_solve_params q = *p;
+    q.nested = 0;
+    q.tol = p->tol > kNestedTol ? p->tol : kNestedTol;
+    q.check_every = p->check_every < 64 ? p->check_every : 64;
+    fld_solve_result acc;
+    memset(&acc, 0, sizeof(acc));
+    for (int l = levels; l >= 0; --l) {
+        fld_grid_s *c = chain[l];
+        if (l < levels) {
+            // prolong the coarser solution into c's state
+            fld_grid_s *from = chain[l + 1];
+            const Family fam = FAM_F32;
+            if ((st = prepare(c, p, fam)) != FLD_OK) return st;
+            if ((st = init_state(c, p, fam)) != FLD_OK) return st;   // ghosts, defaults
+            if ((st = sync_family(c, fam)) != FLD_OK) return st;
+            if ((st = sync_family(from, from->valid_float ? (from->lo_live ? FAM_FF : FAM_F32) : FAM_F64)) != FLD_OK)
+                return st;
+            PhiSource ps;
+            ps.phi = from->valid_float ? from->f.phi : nullptr;
+            ps.phlo = from->valid_float && from->lo_live ? from->f.phlo : nullptr;
+            ps.phi64 = from->valid_float ? nullptr : from->f.phi64;
+            ps.coarse = true;
+            ps.C = from->L;
+            ps.hc = from->h;
+            FLD_CK(cudaStreamSynchronize(from->stream));
+            FLD_CK(launch_prolong(c->L, c->f, ps, c->h, c->stream));
+            FLD_CK(launch_fresh_D_into(c->L, c->f, pass_params(c, p), c->stream));
+            c->kernels += 2;
+            c->lo_live = false;
+            c->valid_float = true;
+            c->valid_d = false;
+            q.warm_start = 1;
+        } else {
+            q.warm_start = 0;
+        }
+        if (l == 0) {
+            q.tol = p->tol;
+            q.check_every = p->check_every;
+        }
+        fld_solve_result rl;
+        memset(&rl, 0, sizeof(rl));
+        st = solve_core(c, &q, &rl);
+        if (st != FLD_OK && st != FLD_ERR_NOT_CONVERGED) return st;
+        if (l > 0) {
+            acc.iterations_coarse += rl.iterations;
+            acc.ms_coarse += rl.ms;
+            acc.updates_coarse += (long long)rl.iterations * c->nx * c->ny * c->nz;
+            acc.kernels += rl.kernels;
+        } else {
+            const int ic = acc.iterations_coarse;
+            const double mc = acc.ms_coarse;
+            const long long uc = acc.updates_coarse;
+            const long long kc = acc.kernels;
+            acc = rl;
+            acc.iterations_coarse = ic;
+            acc.ms_coarse = mc;
+            acc.updates_coarse = uc;
+            acc.ms += mc;
+            acc.kernels += kc;
+        }
+        if (l == 0 && r) *r = acc;
+        if (l == 0) return st;
+    }
+    return st;
+}
+
+fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r) {
+    fld_status st = FLD_OK;
     fld_solve_result res;
     memset(&res, 0, sizeof(res));
     const long long kernels0 = g->kernels;
@@ -1116,6 +1236,8 @@ fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r)
         g_last_error = stalled ? "residual stalled above tol (floor of the arithmetic)" : "max_iters reached before tol";
     return outcome;
 }
+
+}  // namespace
 
 
 // ===========================================================================

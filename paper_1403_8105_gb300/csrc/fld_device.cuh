@@ -104,21 +104,21 @@ __device__ __forceinline__ double lp_series_d(double R) {
 __device__ __forceinline__ float limiter_f(int kind, float larsen_n, float R) {
     switch (kind) {
     case LIM_CDA: return 1.0f / 3.0f;
-    case LIM_SUM: return 1.0f / (3.0f + R);
+    case LIM_SUM: return 1.0f / __fadd_rn(3.0f, R);
     case LIM_MAX: return 1.0f / fmaxf(3.0f, R);
-    case LIM_KERSHAW: return 2.0f / (3.0f + hypotf(3.0f, 2.0f * R));
+    case LIM_KERSHAW: return 2.0f / __fadd_rn(3.0f, hypotf(3.0f, 2.0f * R));
     case LIM_LARSEN: {
         // (3^n + R^n)^(-1/n) = 1 / (m (1 + (s/m)^n)^(1/n)), m = max, s = min
         const float m = fmaxf(3.0f, R), s = fminf(3.0f, R);
-        return 1.0f / (m * powf(1.0f + powf(s / m, larsen_n), 1.0f / larsen_n));
+        return 1.0f / (m * powf(__fadd_rn(1.0f, powf(s / m, larsen_n)), 1.0f / larsen_n));
     }
     default: {  // LIM_LP
         if (R < 1.0f) return lp_series_f(R);
         // F = r ((1 - r) + 2/(e^{2R} - 1)), r = 1/R; the last term is below
         // 3.4e-8 of the first once R > 9 and is dropped there
         const float r = 1.0f / R;
-        const float tail = R < 9.0f ? 2.0f / (expf(2.0f * R) - 1.0f) : 0.0f;
-        return r * ((1.0f - r) + tail);
+        const float tail = R < 9.0f ? 2.0f / __fsub_rn(expf(2.0f * R), 1.0f) : 0.0f;
+        return r * __fadd_rn(__fsub_rn(1.0f, r), tail);
     }
     }
 }
@@ -216,13 +216,15 @@ __device__ __forceinline__ float D_of_f(float gmax, float sp, float phi_p, float
         // one correctly rounded quotient per branch: R = gmax/den below 1
         // (Laurent series), 1/R = den/gmax above (the exponential term,
         // which needs R itself, only for 1 <= R < 9)
+        // (explicit round-to-nearest adds: no contraction into an FMA, so
+        // every kernel calling this evaluates it to the same bits)
         float F;
         if (gmax < den) {
             F = lp_series_f(gmax / den);
         } else {
             const float r = den / gmax;
-            const float tail = r > (1.0f / 9.0f) ? 2.0f / (expf(2.0f * (gmax / den)) - 1.0f) : 0.0f;
-            F = r * ((1.0f - r) + tail);
+            const float tail = r > (1.0f / 9.0f) ? 2.0f / __fsub_rn(expf(2.0f * (gmax / den)), 1.0f) : 0.0f;
+            F = r * __fadd_rn(__fsub_rn(1.0f, r), tail);
         }
         return F / sp;
     }

@@ -87,6 +87,12 @@ struct PhiSource {
 cudaError_t launch_render(const Layout &L, const Fields &f, const PhiSource &ps, const RenderCamera &c,
                           float4 *vol, float *radiance, uint8_t *codes, double exposure, double gamma,
                           cudaStream_t s);
+// phi (hi word; low word 0) at the unknowns of L from a coarser grid's phi,
+// blended trilinearly between its voxel centres (ps.coarse must be true).
+cudaError_t launch_prolong(const Layout &L, Fields &f, const PhiSource &ps, double h, cudaStream_t s);
+// D from the current single-precision phi at every unknown (Eq. 33-35), into f.D.
+cudaError_t launch_fresh_D_into(const Layout &L, Fields &f, const PassParams &p, cudaStream_t s);
+
 // Box averages of the fine grid's sigma_t, albedo (sigma_s-weighted) and
 // source over factor^3 blocks into the coarse grid's input arrays.
 cudaError_t launch_downsample(const Layout &L, const Fields &f, int factor, const Layout &C, Fields &fc,

@@ -255,22 +255,27 @@ __device__ __forceinline__ bool pass_cell(const Layout &L, int c, int t, int J, 
 // Limiter (Table 2) with approximate reciprocals, for the bulk
 // single-precision sweeps, whose accuracy is bounded by phi stored in float;
 // the correction sweeps and the residual use the correctly rounded forms.
+// The sums below are written with explicit round-to-nearest adds: an
+// operand here can be a product (the approximate quotients are x * rcp(y)),
+// and a plain `+` could then be contracted into an FMA in one kernel and not
+// in another, so kernels sharing this code would differ in the last bit.
 __device__ __forceinline__ float limiter_fast(int kind, float larsen_n, float R) {
     switch (kind) {
     case LIM_CDA: return 1.0f / 3.0f;
-    case LIM_SUM: return __fdividef(1.0f, 3.0f + R);
+    case LIM_SUM: return __fdividef(1.0f, __fadd_rn(3.0f, R));
     case LIM_MAX: return __fdividef(1.0f, fmaxf(3.0f, R));
-    case LIM_KERSHAW: return __fdividef(2.0f, 3.0f + hypotf(3.0f, 2.0f * R));
+    case LIM_KERSHAW: return __fdividef(2.0f, __fadd_rn(3.0f, hypotf(3.0f, 2.0f * R)));
     case LIM_LARSEN: {
         const float m = fmaxf(3.0f, R), s = fminf(3.0f, R);
-        return __fdividef(1.0f, m * __powf(1.0f + __powf(__fdividef(s, m), larsen_n), __fdividef(1.0f, larsen_n)));
+        return __fdividef(1.0f, m * __powf(__fadd_rn(1.0f, __powf(__fdividef(s, m), larsen_n)),
+                                           __fdividef(1.0f, larsen_n)));
     }
     default: {
         if (R < 1.0f) return lp_series_f(R);
         const float r = __fdividef(1.0f, R);
         // 2e/(1-e), e = exp(-2R), is below 3.4e-8 of (1 - 1/R) once R > 9
-        const float tail = R < 9.0f ? __fdividef(2.0f, __expf(2.0f * R) - 1.0f) : 0.0f;
-        return r * ((1.0f - r) + tail);
+        const float tail = R < 9.0f ? __fdividef(2.0f, __fsub_rn(__expf(2.0f * R), 1.0f)) : 0.0f;
+        return r * __fadd_rn(__fsub_rn(1.0f, r), tail);
     }
     }
 }
@@ -350,7 +355,7 @@ __device__ __forceinline__ void cell_f32(float p0, const float ps[6], const floa
 #pragma unroll
     for (int r = 0; r < (ROUNDS > 0 ? ROUNDS : 64); ++r) {
         if (ROUNDS == 0 && r >= local_iters) break;
-        const float R = __fdividef(gmax, fmaxf(s_ * (p0 + delta), floor_));     // Eq. 35
+        const float R = __fdividef(gmax, fmaxf(s_ * __fadd_rn(p0, delta), floor_));     // Eq. 35
         Dp = limiter_fast(lim, larsen_n, R) * inv_sp;                          // Eq. 33
         delta = __fdividef(fmaf(0.5f * Dp, A, base), fmaf(3.0f, Dp, den0));   // Eq. 32
     }
@@ -388,8 +393,9 @@ __device__ __forceinline__ float2 ld2(const float *__restrict__ p, int off) {
     return *reinterpret_cast<const float2 *>(p + off);
 }
 
+
 // Gather the six neighbours of the two cells of a pair from one field.
-__device__ __forceinline__ void gather_pair(const float *__restrict__ f, const Pair &q, float v0[6], float v1[6]) {
+__device__ __forceinline__ void gather_pair(const float *f, const Pair &q, float v0[6], float v1[6]) {
     const float2 xv = ld2(f, q.xv);
     const float xe = q.left ? f[q.xv - 1] : f[q.xv + 2];
     if (q.left) {
@@ -431,19 +437,15 @@ __device__ __forceinline__ void medium_pair(const float *__restrict__ sp, const 
     }
 }
 
-// Single-precision pass (the bulk sweeps), two unknowns per thread (40
-// registers: six CTAs per SM).
+// Single-precision pass (the bulk sweeps), two unknowns per thread: the pair
+// (t, t+1) of row (J, K); waits for the preceding grid (pdl_wait) before
+// reading phi / D.
 template <int LIM, int ROUNDS, bool BF>
-__global__ void __launch_bounds__(256, 6) k_pass2_f32(Layout L, const float *__restrict__ sp,
-                                                   const float *__restrict__ ah2, const float *__restrict__ jh2,
-                                                   const uint16_t *__restrict__ spb,
-                                                   const uint16_t *__restrict__ sab, float h2,
-                                                   float *__restrict__ phi, float *__restrict__ D, int colour,
-                                                   int lim_rt, float larsen_n, float omega, float inv2h,
-                                                   float floor_, int rounds_rt) {
-    pdl_launch_dependents();
-    const int t = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int J = blockIdx.y * blockDim.y + threadIdx.y + 1, K = blockIdx.z + 1;
+__device__ __forceinline__ void tile_f32(const Layout &L, const float *__restrict__ sp,
+                                         const float *__restrict__ ah2, const float *__restrict__ jh2,
+                                         const uint16_t *__restrict__ spb, const uint16_t *__restrict__ sab, float h2,
+                                         float *phi, float *D, int colour, int lim_rt, float larsen_n, float omega,
+                                         float inv2h, float floor_, int rounds_rt, int t, int J, int K) {
     if (J > L.ny) return;
     Pair q;
     pair_cells(L, colour, t, J, K, q);
@@ -470,11 +472,27 @@ __global__ void __launch_bounds__(256, 6) k_pass2_f32(Layout L, const float *__r
     }
 }
 
+// The launched FP32 pass (40 registers: six CTAs per SM).
+template <int LIM, int ROUNDS, bool BF>
+__global__ void __launch_bounds__(256, 6) k_pass2_f32(Layout L, const float *__restrict__ sp,
+                                                   const float *__restrict__ ah2, const float *__restrict__ jh2,
+                                                   const uint16_t *__restrict__ spb,
+                                                   const uint16_t *__restrict__ sab, float h2,
+                                                   float *__restrict__ phi, float *__restrict__ D, int colour,
+                                                   int lim_rt, float larsen_n, float omega, float inv2h,
+                                                   float floor_, int rounds_rt) {
+    pdl_launch_dependents();
+    tile_f32<LIM, ROUNDS, BF>(L, sp, ah2, jh2, spb, sab, h2, phi, D, colour, lim_rt, larsen_n, omega,
+                                           inv2h, floor_, rounds_rt, 2 * (blockIdx.x * blockDim.x + threadIdx.x),
+                                           blockIdx.y * blockDim.y + threadIdx.y + 1, blockIdx.z + 1);
+}
+
 // Middle pass: phi kept as a hi/lo pair (no storage floor) but the update
 // summed in plain FP32 with the approximate D of the bulk sweeps -- about the
 // cost of the FP32 pass, reaching residuals a few times above the
-// float-float pass's.  cell_fh is the arithmetic of one point; k_pass2_fh
-// updates two unknowns per thread (48 registers for five CTAs per SM).
+// float-float pass's.  cell_fh is the arithmetic of one point, tile_fh that
+// of a pair of unknowns; k_pass2_fh launches it (48 registers for five CTAs
+// per SM).
 template <int LIM, int ROUNDS>
 __device__ __forceinline__ void cell_fh(float p0, float p0lo, const float ps[6], const float ls[6],
                                         const float Ds[6], float s_, float ah, float jj, int lim_rt, float larsen_n,
@@ -503,7 +521,7 @@ __device__ __forceinline__ void cell_fh(float p0, float p0lo, const float ps[6],
 #pragma unroll
     for (int r = 0; r < (ROUNDS > 0 ? ROUNDS : 64); ++r) {
         if (ROUNDS == 0 && r >= local_iters) break;
-        const float R = __fdividef(gmax, fmaxf(s_ * (p0 + delta), floor_));
+        const float R = __fdividef(gmax, fmaxf(s_ * __fadd_rn(p0, delta), floor_));
         Dp = limiter_fast(lim, larsen_n, R) * inv_sp;
         delta = __fdividef(fmaf(0.5f * Dp, A, base), fmaf(3.0f, Dp, den0));
     }
@@ -514,16 +532,11 @@ __device__ __forceinline__ void cell_fh(float p0, float p0lo, const float ps[6],
 }
 
 template <int LIM, int ROUNDS, bool BF>
-__global__ void __launch_bounds__(256, 5) k_pass2_fh(Layout L, const float *__restrict__ sp,
-                                                  const float *__restrict__ ah2, const float *__restrict__ jh2,
-                                                  const uint16_t *__restrict__ spb,
-                                                  const uint16_t *__restrict__ sab, float h2,
-                                                  float *__restrict__ phi, float *__restrict__ phlo,
-                                                  float *__restrict__ D, int colour, int lim_rt, float larsen_n,
-                                                  float omega, float inv2h, float floor_, int rounds_rt) {
-    pdl_launch_dependents();
-    const int t = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int J = blockIdx.y * blockDim.y + threadIdx.y + 1, K = blockIdx.z + 1;
+__device__ __forceinline__ void tile_fh(const Layout &L, const float *__restrict__ sp,
+                                        const float *__restrict__ ah2, const float *__restrict__ jh2,
+                                        const uint16_t *__restrict__ spb, const uint16_t *__restrict__ sab, float h2,
+                                        float *phi, float *phlo, float *D, int colour, int lim_rt, float larsen_n,
+                                        float omega, float inv2h, float floor_, int rounds_rt, int t, int J, int K) {
     if (J > L.ny) return;
     Pair q;
     pair_cells(L, colour, t, J, K, q);
@@ -551,6 +564,21 @@ __global__ void __launch_bounds__(256, 5) k_pass2_fh(Layout L, const float *__re
         phlo[q.own] = lo0;
         D[q.own] = d0;
     }
+}
+
+template <int LIM, int ROUNDS, bool BF>
+__global__ void __launch_bounds__(256, 5) k_pass2_fh(Layout L, const float *__restrict__ sp,
+                                                  const float *__restrict__ ah2, const float *__restrict__ jh2,
+                                                  const uint16_t *__restrict__ spb,
+                                                  const uint16_t *__restrict__ sab, float h2,
+                                                  float *__restrict__ phi, float *__restrict__ phlo,
+                                                  float *__restrict__ D, int colour, int lim_rt, float larsen_n,
+                                                  float omega, float inv2h, float floor_, int rounds_rt) {
+    pdl_launch_dependents();
+    tile_fh<LIM, ROUNDS, BF>(L, sp, ah2, jh2, spb, sab, h2, phi, phlo, D, colour, lim_rt, larsen_n,
+                                          omega, inv2h, floor_, rounds_rt,
+                                          2 * (blockIdx.x * blockDim.x + threadIdx.x),
+                                          blockIdx.y * blockDim.y + threadIdx.y + 1, blockIdx.z + 1);
 }
 
 // Float-float correction pass: phi kept as a hi/lo pair, S summed so the
@@ -1190,6 +1218,12 @@ int reduction_blocks(const Layout &L) {
     const dim3 g = vox_grid(L);
     const long long n = (long long)g.x * g.y * g.z;
     return (int)(n > 4096 ? n : 4096);
+}
+
+cudaError_t launch_fresh_D_into(const Layout &L, Fields &f, const PassParams &p, cudaStream_t s) {
+    k_fresh_D_f<<<vox_grid(L), vox_block(), 0, s>>>(L, f.sp, f.phi, nullptr, f.D, p.lim, (float)p.larsen_n,
+                                                    (float)p.inv2h, (float)p.floor_);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_jacobi(Family fam, const Layout &L, const Fields &f, const PassParams &p, int to_second,

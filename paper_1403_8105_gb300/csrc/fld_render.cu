@@ -79,6 +79,18 @@ __global__ void k_render_pack(Layout L, const float *__restrict__ st, const floa
     out[v] = make_float4(s, __fmul_rn(alb[v], s), q[v], ph);
 }
 
+__global__ void k_prolong(Layout L, float *__restrict__ phi, float *__restrict__ phlo, const float *__restrict__ cphi,
+                          const float *__restrict__ cphlo, const double *__restrict__ cphi64, Layout C, float h,
+                          float hc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= L.nx || j >= L.ny) return;
+    const int q = L.at(i, j, k);
+    phi[q] = phi_trilinear(C, cphi, cphlo, cphi64, hc, (i + 0.5f) * h, (j + 0.5f) * h, (k + 0.5f) * h);
+    phlo[q] = 0.0f;
+}
+
 // Box averages over f^3 blocks (the voxels that exist): sigma_t, albedo =
 // mean(albedo sigma_t) / mean(sigma_t) (0 in vacuum) and the source of the
 // coarse grid, accumulated in double.
@@ -214,6 +226,12 @@ cudaError_t launch_downsample(const Layout &L, const Fields &f, int factor, cons
     const dim3 b(32, 8, 1), g((C.nx + 31) / 32, (C.ny + 7) / 8, C.nz);
     k_downsample<<<g, b, 0, s>>>(L.nx, L.ny, L.nz, factor, C.nx, C.ny, C.nz, f.sigma_t, f.albedo, f.jsrc,
                                  fc.sigma_t, fc.albedo, fc.jsrc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prolong(const Layout &L, Fields &f, const PhiSource &ps, double h, cudaStream_t s) {
+    const dim3 b(32, 8, 1), g((L.nx + 31) / 32, (L.ny + 7) / 8, L.nz);
+    k_prolong<<<g, b, 0, s>>>(L, f.phi, f.phlo, ps.phi, ps.phlo, ps.phi64, ps.C, (float)h, (float)ps.hc);
     return cudaGetLastError();
 }
 

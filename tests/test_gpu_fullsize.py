@@ -95,7 +95,8 @@ def test_render_at_full_size_matches_oracle_pixels(c2):
     got = np.array([rad[y, x] for x, y in pix], dtype=np.float64)
     scale = float(np.abs(want).max())
     assert np.abs(got - want).max() <= 1e-4 * scale
-    assert (rad > 1.05 * cam["background"]).mean() > 0.05     # the lit cloud covers part of the view
+    # the cloud covers part of the view (seen from below it is darker than the background)
+    assert (np.abs(rad - cam["background"]) > 0.01 * cam["background"]).mean() > 0.05
     # tone map: the GPU's 8-bit codes are the gamma compression of its own radiance
     mine = oracle.tonemap(rad.astype(np.float64), exposure=2.0)
     assert np.abs(mine.astype(int) - codes.astype(int)).max() <= 1
