@@ -629,8 +629,12 @@ fld_status fld_create_grid(int nx, int ny, int nz, double h, void *stream, fld_g
     *out = nullptr;
     if (nx < 1 || ny < 1 || nz < 1) return fail(FLD_ERR_INVALID_ARG, "grid extents must be >= 1");
     if (!(h > 0.0) || !isfinite(h)) return fail(FLD_ERR_INVALID_ARG, "h must be a positive finite number");
-    if ((long long)(nx + 2) * (ny + 2) * (nz + 2) > (1LL << 40))
+    if (nx > (1 << 30) || ny > (1 << 30) || nz > (1 << 30) ||
+        ((long long)nx + 2) * ((long long)ny + 2) * ((long long)nz + 2) > (1LL << 40))
         return fail(FLD_ERR_INVALID_ARG, "grid too large");
+    Layout probe;
+    if (!make_layout(nx, ny, nz, &probe))
+        return fail(FLD_ERR_INVALID_ARG, "grid too large: a padded field must stay below 2e9 elements");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
         (void)cudaGetLastError();

@@ -74,6 +74,12 @@ def test_create_grid_argument_checks_need_no_gpu():
     with pytest.raises(fld.FldError) as e:
         fld.fld_create_grid(4, 4, 4, -1.0)
     assert e.value.status == fld.FLD_ERR_INVALID_ARG
+    # beyond the 32-bit offsets of the layout (2e9 padded elements per field):
+    # rejected before anything is allocated
+    for shape in ((1300, 1300, 1300), (2 ** 31 - 1, 1, 1), (1, 2 ** 31 - 1, 1), (4000, 4000, 200)):
+        with pytest.raises(fld.FldError) as e:
+            fld.fld_create_grid(*shape, 0.001)
+        assert e.value.status == fld.FLD_ERR_INVALID_ARG, shape
 
 
 def test_no_cpu_fallback_without_device():

@@ -17,7 +17,7 @@ if not torch.cuda.is_available():  # pragma: no cover
 INNER = (slice(1, -1),) * 3
 
 
-@pytest.mark.parametrize("shape,levels", [((48, 48, 48), 1), ((48, 48, 48), 2), ((29, 17, 23), 1), ((20, 20, 20), 3)])
+@pytest.mark.parametrize("shape,levels", [((32, 32, 32), 1), ((32, 32, 32), 2), ((29, 17, 23), 1), ((20, 20, 20), 3)])
 def test_nested_solve_reaches_the_oracle_fixed_point(shape, levels):
     nz, ny, nx = shape
     sig, alb = fld_inputs.cloud_medium(nx, seed=5, albedo=0.95, ny=ny, nz=nz)
@@ -30,7 +30,7 @@ def test_nested_solve_reaches_the_oracle_fixed_point(shape, levels):
     with fld.Grid(nx, ny, nz, h) as g:
         g.set_medium(sig, alb)
         g.set_source(q)
-        # (1e-6: mixed precision floors near 2e-7 at 48^3 -- single-precision D)
+        # (1e-6: mixed precision floors near 2e-7 at 32^3 -- single-precision D)
         p = fld.params(tol=1e-6, check_every=32, max_iters=400000, nested=levels)
         r = g.solve(p)
         assert r.status == fld.FLD_OK, r.as_dict()
