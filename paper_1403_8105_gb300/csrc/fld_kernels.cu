@@ -472,9 +472,11 @@ __device__ __forceinline__ void tile_f32(const Layout &L, const float *__restric
     }
 }
 
-// The launched FP32 pass (40 registers: six CTAs per SM).
+// The launched FP32 pass.  Registers are left to hold all of a thread's
+// loads in flight (48, five CTAs per SM): measured faster than capping them
+// for occupancy (six CTAs at 40 registers: 8.0 against 7.8 us per 128^3 pass).
 template <int LIM, int ROUNDS, bool BF>
-__global__ void __launch_bounds__(256, 6) k_pass2_f32(Layout L, const float *__restrict__ sp,
+__global__ void __launch_bounds__(256, 4) k_pass2_f32(Layout L, const float *__restrict__ sp,
                                                    const float *__restrict__ ah2, const float *__restrict__ jh2,
                                                    const uint16_t *__restrict__ spb,
                                                    const uint16_t *__restrict__ sab, float h2,
@@ -491,8 +493,7 @@ __global__ void __launch_bounds__(256, 6) k_pass2_f32(Layout L, const float *__r
 // summed in plain FP32 with the approximate D of the bulk sweeps -- about the
 // cost of the FP32 pass, reaching residuals a few times above the
 // float-float pass's.  cell_fh is the arithmetic of one point, tile_fh that
-// of a pair of unknowns; k_pass2_fh launches it (48 registers for five CTAs
-// per SM).
+// of a pair of unknowns; k_pass2_fh launches it.
 template <int LIM, int ROUNDS>
 __device__ __forceinline__ void cell_fh(float p0, float p0lo, const float ps[6], const float ls[6],
                                         const float Ds[6], float s_, float ah, float jj, int lim_rt, float larsen_n,
@@ -566,8 +567,10 @@ __device__ __forceinline__ void tile_fh(const Layout &L, const float *__restrict
     }
 }
 
+// The launched hi/lo pass (64 registers, four CTAs per SM, no spills; at
+// five CTAs per SM it spilled and ran 15 % slower at 256^3).
 template <int LIM, int ROUNDS, bool BF>
-__global__ void __launch_bounds__(256, 5) k_pass2_fh(Layout L, const float *__restrict__ sp,
+__global__ void __launch_bounds__(256, 4) k_pass2_fh(Layout L, const float *__restrict__ sp,
                                                   const float *__restrict__ ah2, const float *__restrict__ jh2,
                                                   const uint16_t *__restrict__ spb,
                                                   const uint16_t *__restrict__ sab, float h2,
