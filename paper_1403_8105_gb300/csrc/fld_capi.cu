@@ -1497,8 +1497,8 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
             d.L = e.g->L;
             d.sp = e.g->f.sp; d.ah2 = e.g->f.ah2; d.jh2 = e.g->f.jh2; d.phi = e.g->f.phi; d.phlo = e.g->f.phlo;
             d.D = e.g->f.D; d.Df = e.g->f.Df;
-            d.omega = (float)e.pp.omega; d.inv2h = (float)e.pp.inv2h; d.floor_ = (float)e.pp.floor_;
-            d.larsen_n = (float)e.pp.larsen_n; d.lim = e.pp.lim; d.rounds = e.pp.local_iters;
+            d.inv2h = (float)e.pp.inv2h; d.floor_ = (float)e.pp.floor_;
+            d.larsen_n = (float)e.pp.larsen_n; d.lim = e.pp.lim;
             d.mode = e.fam == FAM_F32 ? 0 : 1;
             d.active = 1;
             residual_dims(e.g->L, &d.res_bx, &d.res_by);

@@ -145,14 +145,12 @@ cudaError_t launch_validate(long long n, const Fields &f, const float *sigma_t, 
 struct alignas(16) BatchDesc {
     Layout L;
     float *sp, *ah2, *jh2, *phi, *phlo, *D, *Df;
-    float omega, inv2h, floor_, larsen_n;
-    int lim, rounds;
+    float inv2h, floor_, larsen_n;
+    int lim;
     int mode;            // 0: single-precision sweeps, 1: float-float correction sweeps
     int active;          // 0: converged / stopped, its CTAs return at once
-    int pass_first, pass_bx, pass_by;   // (unused by the residual) pass grid dims
-    int res_first, res_bx, res_by;      // same for the residual table
+    int res_first, res_bx, res_by;      // first CTA of this grid in the residual table, grid dims
     int res_slot;                       // first partial-sum slot of this grid
-    int pad_[3];
 };
 static_assert(sizeof(BatchDesc) % 16 == 0, "BatchDesc is read with 16-byte loads");
 
