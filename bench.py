@@ -865,7 +865,7 @@ def run_c3(args):
 
 # The paper's end-to-end render times (GTX TITAN, single precision, solve to
 # Rbar/jbar = 1e-4 on a grid of a quarter of the data's resolution, light bake
-# and 1024^2 primary ray march included; Sec. 7, Figs. 1, 8, 9): context only.
+# and 1024^2 primary ray march included; Sec. 6.2, Figs. 1, 8, 9): context only.
 PAPER_RENDER_S = {"nebulae": 0.6, "manix": 1.8, "explosion": 0.7}
 
 

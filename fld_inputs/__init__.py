@@ -11,8 +11,8 @@ voxel (i, j, k) centred at ((i + 1/2) h, (j + 1/2) h, (k + 1/2) h) on a grid of
 spacing h.
 
 The paper's datasets (Nebulae 200^3, MANIX CT, explosion) are not available;
-its CPU testbed used "an embedded spherical cloud (with a vacuum exterior)"
-driven by Perlin noise (Sec. 5).  The fBm sphere cloud below stands in for
+its CPU testbed was a spherical cloud embedded in vacuum, driven by Perlin
+noise (Sec. 5).  The fBm sphere cloud below stands in for
 those workloads.  The paper does not define its noise, so the definition here
 is this project's own:
 
@@ -229,7 +229,7 @@ class Scene:
 
 def paper_scene(name: str) -> Scene:
     """Stand-ins for the paper's three rendered datasets, with their grid
-    shapes (Sec. 7): "nebulae" -- 200^3, albedo 0.9, one directional light;
+    shapes (Sec. 6.2): "nebulae" -- 200^3, albedo 0.9, one directional light;
     "manix" -- 256 x 329 x 256 (x, y, z), extinction and a per-channel (RGB)
     albedo from one density via a transfer function; "explosion" -- 201 x
     272 x 230, albedo 1, a black-body-like emission field from a second noise

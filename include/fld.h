@@ -364,10 +364,10 @@ typedef struct {
  * fld_solve).  phi_grid: NULL to take phi from g itself, or a coarser grid
  * covering g's box whose solved phi is blended trilinearly (between its
  * voxel centres) to g's voxel centres before the march -- the
- * quarter-resolution solve of Sec. 7 (see fld_downsample).  radiance:
+ * quarter-resolution solve of Sec. 6.2 (see fld_downsample).  radiance:
  * width*height floats, row-major, or NULL; codes:
  * width*height bytes of round(255 min(1, (exposure L)^(1/gamma))), the gamma
- * compression of Sec. 7, or NULL (one of the two must be given).  `where`
+ * compression of Sec. 6.2, or NULL (one of the two must be given).  `where`
  * (fld_mem) applies to both outputs; with host outputs the call returns when
  * they are written.  Keeps a 16-byte-per-voxel sampling volume with the
  * grid.  Errors: FLD_ERR_INVALID_ARG for a bad camera, exposure <= 0 or
@@ -375,7 +375,7 @@ typedef struct {
 fld_status fld_render(fld_grid g, fld_grid phi_grid, const fld_camera *cam, float *radiance, unsigned char *codes,
                       double exposure, double gamma, int where);
 
-/* Quarter-resolution solve (Sec. 7: phi is solved on a grid with a quarter
+/* Quarter-resolution solve (Sec. 6.2: phi is solved on a grid with a quarter
  * of the data's resolution per axis, the multiply scattered light being much
  * smoother than the medium): set the coarse grid's medium and source from
  * the fine grid's by box averages over factor^3 blocks -- sigma_t and the

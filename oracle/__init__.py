@@ -300,7 +300,7 @@ def render(sigma_t: np.ndarray, albedo: np.ndarray, q: np.ndarray, phi: np.ndarr
 
 
 def downsample(sigma_t: np.ndarray, albedo: np.ndarray, q: np.ndarray, factor: int = 4):
-    """Box averages over factor^3 blocks (Sec. 7's quarter-resolution solve):
+    """Box averages over factor^3 blocks (Sec. 6.2's quarter-resolution solve):
     returns (sigma_t_c, albedo_c, q_c) on the ceil(n / factor) grid."""
     lib = _load()
     sigma_t = np.ascontiguousarray(sigma_t, dtype=np.float32)
@@ -330,7 +330,7 @@ def upsample(phi_c: np.ndarray, fine_shape, h: float, factor: int = 4) -> np.nda
 
 
 def tonemap(radiance: np.ndarray, exposure: float = 1.0, gamma: float = 2.2) -> np.ndarray:
-    """Gamma compression to 8 bits (Sec. 7): round(255 clamp((e L)^(1/gamma), 0, 1))."""
+    """Gamma compression to 8 bits (Sec. 6.2): round(255 clamp((e L)^(1/gamma), 0, 1))."""
     v = np.clip(exposure * np.asarray(radiance, dtype=np.float64), 0.0, None) ** (1.0 / gamma)
     return np.floor(255.0 * np.clip(v, 0.0, 1.0) + 0.5).astype(np.uint8)
 

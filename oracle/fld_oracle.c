@@ -825,7 +825,7 @@ void fldo_render_pixels(int nx, int ny, int nz, double h, const double *sigma_t,
 }
 
 /* ------------------------------------------------------------------------ */
-/* Quarter-resolution solve (Sec. 7: phi is solved on a grid with a quarter  */
+/* Quarter-resolution solve (Sec. 6.2: phi is solved on a grid with a quarter  */
 /* of the data's resolution per axis, then used at full resolution in the    */
 /* ray march).  Downsampling: the coarse voxel (I,J,K) covers the fine       */
 /* voxels f I .. f I + f - 1 per axis (those that exist); sigma_t, sigma_s =  */

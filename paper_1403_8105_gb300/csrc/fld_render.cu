@@ -9,7 +9,7 @@
 // phi into one float4 per voxel (unpadded, x fastest), so that each sample's
 // trilinear blend reads eight 16-byte corners; k_render marches one pixel per
 // thread in 16x16 tiles (neighbouring rays touch neighbouring voxels, which
-// stay in L1/L2) and also writes the gamma-compressed 8-bit code of Sec. 7.
+// stay in L1/L2) and also writes the gamma-compressed 8-bit code of Sec. 6.2.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -57,7 +57,7 @@ __device__ __forceinline__ float phi_trilinear(const Layout &C, const float *__r
 
 // One float4 {sigma_t, albedo sigma_t, source, phi} per voxel.  phi is the
 // grid's own (coarse == false) or a coarser grid's, upsampled trilinearly to
-// this grid's voxel centres (the quarter-resolution solve of Sec. 7).
+// this grid's voxel centres (the quarter-resolution solve of Sec. 6.2).
 __global__ void k_render_pack(Layout L, const float *__restrict__ st, const float *__restrict__ alb,
                               const float *__restrict__ q, const float *__restrict__ phi,
                               const float *__restrict__ phlo, const double *__restrict__ phi64, bool coarse,

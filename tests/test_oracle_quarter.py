@@ -1,4 +1,4 @@
-"""Pins of the oracle's quarter-resolution path (Sec. 7: phi solved on a grid
+"""Pins of the oracle's quarter-resolution path (Sec. 6.2: phi solved on a grid
 with a quarter of the data's resolution per axis, used at full resolution in
 the ray march).
 
