@@ -75,6 +75,10 @@ def parse_args():
                     help="residual at which the float-float sweeps take over (0 = library default)")
     ap.add_argument("--nested", type=int, default=0,
                     help="start each solve from the solution of this many 2x coarser problems (0: cold start)")
+    ap.add_argument("--anderson", type=int, default=0,
+                    help="Anderson mixing over this many blocks of sweeps in the timed solves (0: plain SOR)")
+    ap.add_argument("--anderson-m", type=int, default=8, help="extra 'anderson': history length")
+    ap.add_argument("--anderson-check", type=int, default=64, help="extra 'anderson': sweeps per block")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="CPU-baseline sample length")
     ap.add_argument("--no-extras", action="store_true", help="skip cpu baseline / 256^3 roofline / e2e")
@@ -245,7 +249,8 @@ def workload_config(args, ranks):
         "precision": "mixed: fp32 sweeps, float-float correction sweeps after the fp32 stall",
         "start": (f"nested: from the solution of {args.nested} successively 2x coarser box-averaged problems"
                   if args.nested else "cold: the paper's initial state, omega = 1 warm-up"),
-        "scheme": "red-black SOR (Algorithm 1), self-consistent point update (local_iters=2)",
+        "scheme": "red-black SOR (Algorithm 1), self-consistent point update (local_iters=2)"
+                  + (f", Anderson mixing over the last {args.anderson} blocks of sweeps" if args.anderson else ""),
         "limiter": "levermore-pomraning",
         "tol": args.tol,
         "l2": "flushed (256 MB write) before every timed step; the 128^3 working set (~70 MB) is L2-resident "
@@ -279,7 +284,7 @@ def run_gpu(args):
     g = fld.Grid(n, n, n, h, stream=stream.cuda_stream)
     p = fld.params(limiter="lp", precision="mixed", tol=args.tol, omega=args.omega, local_iters=2,
                    check_every=args.check_every, max_iters=args.max_iters, fp32_switch=args.fp32_switch,
-                   nested=args.nested)
+                   nested=args.nested, anderson=args.anderson)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
 
     def step():
@@ -347,6 +352,7 @@ def run_gpu(args):
         extras["roofline_hbm_resident"] = roofline_256(fld, torch, dev, sig_np, alb_np, roof)
         extras["roofline_jacobi"] = roofline_jacobi(fld, torch, dev, sig_np, alb_np, peak, peak_src)
         extras["nested_start"] = nested_measure(fld, torch, g, stream, flush, sig, alb, p, n)
+        extras["anderson"] = anderson_measure(fld, torch, g, stream, flush, sig, alb, p, n, args)
         extras["e2e"] = e2e_measure(fld, g, sig_np, alb_np, p, n, args)
         extras["cpu_baseline"] = cpu_baseline(sig_np, alb_np, n, args.cpu_seconds)
     g.close()
@@ -427,6 +433,36 @@ def nested_measure(fld, torch, g, stream, flush, sig, alb, p, n):
     return {"time_to_residual_s_p50": statistics.median(times), "iterations": r.iterations,
             "coarse_iterations": r.iterations_coarse, "coarse_grid": [(n + 1) // 2] * 3,
             "voxel_updates_per_s": (r.iterations * n ** 3 + r.updates_coarse) / (r.ms / 1e3),
+            "rel_residual": r.rel_residual, "status": fld.fld_status_string(r.status)}
+
+
+def anderson_measure(fld, torch, g, stream, flush, sig, alb, p, n, args):
+    """The same cold solve with Anderson mixing over the last --anderson-m
+    blocks of --anderson-check sweeps (fld_solve_params.anderson): one
+    warm-up, then the median of 3."""
+    import ctypes
+    q = type(p)()
+    ctypes.memmove(ctypes.byref(q), ctypes.byref(p), ctypes.sizeof(p))
+    q.anderson = args.anderson_m
+    q.check_every = args.anderson_check
+    q.nested = 0
+    times, res = [], []
+    with torch.cuda.stream(stream):
+        for k in range(4):
+            flush.fill_(1.0)
+            stream.synchronize()
+            g.set_medium(sig, alb)
+            g.bake_directional((0.0, 0.0, -1.0), 1.0)
+            r = g.solve(q, check=False)
+            if k:
+                times.append(r.ms / 1e3)
+                res.append(r)
+    r = res[0]
+    return {"m": args.anderson_m, "sweeps_per_block": args.anderson_check,
+            "time_to_residual_s_p50": statistics.median(times), "iterations": r.iterations,
+            "iterations_by_family": {"fp32": r.iterations_fp32, "fh": r.iterations_mid, "ff": r.iterations_corr},
+            "mixing_steps": r.anderson_steps, "history_restarts": r.anderson_resets,
+            "voxel_updates_per_s": r.iterations * n ** 3 / (r.ms / 1e3),
             "rel_residual": r.rel_residual, "status": fld.fld_status_string(r.status)}
 
 

@@ -157,6 +157,23 @@ typedef struct {
                              the start removes the smooth error SOR is slowest
                              on.  Coarse edges stay >= 8.  0 (default): the
                              paper's initial state.  Not in the paper.        */
+    int anderson;         /* fld_solve only: Anderson mixing over the last
+                             `anderson` blocks (2..16) of check_every sweeps.
+                             Each block of red-black sweeps (Algorithm 1) is a
+                             map G(phi) with the solution of Eq. 31 as its fixed
+                             point; after a block, the next one starts from
+                             sum_i a_i G(x_i), sum a_i = 1, with the weights that
+                             minimise |sum_i a_i (G(x_i) - x_i)| (Gram matrix
+                             reduced in FP64 on the device, solved on the host).
+                             The fixed point is the same; SOR's slow smooth
+                             error is removed much faster.  The history restarts
+                             after the warm-up, at precision switches and when
+                             the safeguard returns to its best state.  Costs
+                             12 bytes per voxel per slot plus 8.  Red-black
+                             scheme only (mixed Jacobi sweeps, whose error
+                             modes near -1 the mix amplifies, diverged on the
+                             oracle).  0 (default): plain red-black SOR.  Not
+                             in the paper.                                     */
 } fld_solve_params;
 
 typedef struct {
@@ -180,6 +197,8 @@ typedef struct {
     int iterations_coarse; /* nested: iterations on the coarser grids (summed)    */
     double ms_coarse;      /* nested: their device time (included in ms)          */
     long long updates_coarse; /* nested: their voxel updates                      */
+    int anderson_steps;    /* anderson: blocks whose successor started from a mix */
+    int anderson_resets;   /* anderson: history restarts (ill-conditioned weights) */
 } fld_solve_result;
 
 /* Fill *p with the defaults: LP limiter, Larsen n = 2, omega auto,

@@ -95,6 +95,10 @@ struct fld_grid_s {
     // last good state of a solve (float family: phi, lo, D; FP64: phi, D)
     float *snap_phi = nullptr, *snap_lo = nullptr, *snap_D = nullptr;
     double *snap_phi64 = nullptr, *snap_D64 = nullptr;
+    // Anderson mixing (fld_solve_params.anderson): history slots, allocated on first use
+    AndersonBuffers anderson{};
+    int anderson_slots = 0;
+    int nsm = 0;
 };
 
 namespace {
@@ -143,6 +147,82 @@ fld_status ensure_jacobi(fld_grid_s *g, Family fam) {
         return fail(FLD_ERR_OOM, "cudaMalloc of the Jacobi buffer failed");
     }
     return FLD_OK;
+}
+
+void free_anderson(fld_grid_s *g) {
+    void *ptrs[] = {g->anderson.g, g->anderson.f, g->anderson.x, g->anderson.part, g->anderson.dots};
+    for (void *q : ptrs)
+        if (q) cudaFree(q);
+    g->anderson = AndersonBuffers{};
+    g->anderson_slots = 0;
+}
+
+// History of m slots for Anderson mixing (allocated outside graph capture).
+fld_status ensure_anderson(fld_grid_s *g, int m) {
+    if (g->anderson_slots >= m) return FLD_OK;
+    FLD_CK(cudaStreamSynchronize(g->stream));
+    free_anderson(g);
+    if (g->nsm <= 0) {
+        FLD_CK(cudaDeviceGetAttribute(&g->nsm, cudaDevAttrMultiProcessorCount, g->device));
+        if (g->nsm <= 0) g->nsm = 1;
+    }
+    const size_t n = (size_t)g->L.total;
+    AndersonBuffers &b = g->anderson;
+    if (cudaMalloc((void **)&b.g, sizeof(double) * n * m) != cudaSuccess ||
+        cudaMalloc((void **)&b.f, sizeof(float) * n * m) != cudaSuccess ||
+        cudaMalloc((void **)&b.x, sizeof(double) * n) != cudaSuccess ||
+        cudaMalloc((void **)&b.part, sizeof(double) * kAndersonMax * 4 * (size_t)g->nsm) != cudaSuccess ||
+        cudaMalloc((void **)&b.dots, sizeof(double) * kAndersonMax) != cudaSuccess) {
+        (void)cudaGetLastError();
+        free_anderson(g);
+        return fail(FLD_ERR_OOM, "cudaMalloc of the Anderson history failed");
+    }
+    g->anderson_slots = m;
+    return FLD_OK;
+}
+
+// Weights of Anderson mixing over w slots: minimise |sum a_i f_i| subject to
+// sum a_i = 1, i.e. a = y / sum(y) with (G + lambda I) y = 1, G the Gram
+// matrix <f_i, f_j> and lambda = 1e-12 of its mean diagonal (Tikhonov).
+// Gaussian elimination with partial pivoting; false if the system is
+// singular or the weights are not finite or exceed kAndersonMaxWeight.
+constexpr double kAndersonMaxWeight = 1e3;
+bool anderson_weights(const double gram[kAndersonMax][kAndersonMax], int w, double *a) {
+    double A[kAndersonMax][kAndersonMax + 1];
+    double tr = 0.0;
+    for (int i = 0; i < w; ++i) tr += gram[i][i];
+    const double lam = 1e-12 * (tr / w);
+    if (!(tr > 0.0) || !isfinite(tr)) return false;
+    for (int i = 0; i < w; ++i) {
+        for (int j = 0; j < w; ++j) A[i][j] = gram[i][j] + (i == j ? lam : 0.0);
+        A[i][w] = 1.0;
+    }
+    for (int c = 0; c < w; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < w; ++r)
+            if (fabs(A[r][c]) > fabs(A[piv][c])) piv = r;
+        if (!(fabs(A[piv][c]) > 0.0)) return false;
+        if (piv != c)
+            for (int k = c; k <= w; ++k) std::swap(A[c][k], A[piv][k]);
+        for (int r = c + 1; r < w; ++r) {
+            const double m = A[r][c] / A[c][c];
+            for (int k = c; k <= w; ++k) A[r][k] -= m * A[c][k];
+        }
+    }
+    double y[kAndersonMax];
+    for (int r = w - 1; r >= 0; --r) {
+        double v = A[r][w];
+        for (int k = r + 1; k < w; ++k) v -= A[r][k] * y[k];
+        y[r] = v / A[r][r];
+    }
+    double sum = 0.0;
+    for (int i = 0; i < w; ++i) sum += y[i];
+    if (!(fabs(sum) > 0.0) || !isfinite(sum)) return false;
+    for (int i = 0; i < w; ++i) {
+        a[i] = y[i] / sum;
+        if (!isfinite(a[i]) || fabs(a[i]) > kAndersonMaxWeight) return false;
+    }
+    return true;
 }
 
 // sigma_eps = 1e-3 / L with L the largest grid extent (Sec. 5), unless given.
@@ -406,6 +486,10 @@ fld_status check_params(const fld_grid_s *g, const fld_solve_params *p) {
     if (p->warmup_iters < -1) return fail(FLD_ERR_INVALID_ARG, "warmup_iters must be >= -1");
     if (p->scheme != FLD_SCHEME_RED_BLACK && p->scheme != FLD_SCHEME_JACOBI)
         return fail(FLD_ERR_INVALID_ARG, "unknown scheme");
+    if (p->anderson < 0 || p->anderson > kAndersonMax)
+        return fail(FLD_ERR_INVALID_ARG, "anderson must lie in [0, 16]");
+    if (p->anderson > 0 && p->scheme == FLD_SCHEME_JACOBI)
+        return fail(FLD_ERR_INVALID_ARG, "Anderson mixing accelerates the red-black scheme only");
     if (p->scheme == FLD_SCHEME_JACOBI) {
         if (p->precision != FLD_PREC_FP32 && p->precision != FLD_PREC_FP64)
             return fail(FLD_ERR_INVALID_ARG, "the Jacobi scheme runs in FP32 or FP64 precision");
@@ -606,6 +690,7 @@ void fld_default_params(fld_solve_params *p) {
     p->phi_b = -1.0;
     p->D_b = -1.0;
     p->warmup_iters = -1;
+    p->anderson = 0;
 }
 
 const char *fld_status_string(fld_status s) {
@@ -717,6 +802,7 @@ void fld_destroy(fld_grid g) {
     void *snaps[] = {g->snap_phi, g->snap_lo, g->snap_D, g->snap_phi64, g->snap_D64};
     for (void *p : snaps)
         if (p) cudaFree(p);
+    free_anderson(g);
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
     delete g;
 }
@@ -1181,8 +1267,32 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
     else if (a == ACT_DIVERGED) outcome = FLD_ERR_DIVERGED;
     else if ((st = save()) != FLD_OK) return st;
     const int warm = warmup_of(g, p);
+    // Anderson mixing (fld_solve_params.anderson): after the warm-up, each
+    // block of sweeps is one application of the fixed-point map G; the next
+    // block starts from the mix of the last `am` images.
+    const int am = p->anderson;
+    if (am > 0 && (st = ensure_anderson(g, am)) != FLD_OK) return st;
+    double gram[kAndersonMax][kAndersonMax] = {};
+    int acount = 0;          // blocks collected since the history (re)started
+    bool have_x = false;     // the Anderson x holds the state the next block starts from
+    auto state_ptrs = [&](float **hi, float **lo, double **p64) {
+        const bool d = fam == FAM_F64;
+        *hi = d ? nullptr : g->f.phi;
+        *lo = !d && g->lo_live ? g->f.phlo : nullptr;
+        *p64 = d ? g->f.phi64 : nullptr;
+    };
     while (outcome == FLD_ERR_NOT_CONVERGED && it < p->max_iters) {
         const int k = block_len(it, p->check_every, p->max_iters, warm);
+        const bool mixing = am > 0 && it >= warm;
+        if (mixing && !have_x) {
+            float *hi, *lo;
+            double *p64;
+            state_ptrs(&hi, &lo, &p64);
+            FLD_CK(launch_anderson_capture(g->anderson, g->L.total, hi, lo, p64, g->nsm, g->stream));
+            g->kernels += 1;
+            have_x = true;
+            acount = 0;
+        }
         FLD_CK(cudaEventRecord(g->evb0, g->stream));
         if ((st = run_block(g, fam, block_params(pp, it, warm), k)) != FLD_OK) return st;
         FLD_CK(cudaEventRecord(g->evb1, g->stream));
@@ -1212,16 +1322,47 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
             g->lo_live = snap_lo_live;
             pp.omega = 1.0 + 0.97 * (pp.omega - 1.0);
             rel = ctl.best;
+            have_x = false;
             break;
         case ACT_SWITCH:
             fam = next_family(fam);
             if ((st = sync_family(g, fam)) != FLD_OK) return st;
             ctl.fam = fam;
             ctl.begin_phase();
+            have_x = false;
             break;
         case ACT_CONTINUE: break;
         }
         if (stalled) break;
+        // Anderson step after a block that made ordinary progress (never after
+        // the last one: the solve ends on a checked state)
+        if (mixing && have_x && (a == ACT_CONTINUE || a == ACT_SAVE) && it < p->max_iters) {
+            const int slot = acount % am;
+            ++acount;
+            const int w = acount < am ? acount : am;
+            float *hi, *lo;
+            double *p64;
+            state_ptrs(&hi, &lo, &p64);
+            FLD_CK(launch_anderson_collect(g->anderson, g->L.total, hi, lo, p64, slot, w, g->nsm, g->stream));
+            double dots[kAndersonMax];
+            FLD_CK(cudaMemcpyAsync(dots, g->anderson.dots, sizeof(double) * w, cudaMemcpyDeviceToHost, g->stream));
+            FLD_CK(cudaStreamSynchronize(g->stream));
+            g->kernels += 2;
+            for (int j = 0; j < w; ++j) gram[slot][j] = gram[j][slot] = dots[j];
+            double wts[kAndersonMax];
+            bool ok = true;
+            if (w == 1) wts[0] = 1.0;   // x = g: the next block starts where this one ended
+            else ok = anderson_weights(gram, w, wts);
+            if (ok) {
+                FLD_CK(launch_anderson_mix(g->anderson, g->L.total, slot, w, wts, hi, lo, p64, g->nsm, g->stream));
+                g->kernels += 1;
+                if (w > 1) ++res.anderson_steps;
+            } else {
+                // ill-conditioned history: continue from this block's result
+                ++res.anderson_resets;
+                have_x = false;
+            }
+        }
     }
     res.omega_backoffs = ctl.backoffs;
     FLD_CK(cudaEventRecord(g->ev1, g->stream));
@@ -1343,6 +1484,7 @@ fld_status fld_server_create(const fld_solve_params *p, void *stream, fld_server
     if (!p) return fail(FLD_ERR_INVALID_ARG, "params is NULL");
     if (p->precision == FLD_PREC_FP64 || p->precision < 0 || p->precision > FLD_PREC_PAIR)
         return fail(FLD_ERR_INVALID_ARG, "the server runs the FP32 / MIXED / PAIR sweeps; use fld_solve for FP64");
+    if (p->anderson != 0) return fail(FLD_ERR_INVALID_ARG, "Anderson mixing runs in fld_solve only");
     if (p->limiter < FLD_LIM_CDA || p->limiter > FLD_LIM_LP) return fail(FLD_ERR_INVALID_ARG, "unknown limiter");
     if (p->limiter == FLD_LIM_LARSEN && !(p->larsen_n > 0.0)) return fail(FLD_ERR_INVALID_ARG, "larsen_n must be > 0");
     if (p->omega > 0.0 && !(p->omega < 2.0)) return fail(FLD_ERR_INVALID_ARG, "omega must lie in (0, 2)");
@@ -1587,6 +1729,7 @@ fld_status fld_solve_batch(fld_grid *grids, int count, const fld_solve_params *p
     if ((st = check_params(grids[0], p)) != FLD_OK) return st;
     if (p->precision == FLD_PREC_FP64)
         return fail(FLD_ERR_INVALID_ARG, "batched solves run the FP32 / MIXED sweeps; use fld_solve for FP64");
+    if (p->anderson != 0) return fail(FLD_ERR_INVALID_ARG, "Anderson mixing runs in fld_solve only");
     if (!(p->tol >= 0.0)) return fail(FLD_ERR_INVALID_ARG, "tol must be >= 0");
     if (p->max_iters < 0 || p->check_every < 1) return fail(FLD_ERR_INVALID_ARG, "bad max_iters / check_every");
     // Grids of one group should keep their per-iteration working set (24 bytes

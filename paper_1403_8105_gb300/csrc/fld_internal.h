@@ -162,6 +162,27 @@ cudaError_t launch_residual_batch(const BatchDesc *descs, const int *cta_grid, i
 // Pass / residual grid dimensions of a layout (CTAs = x * y * nz).
 void residual_dims(const Layout &L, int *bx, int *by);
 
+// Anderson mixing of blocks of sweeps (fld_anderson.cu): m history slots of
+// g (FP64) and f (FP32) per element of the padded field, the current start
+// point x (FP64), per-CTA partial dot products and their m sums.
+constexpr int kAndersonMax = 16;
+struct AndersonBuffers {
+    double *g = nullptr;      // m * total
+    float *f = nullptr;       // m * total
+    double *x = nullptr;      // total
+    double *part = nullptr;   // (4 * SMs) * kAndersonMax
+    double *dots = nullptr;   // kAndersonMax
+};
+// x = the current state (hi + lo, hi alone when lo is null, or p64).
+cudaError_t launch_anderson_capture(const AndersonBuffers &b, int n, const float *hi, const float *lo,
+                                    const double *p64, int nsm, cudaStream_t s);
+// g -> slot, f = g - x -> slot, dots[j] = <f, f_j> for the w occupied slots.
+cudaError_t launch_anderson_collect(const AndersonBuffers &b, int n, const float *hi, const float *lo,
+                                    const double *p64, int slot, int w, int nsm, cudaStream_t s);
+// state = x = g_slot + sum_{j != slot} a_j (g_j - g_slot).
+cudaError_t launch_anderson_mix(const AndersonBuffers &b, int n, int slot, int w, const double *a, float *hi,
+                                float *lo, double *p64, int nsm, cudaStream_t s);
+
 // Sets the thread-local text that fld_last_error() returns.
 void set_error_text(const char *msg);
 

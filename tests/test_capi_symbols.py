@@ -45,6 +45,7 @@ def test_default_params_and_status_strings():
     p = fld.fld_default_params()
     assert p.limiter == fld.LIMITERS["lp"] and p.precision == fld.PRECISIONS["mixed"]
     assert p.tol == 1e-6 and p.local_iters == 2 and p.check_every >= 1
+    assert p.anderson == 0 and p.nested == 0          # plain red-black SOR from the paper's start
     assert fld.fld_status_string(fld.FLD_ERR_DIVERGED) == "FLD_ERR_DIVERGED"
     assert fld.fld_status_string(99) == "FLD_ERR_UNKNOWN"
 
