@@ -22,7 +22,9 @@ samples of its iterations) on the host cores.
 Besides the headline line's roofline of the dominant sweep kernel, the cloud
 workload reports the other sweep families, the same sweeps at 256^3 (HBM-
 resident), the Jacobi iteration, the solve from a 2x coarser start (nested),
-the end-to-end number through the API with host buffers, and the oracle's
+the solve with Anderson mixing of its blocks of sweeps (anderson; --anderson M
+puts it in the timed solves instead), the end-to-end number through the API
+with host buffers, and the oracle's
 rate on the host cores.  Other workloads (--workload): c3 (the 256^3 three-
 limiter runs with the bfloat16 medium and oracle checks), batch (many solves
 of uneven size, one after another and batched), serve (a Poisson request
