@@ -158,7 +158,8 @@ typedef struct {
                              on.  Coarse edges stay >= 8.  0 (default): the
                              paper's initial state.  Not in the paper.        */
     int anderson;         /* fld_solve only: Anderson mixing over the last
-                             `anderson` blocks (2..16) of check_every sweeps.
+                             `anderson` blocks (at most 16; 1 mixes nothing) of
+                             check_every sweeps.
                              Each block of red-black sweeps (Algorithm 1) is a
                              map G(phi) with the solution of Eq. 31 as its fixed
                              point; after a block, the next one starts from
