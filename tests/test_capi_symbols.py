@@ -93,3 +93,13 @@ def test_no_cpu_fallback_without_device():
     with pytest.raises(fld.FldError) as e:
         fld.fld_create_grid(4, 4, 4, 0.25)
     assert e.value.status == fld.FLD_ERR_NO_DEVICE
+
+
+def test_server_rejects_anderson_before_touching_a_device():
+    # Anderson mixing is a fld_solve option; the server refuses it while
+    # checking its parameters, which happens before any device call.
+    import paper_1403_8105_gb300 as fld
+    with pytest.raises(fld.FldError) as e:
+        fld.fld_server_create(fld.params(anderson=4))
+    assert e.value.status == fld.FLD_ERR_INVALID_ARG
+    assert "Anderson" in fld.fld_last_error()
