@@ -103,6 +103,7 @@ def serve(requests, backend, max_active: int = 64, memory_fraction: float = 0.9,
     t0 = clock()
     steps = 0
     max_in_flight = 0
+    depth = []          # requests arrived but not admitted, after each admission round
     while pending or waiting or backend.active() > 0:
         now = clock() - t0
         while pending and pending[0].arrival <= now:
@@ -115,6 +116,7 @@ def serve(requests, backend, max_active: int = 64, memory_fraction: float = 0.9,
             req.admitted = clock() - t0
             grids[req.rid] = backend.admit(req)
         max_in_flight = max(max_in_flight, backend.active())
+        depth.append(len(waiting))
         if backend.active() == 0:
             if pending:
                 sleep(max(0.0, min(0.01, pending[0].arrival - (clock() - t0))))
@@ -142,6 +144,8 @@ def serve(requests, backend, max_active: int = 64, memory_fraction: float = 0.9,
         "latency_s_p99": float(np.percentile(lat, 99)) if len(lat) else None,
         "latency_s_mean": float(lat.mean()) if len(lat) else None,
         "queue_s_p99": float(np.percentile([r.admitted - r.arrival for r in done], 99)) if done else None,
+        "queue_depth_max": max(depth) if depth else 0,
+        "queue_depth_mean": float(np.mean(depth)) if depth else 0.0,
         "span_s": span,
         "throughput_req_s": len(done) / span if span > 0 else None,
     }

@@ -102,3 +102,18 @@ def test_request_that_never_fits_is_reported():
     clk = FakeClock()
     with pytest.raises(RuntimeError):
         serve.serve(_requests(count=3, foot=10 ** 6), FakeBackend(clk, free=1000), clock=clk, sleep=clk.sleep)
+
+
+def test_queue_depth_reflects_the_slot_limit():
+    # one slot and a burst of arrivals: requests pile up while the slot is
+    # busy; with many slots nobody waits
+    clk = FakeClock()
+    _, st1 = serve.serve(_requests(rate=500.0), FakeBackend(clk), max_active=1, clock=clk, sleep=clk.sleep)
+    clk = FakeClock()
+    _, st64 = serve.serve(_requests(rate=500.0), FakeBackend(clk, free=10 ** 9), max_active=64, clock=clk,
+                          sleep=clk.sleep)
+    assert st1["queue_depth_max"] > 5 and st1["queue_depth_mean"] > 1.0
+    assert st64["queue_depth_max"] == 0 and st64["queue_depth_mean"] == 0.0
+    # (with free slots a request still waits for the step in flight when it arrives)
+    assert st64["queue_s_p99"] <= 0.0101
+    assert st1["queue_s_p99"] > 10 * st64["queue_s_p99"]
