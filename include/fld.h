@@ -175,6 +175,18 @@ typedef struct {
                              modes near -1 the mix amplifies, diverged on the
                              oracle).  0 (default): plain red-black SOR.  Not
                              in the paper.                                     */
+    int fp64_verify;      /* MIXED only.  1 (default): once the float-float sweeps
+                             bring the residual (D evaluated in single precision)
+                             to tol, the state is converted to FP64 and the stop
+                             test of Algorithm 1 is taken on the residual of
+                             Eq. 37 evaluated entirely in FP64 (D recomputed from
+                             phi in double).  If that residual is still above tol
+                             -- the single-precision rounding of D leaves a floor
+                             of a few 1e-7 on large grids -- FP64 red-black sweeps
+                             follow, checked every min(check_every, 16)
+                             iterations, until it is at or below tol; the solve
+                             then ends in FP64.  0: stop on the single-precision-D
+                             residual.                                          */
 } fld_solve_params;
 
 typedef struct {
@@ -200,6 +212,12 @@ typedef struct {
     long long updates_coarse; /* nested: their voxel updates                      */
     int anderson_steps;    /* anderson: blocks whose successor started from a mix */
     int anderson_resets;   /* anderson: history restarts (ill-conditioned weights) */
+    int iterations_fp64;   /* MIXED with fp64_verify: FP64 sweeps after the
+                              float-float phase (counted in iterations too)   */
+    double ms_sweep_fp64;  /* device time inside those sweeps                 */
+    double rel_residual_single; /* MIXED with fp64_verify: the single-precision-D
+                              residual at which the FP64 check was first taken
+                              (rel_residual then holds the FP64 value)          */
 } fld_solve_result;
 
 /* Fill *p with the defaults: LP limiter, Larsen n = 2, omega auto,

@@ -50,7 +50,7 @@ class SolveParams(ctypes.Structure):
         ("warm_start", ctypes.c_int), ("phi0", ctypes.c_double), ("D0", ctypes.c_double),
         ("phi_b", ctypes.c_double), ("D_b", ctypes.c_double), ("warmup_iters", ctypes.c_int),
         ("medium_bf16", ctypes.c_int), ("scheme", ctypes.c_int), ("nested", ctypes.c_int),
-        ("anderson", ctypes.c_int),
+        ("anderson", ctypes.c_int), ("fp64_verify", ctypes.c_int),
     ]
 
 
@@ -64,6 +64,8 @@ class SolveResult(ctypes.Structure):
         ("omega_backoffs", ctypes.c_int), ("iterations_mid", ctypes.c_int), ("ms_sweep_mid", ctypes.c_double),
         ("iterations_coarse", ctypes.c_int), ("ms_coarse", ctypes.c_double), ("updates_coarse", ctypes.c_longlong),
         ("anderson_steps", ctypes.c_int), ("anderson_resets", ctypes.c_int),
+        ("iterations_fp64", ctypes.c_int), ("ms_sweep_fp64", ctypes.c_double),
+        ("rel_residual_single", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -54,6 +54,7 @@ constexpr int kMaxBackoffs = 8;               // omega reductions before reporti
 constexpr double kOmegaMax = 1.98;            // upper clamp of the automatic omega
 constexpr int kWarmupPerEdge = 4;             // automatic warm-up: iterations per voxel of the largest extent
 constexpr double kNestedTol = 1e-4;           // nested solves: tolerance of the coarser levels
+constexpr int kPolishBlock = 16;              // MIXED + fp64_verify: FP64 sweeps between FP64 checks
 
 struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
@@ -269,6 +270,14 @@ int block_len(int it, int check_every, int max_iters, int warm) {
     return k;
 }
 
+// Iterations between checks in family `fam`: the FP64 sweeps that follow a
+// MIXED solve's float-float phase only remove the rounding noise of the
+// single-precision D, so they are checked more often.
+int check_len(Family fam, int precision, int check_every) {
+    if (fam == FAM_F64 && precision == FLD_PREC_MIXED && check_every > kPolishBlock) return kPolishBlock;
+    return check_every;
+}
+
 // Pass parameters of a block starting at iteration `it`.
 PassParams block_params(const PassParams &pp, int it, int warm) {
     PassParams q = pp;
@@ -473,6 +482,23 @@ fld_status residual_now(fld_grid_s *g, Family fam, const PassParams &pp, int mar
     return FLD_OK;
 }
 
+// The stop test in FP64 (fld_solve_params.fp64_verify): the FP64 medium
+// (once per medium version), the current single-precision state converted to
+// double (hi + lo) and the residual of Eq. 37 with D recomputed from phi in
+// double.  Afterwards the state lives in the FP64 fields.
+fld_status fp64_check(fld_grid_s *g, const fld_solve_params *p, const PassParams &pp, double *rel) {
+    fld_status st = prepare(g, p, FAM_F64);
+    if (st != FLD_OK) return st;
+    if ((st = sync_family(g, FAM_F64)) != FLD_OK) return st;
+    return residual_now(g, FAM_F64, pp, p->residual_margin, rel);
+}
+
+// After a restore: the snapshot's family holds the state.
+void set_valid(fld_grid_s *g, Family fam) {
+    g->valid_d = fam == FAM_F64;
+    g->valid_float = fam != FAM_F64;
+}
+
 fld_status check_params(const fld_grid_s *g, const fld_solve_params *p) {
     if (!p) return fail(FLD_ERR_INVALID_ARG, "params is NULL");
     if (p->limiter < FLD_LIM_CDA || p->limiter > FLD_LIM_LP) return fail(FLD_ERR_INVALID_ARG, "unknown limiter");
@@ -490,6 +516,7 @@ fld_status check_params(const fld_grid_s *g, const fld_solve_params *p) {
         return fail(FLD_ERR_INVALID_ARG, "anderson must lie in [0, 16]");
     if (p->anderson > 0 && p->scheme == FLD_SCHEME_JACOBI)
         return fail(FLD_ERR_INVALID_ARG, "Anderson mixing accelerates the red-black scheme only");
+    if (p->fp64_verify != 0 && p->fp64_verify != 1) return fail(FLD_ERR_INVALID_ARG, "fp64_verify must be 0 or 1");
     if (p->scheme == FLD_SCHEME_JACOBI) {
         if (p->precision != FLD_PREC_FP32 && p->precision != FLD_PREC_FP64)
             return fail(FLD_ERR_INVALID_ARG, "the Jacobi scheme runs in FP32 or FP64 precision");
@@ -594,6 +621,14 @@ struct Controller {
         const double then = recent[(nrecent - 1 - kFlatWindow) % (kFlatWindow + 1)];
         return rel > (1.0 - kFlatGain) * then && rel < 1.1 * best && rel < kFlatBelow * initial;
     }
+    // The float-float phase met tol on its single-precision-D residual and the
+    // FP64 residual (rel) is above it: FP64 sweeps continue from here, with
+    // progress measured against that FP64 value.
+    void enter_fp64(double rel) {
+        fam = FAM_F64;
+        best = rel;
+        begin_phase();
+    }
     // First check (before any iteration): the state is kept as the fallback of
     // the safeguard, but progress is measured from the first block onwards
     // (SOR's early transient may sit above the initial residual for a while).
@@ -691,6 +726,7 @@ void fld_default_params(fld_solve_params *p) {
     p->D_b = -1.0;
     p->warmup_iters = -1;
     p->anderson = 0;
+    p->fp64_verify = 1;
 }
 
 const char *fld_status_string(fld_status s) {
@@ -1157,6 +1193,7 @@ fld_status solve_nested(fld_grid g, const fld_solve_params *p, fld_solve_result 
         if ((st = fld_downsample(chain[l - 1], chain[l], 2)) != FLD_OK) return st;
     fld_solve_params q = *p;
     q.nested = 0;
+    q.fp64_verify = 0;          // the coarser levels only provide a start
     q.tol = p->tol > kNestedTol ? p->tol : kNestedTol;
     q.check_every = p->check_every < 64 ? p->check_every : 64;
     fld_solve_result acc;
@@ -1193,6 +1230,7 @@ fld_status solve_nested(fld_grid g, const fld_solve_params *p, fld_solve_result 
         if (l == 0) {
             q.tol = p->tol;
             q.check_every = p->check_every;
+            q.fp64_verify = p->fp64_verify;
         }
         fld_solve_result rl;
         memset(&rl, 0, sizeof(rl));
@@ -1281,8 +1319,9 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
         *lo = !d && g->lo_live ? g->f.phlo : nullptr;
         *p64 = d ? g->f.phi64 : nullptr;
     };
+    const bool verify = p->precision == FLD_PREC_MIXED && p->fp64_verify;
     while (outcome == FLD_ERR_NOT_CONVERGED && it < p->max_iters) {
-        const int k = block_len(it, p->check_every, p->max_iters, warm);
+        const int k = block_len(it, check_len(fam, p->precision, p->check_every), p->max_iters, warm);
         const bool mixing = am > 0 && it >= warm;
         if (mixing && !have_x) {
             float *hi, *lo;
@@ -1297,8 +1336,10 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
         if ((st = run_block(g, fam, block_params(pp, it, warm), k)) != FLD_OK) return st;
         FLD_CK(cudaEventRecord(g->evb1, g->stream));
         it += k;
+        const bool polish = fam == FAM_F64 && p->precision == FLD_PREC_MIXED;
         if (fam == FAM_F32) res.iterations_fp32 += k;
         else if (fam == FAM_FH) res.iterations_mid += k;
+        else if (polish) res.iterations_fp64 += k;
         else res.iterations_corr += k;
         if ((st = residual_now(g, fam, pp, p->residual_margin, &rel)) != FLD_OK) return st;
         ++res.checks;
@@ -1306,10 +1347,26 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
         FLD_CK(cudaEventElapsedTime(&bms, g->evb0, g->evb1));
         if (fam == FAM_F32) res.ms_sweep_fp32 += bms;
         else if (fam == FAM_FH) res.ms_sweep_mid += bms;
+        else if (polish) res.ms_sweep_fp64 += bms;
         else res.ms_sweep_corr += bms;
         a = (warm > 0 && it == warm) ? ctl.restart(rel) : ctl.next(rel, pp.omega);
         switch (a) {
-        case ACT_CONVERGED: outcome = FLD_OK; break;
+        case ACT_CONVERGED:
+            if (verify && fam == FAM_FF) {
+                // the stop test of Algorithm 1 in FP64
+                double r64 = 0.0;
+                if ((st = fp64_check(g, p, pp, &r64)) != FLD_OK) return st;
+                ++res.checks;
+                res.rel_residual_single = rel;
+                rel = r64;
+                fam = FAM_F64;
+                ctl.enter_fp64(r64);
+                have_x = false;
+                if (r64 <= p->tol) outcome = FLD_OK;
+            } else {
+                outcome = FLD_OK;
+            }
+            break;
         case ACT_DIVERGED: outcome = FLD_ERR_DIVERGED; break;
         case ACT_STALLED: stalled = true; break;
         case ACT_SAVE:
@@ -1319,6 +1376,7 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
             if ((st = snapshot(g, snap_fam, false)) != FLD_OK) return st;
             fam = snap_fam;
             ctl.fam = fam;
+            set_valid(g, fam);
             g->lo_live = snap_lo_live;
             pp.omega = 1.0 + 0.97 * (pp.omega - 1.0);
             rel = ctl.best;
@@ -1364,6 +1422,10 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
             }
         }
     }
+    // a MIXED solve that ended in the FP64 sweeps hands its state back to the
+    // hi/lo fields (about 48 significant bits), where MIXED warm starts and the
+    // batched paths continue from
+    if (fam == FAM_F64 && p->precision == FLD_PREC_MIXED && (st = sync_family(g, FAM_FF)) != FLD_OK) return st;
     res.omega_backoffs = ctl.backoffs;
     FLD_CK(cudaEventRecord(g->ev1, g->stream));
     FLD_CK(cudaEventSynchronize(g->ev1));
@@ -1612,7 +1674,7 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
         std::vector<int> k(n);
         for (size_t i = 0; i < n; ++i) {
             ServerEntry &e = s->active[i];
-            k[i] = block_len(e.res.iterations, p->check_every, p->max_iters, e.warm);
+            k[i] = block_len(e.res.iterations, check_len(e.fam, p->precision, p->check_every), p->max_iters, e.warm);
             if (k[i] <= 0) continue;
             e.g->stream = s->side[i % nside];
             st = run_block(e.g, e.fam, block_params(e.pp, e.res.iterations, e.warm), k[i]);
@@ -1622,6 +1684,7 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
             e.res.iterations += k[i];
             if (e.fam == FAM_F32) e.res.iterations_fp32 += k[i];
             else if (e.fam == FAM_FH) e.res.iterations_mid += k[i];
+            else if (e.fam == FAM_F64) e.res.iterations_fp64 += k[i];
             else e.res.iterations_corr += k[i];
         }
         for (size_t i = 0; i < nside; ++i) {
@@ -1629,12 +1692,18 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
             FLD_CK(cudaStreamWaitEvent(s->bs, s->join[i], 0));
         }
         // -- residuals of all active grids in one batched pass
+        // (grids in their FP64 sweeps are checked one by one, as fld_solve does)
         std::vector<BatchDesc> hd(n);
         std::vector<int> res_tab, res_count(n);
         int slots = 0;
         for (size_t i = 0; i < n; ++i) {
             const ServerEntry &e = s->active[i];
             BatchDesc &d = hd[i];
+            if (e.fam == FAM_F64) {
+                memset(&d, 0, sizeof(d));
+                res_count[i] = 0;
+                continue;
+            }
             memset(&d, 0, sizeof(d));
             d.L = e.g->L;
             d.sp = e.g->f.sp; d.ah2 = e.g->f.ah2; d.jh2 = e.g->f.jh2; d.phi = e.g->f.phi; d.phlo = e.g->f.phlo;
@@ -1660,18 +1729,40 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
         std::vector<double> out(2 * n);
         FLD_CK(cudaMemcpyAsync(out.data(), s->d_out, sizeof(double) * 2 * n, cudaMemcpyDeviceToHost, s->bs));
         FLD_CK(cudaStreamSynchronize(s->bs));
+        std::vector<double> rel64(n, 0.0);
+        for (size_t i = 0; i < n; ++i) {
+            ServerEntry &e = s->active[i];
+            if (e.fam != FAM_F64) continue;
+            if ((st = residual_now(e.g, FAM_F64, e.pp, p->residual_margin, &rel64[i])) != FLD_OK) return st;
+            s->launches += 3;
+        }
         // -- each grid's own decisions (same as fld_solve)
         std::vector<std::pair<size_t, std::pair<fld_status, double>>> retire;
         for (size_t i = 0; i < n; ++i) {
             ServerEntry &e = s->active[i];
             fld_grid_s *g = e.g;
-            const double rel = rel_from_sums(g, p->residual_margin, out[2 * i], out[2 * i + 1]);
+            double rel = e.fam == FAM_F64 ? rel64[i] : rel_from_sums(g, p->residual_margin, out[2 * i], out[2 * i + 1]);
             e.res.rel_residual = rel;
             ++e.res.checks;
             const Action a = (e.warm > 0 && e.res.iterations == e.warm) ? e.ctl.restart(rel)
                                                                          : e.ctl.next(rel, e.pp.omega);
             switch (a) {
-            case ACT_CONVERGED: retire.push_back({i, {FLD_OK, rel}}); break;
+            case ACT_CONVERGED:
+                if (p->precision == FLD_PREC_MIXED && p->fp64_verify && e.fam == FAM_FF) {
+                    // the stop test in FP64, as in fld_solve
+                    double r64 = 0.0;
+                    if ((st = fp64_check(g, p, e.pp, &r64)) != FLD_OK) return st;
+                    s->launches += 5;
+                    ++e.res.checks;
+                    e.res.rel_residual_single = rel;
+                    e.res.rel_residual = rel = r64;
+                    e.fam = FAM_F64;
+                    e.ctl.enter_fp64(r64);
+                    if (r64 <= p->tol) retire.push_back({i, {FLD_OK, rel}});
+                } else {
+                    retire.push_back({i, {FLD_OK, rel}});
+                }
+                break;
             case ACT_DIVERGED: retire.push_back({i, {FLD_ERR_DIVERGED, rel}}); break;
             case ACT_STALLED: retire.push_back({i, {FLD_ERR_NOT_CONVERGED, rel}}); break;
             case ACT_SAVE:
@@ -1683,6 +1774,7 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
                 if ((st = snapshot(g, e.snap_fam, false)) != FLD_OK) return st;
                 e.fam = e.snap_fam;
                 e.ctl.fam = e.fam;
+                set_valid(g, e.fam);
                 g->lo_live = e.snap_lo;
                 e.pp.omega = 1.0 + 0.97 * (e.pp.omega - 1.0);
                 break;
@@ -1699,6 +1791,7 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
         }
         for (size_t r = retire.size(); r-- > 0;) {
             ServerEntry &e = s->active[retire[r].first];
+            if (e.fam == FAM_F64 && (st = sync_family(e.g, FAM_FF)) != FLD_OK) return st;   // as fld_solve
             e.res.kernels = s->launches;
             server_retire(s, retire[r].first, retire[r].second.first, retire[r].second.second);
         }

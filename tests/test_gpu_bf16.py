@@ -16,7 +16,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("no CUDA device", allow_module_level=True)
 
-from test_gpu_parity import INNER, gpu_grid, random_case, rel_max  # noqa: E402
+from test_gpu_parity import INNER, gpu_grid, random_case, rel_el, rel_l2  # noqa: E402
 
 
 @pytest.mark.parametrize("shape", [(16, 12, 20), (9, 11, 13)])
@@ -39,8 +39,10 @@ def test_one_iteration_bf16_matches_oracle(shape, precision, limiter):
                        medium_bf16=1)
         g.iterate(p, 1)
         phi, D = g.get_state()
-    assert rel_max(phi, ref.phi) <= 3e-6
-    assert rel_max(D, ref.D) <= 3e-5
+    e_phi, e_D = rel_el(phi, ref.phi, also=phi0), rel_el(D, ref.D, also=D0)
+    print(f"bf16 {precision} {limiter} {shape}: per-element phi {e_phi:.2e} D {e_D:.2e}")
+    assert e_phi <= 3e-6
+    assert e_D <= 3e-5
 
 
 def test_residual_uses_the_rounded_medium_and_switches_back():
@@ -81,15 +83,18 @@ def test_cloud_fixed_point_bf16_mixed_and_fp64():
         sols[bf] = ref.phi[INNER].copy()
     quant = np.linalg.norm(sols[True] - sols[False]) / np.linalg.norm(sols[False])
     assert 1e-5 < quant < 2e-2          # rounding effect: measured, above the parity bound
-    for precision, tol, bound in (("mixed", 1e-7, 1e-5), ("fp64", 1e-10, 1e-8)):
+    for precision, tol, bound, bound_el in (("mixed", 1e-6, 1e-5, 1e-4), ("fp64", 1e-10, 1e-8, 1e-7)):
         with gpu_grid(sig, alb, q, h) as g:
             p = fld.params(limiter="lp", precision=precision, tol=tol, omega=1.7, local_iters=2, check_every=32,
                            max_iters=400000, medium_bf16=1)
             r = g.solve(p)
             assert r.status == fld.FLD_OK, r.as_dict()
+            assert r.rel_residual <= tol
             phi, _ = g.get_state()
-        err = np.linalg.norm(phi[INNER] - sols[True]) / np.linalg.norm(sols[True])
+        err, err_el = rel_l2(phi[INNER], sols[True]), rel_el(phi[INNER], sols[True], floor=1e-3)
+        print(f"bf16 fixed point {precision}: rel L2 {err:.2e} per-element {err_el:.2e}")
         assert err <= bound, (precision, err)
+        assert err_el <= bound_el, (precision, err_el)
 
 
 def test_batch_with_bf16_medium_equals_solo():

@@ -39,10 +39,12 @@ def test_converged_solution_satisfies_the_fp64_discrete_equation(c2):
     ref = oracle.make_problem(case.sigma_t, case.alb, j.astype(np.float64), case.h, limiter="lp")
     ref.phi, ref.D = phi, D
     rel64, _, _ = oracle.residual(ref)
-    print(f"GPU rel residual {r.rel_residual:.3e}, FP64 oracle residual of the GPU phi {rel64:.3e}")
-    # the GPU solves Eq. 31 with single-precision D; in FP64 the same phi
-    # leaves a residual of the order of the D rounding
-    assert rel64 <= 2e-6
+    print(f"GPU rel residual {r.rel_residual:.3e} (single-precision D {r.rel_residual_single:.3e}, "
+          f"FP64 sweeps {r.iterations_fp64}), FP64 oracle residual of the GPU phi {rel64:.3e}")
+    # the stop test is taken in FP64 (fp64_verify): the returned phi satisfies
+    # the FP64 discrete equation to the tolerance, as the oracle evaluates it
+    assert r.rel_residual <= 1e-6
+    assert rel64 <= 1e-6 * (1 + 1e-9)
     inner = phi[INNER]
     assert np.all(inner > 0)
     E = oracle.flux_magnitude(ref)
@@ -73,8 +75,11 @@ def test_one_iteration_parity_at_full_size(c2):
     g.set_state(phi0, D0)
     g.iterate(fld.params(limiter="lp", precision="mixed", omega=1.93, local_iters=2, warm_start=1), 1)
     phi, D = g.get_state()
-    assert np.abs(phi - ref.phi).max() <= 1e-6 * np.abs(ref.phi).max()
-    assert np.abs(D - ref.D).max() <= 3e-5 * np.abs(ref.D).max()
+    from test_gpu_parity import rel_el
+    e_phi, e_D = rel_el(phi, ref.phi, also=phi0), rel_el(D, ref.D, also=D0)
+    print(f"128^3 one iteration: per-element phi {e_phi:.2e} D {e_D:.2e}")
+    assert e_phi <= 1e-6
+    assert e_D <= 3e-5
 
 
 def test_render_at_full_size_matches_oracle_pixels(c2):

@@ -50,6 +50,29 @@ def rel_max(a, b):
     return np.abs(a - b).max() / np.abs(b).max()
 
 
+# Per-element comparisons.  Each element is compared relative to its own
+# magnitude, floored at FLOOR times the field's largest magnitude, so dim
+# cells (deep shadow, next to vacuum) are held to the same relative accuracy
+# as bright ones down to 1e-4 of the maximum (and below that, in absolute
+# terms, to tol * 1e-4 of it).  For a single update phi' = phi_p + omega delta
+# the rounding is relative to the operands, so `also` (the state before the
+# update) enters the scale too: where SOR takes a bright cell close to zero,
+# the cancellation is judged against the value it cancelled.
+FLOOR = 1e-4
+
+
+def rel_el(got, ref, floor=FLOOR, also=None):
+    scale = np.abs(ref)
+    if also is not None:
+        scale = np.maximum(scale, np.abs(also))
+    scale = np.maximum(scale, floor * np.abs(ref).max())
+    return float((np.abs(got - ref) / scale).max())
+
+
+def rel_l2(got, ref):
+    return float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+
+
 # ---------------------------------------------------------------------------
 # one iteration from the same state
 # ---------------------------------------------------------------------------
@@ -71,8 +94,10 @@ def test_one_iteration_fp64_matches_oracle(limiter, local):
         p = fld.params(limiter=limiter, precision="fp64", omega=1.4, local_iters=local, warm_start=1)
         g.iterate(p, 1)
         phi, D = g.get_state()
-    assert rel_max(phi, ref.phi) <= 1e-12
-    assert rel_max(D, ref.D) <= 1e-12
+    e_phi, e_D = rel_el(phi, ref.phi, also=phi0), rel_el(D, ref.D, also=D0)
+    print(f"fp64 one iteration {limiter} k={local}: per-element phi {e_phi:.2e} D {e_D:.2e}")
+    assert e_phi <= 1e-12
+    assert e_D <= 1e-12
 
 
 @pytest.mark.parametrize("precision,tol", [("fp32", 3e-6), ("mixed", 3e-6), ("pair", 3e-6)])
@@ -92,8 +117,10 @@ def test_one_iteration_single_matches_oracle(precision, tol, limiter):
         p = fld.params(limiter=limiter, precision=precision, omega=1.5, local_iters=2, warm_start=1)
         g.iterate(p, 1)
         phi, D = g.get_state()
-    assert rel_max(phi, ref.phi) <= tol
-    assert rel_max(D, ref.D) <= 3e-5
+    e_phi, e_D = rel_el(phi, ref.phi, also=phi0), rel_el(D, ref.D, also=D0)
+    print(f"{precision} one iteration {limiter}: per-element phi {e_phi:.2e} D {e_D:.2e}")
+    assert e_phi <= tol
+    assert e_D <= 3e-5
 
 
 # ---------------------------------------------------------------------------
@@ -126,7 +153,9 @@ def test_bake_column_scan_matches_oracle():
         g.set_medium(case.sigma_t, case.alb)
         g.bake_directional((0, 0, -1), 1.0)
         got = g.get_source()
-    assert np.abs(got - want).max() <= 2e-6 * np.abs(want).max()
+    e = rel_el(got, want)
+    print(f"column scan per-element {e:.2e}")
+    assert e <= 2e-6
 
 
 @pytest.mark.parametrize("direction", [(0.3, -0.2, -1.0), (1.0, 0.0, 0.0), (-0.5, 0.7, 0.2)])
@@ -138,7 +167,9 @@ def test_bake_march_matches_oracle(direction):
         g.set_medium(sig, alb)
         g.bake_directional(direction, 2.0)
         got = g.get_source()
-    assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
+    e = rel_el(got, want)
+    print(f"march {direction} per-element {e:.2e}")
+    assert e <= 1e-4
 
 
 def test_bake_point_and_accumulate_match_oracle():
@@ -151,7 +182,9 @@ def test_bake_point_and_accumulate_match_oracle():
         g.bake_point(pos, 3.0)
         g.bake_directional((0, 0, -1), 1.0, accumulate=1)
         got = g.get_source()
-    assert np.abs(got - want).max() <= 1e-4 * np.abs(want).max()
+    e = rel_el(got, want)
+    print(f"point + column per-element {e:.2e}")
+    assert e <= 1e-4
 
 
 # ---------------------------------------------------------------------------
@@ -173,15 +206,28 @@ def test_cloud_fixed_point_mixed_and_fp64(shape):
     h = 1.0 / max(shape)
     q = oracle.bake_directional(sig, alb, h, (0, 0, -1), 1.0).astype(np.float32)
     ref = _oracle_fixed_point(sig, alb, q, h)
-    for precision, tol, bound in (("mixed", 1e-7, 1e-5), ("fp64", 1e-10, 1e-8)):
+    # mixed precision at the solve target 1e-6 (the oracle's own iterate at
+    # 1e-6 is within 4.3e-7 of its fixed point in L2, 5e-5 per element);
+    # FP64 to 1e-10
+    for precision, tol, bound, bound_el in (("mixed", 1e-6, 1e-5, 1e-4), ("fp64", 1e-10, 1e-8, 1e-7)):
         with gpu_grid(sig, alb, q, h) as g:
             p = fld.params(limiter="lp", precision=precision, tol=tol, omega=1.7, local_iters=2,
                            check_every=32, max_iters=400000)
             r = g.solve(p)
             assert r.status == fld.FLD_OK, r.as_dict()
+            assert r.rel_residual <= tol
             phi, _ = g.get_state()
-        err = np.linalg.norm(phi[INNER] - ref.phi[INNER]) / np.linalg.norm(ref.phi[INNER])
+        err, err_el = rel_l2(phi[INNER], ref.phi[INNER]), rel_el(phi[INNER], ref.phi[INNER], floor=1e-3)
+        print(f"{shape} {precision}: rel L2 {err:.2e}, per-element {err_el:.2e}, "
+              f"fp64 sweeps {r.iterations_fp64}, residual {r.rel_residual:.2e} (single-D {r.rel_residual_single:.2e})")
         assert err <= bound, (precision, err)
+        assert err_el <= bound_el, (precision, err_el)
+        if precision == "mixed":
+            # the returned phi meets the stop test in FP64: the oracle agrees
+            ref2 = oracle_problem(sig, alb, q, h, limiter="lp", omega=1.7, local_iters=2)
+            oracle.init_state(ref2)
+            rel64, _, _ = oracle.residual(ref2, phi=phi)
+            assert rel64 <= tol * (1 + 1e-9), rel64
 
 
 def test_point_source_fp64_c1_setup():
@@ -209,7 +255,9 @@ def test_degenerate_and_ragged_sizes(shape):
         r = g.solve(fld.params(precision="mixed", tol=1e-7, omega=1.5, check_every=8, max_iters=100000))
         assert r.status == fld.FLD_OK, r.as_dict()
         phi, _ = g.get_state()
-    assert rel_max(phi[INNER], ref.phi[INNER]) <= 1e-6
+    e = rel_el(phi[INNER], ref.phi[INNER], floor=1e-3)
+    print(f"{shape}: per-element {e:.2e}")
+    assert e <= 1e-6
 
 
 def test_no_emission_stays_zero():
@@ -270,7 +318,7 @@ def test_device_pointers_through_torch():
         fld.fld_get_state(g.handle, phi, None)
         stream.synchronize()
         g.close()
-    assert rel_max(phi.cpu().numpy()[INNER], ref.phi[INNER]) <= 1e-6
+    assert rel_el(phi.cpu().numpy()[INNER], ref.phi[INNER], floor=1e-3) <= 1e-6
 
 
 def test_safeguard_backs_off_a_divergent_omega():

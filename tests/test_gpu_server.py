@@ -79,3 +79,50 @@ def test_serving_loop_runs_a_small_stream():
     assert st["requests"] == 8
     assert all(r.result.status == fld.FLD_OK for r in reqs)
     assert st["max_in_flight"] <= 4
+
+
+def test_served_results_match_the_oracle_fixed_point():
+    # each result of the continuous-batching server, not only its solo twin,
+    # against the oracle's FP64 fixed point of the same inputs (the source is
+    # the oracle's bake, rounded to float, given to both sides)
+    import oracle
+    from test_gpu_parity import rel_el, rel_l2
+    p = fld.params(limiter="lp", precision="mixed", tol=1e-6, omega=1.7, check_every=32, max_iters=200000)
+    shapes = [(16, 16, 16), (12, 20, 18), (10, 14, 12)]
+    grids, refs = [], []
+    try:
+        for a, (nz, ny, nx) in enumerate(shapes):
+            sig, alb = fld_inputs.cloud_medium(nx, seed=70 + a, albedo=0.9, ny=ny, nz=nz)
+            h = 1.0 / max(nx, ny, nz)
+            q = oracle.bake_directional(sig, alb, h, (0.1, 0.2, -1.0), 1.0).astype(np.float32)
+            ref = oracle.make_problem(sig, alb, q.astype(np.float64), h, limiter="lp", omega=1.7, local_iters=2)
+            oracle.init_state(ref)
+            _, rel, _ = oracle.solve(ref, tol=1e-11, max_iters=400000, check_every=20)
+            assert rel <= 1e-11
+            refs.append(ref.phi[1:-1, 1:-1, 1:-1].copy())
+            g = fld.Grid(nx, ny, nz, h)
+            g.set_medium(sig, alb)
+            g.set_source(q)
+            grids.append(g)
+        done = {}
+        with fld.Server(p) as srv:
+            srv.add(grids[0], 0)
+            srv.add(grids[1], 1)
+            steps = 0
+            while srv.active > 0 or len(done) < len(grids):
+                if steps == 2:
+                    srv.add(grids[2], 2)
+                for tag, r in srv.step():
+                    done[tag] = r
+                steps += 1
+                assert steps < 100000
+        for a, g in enumerate(grids):
+            r = done[a]
+            assert r.status == fld.FLD_OK and r.rel_residual <= 1e-6, r.as_dict()
+            phi = g.get_state()[0][1:-1, 1:-1, 1:-1]
+            l2, el = rel_l2(phi, refs[a]), rel_el(phi, refs[a], floor=1e-3)
+            print(f"served {shapes[a]}: rel L2 {l2:.2e} per-element {el:.2e} fp64 sweeps {r.iterations_fp64}")
+            assert l2 <= 1e-5 and el <= 1e-4
+    finally:
+        for g in grids:
+            g.close()

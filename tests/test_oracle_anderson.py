@@ -2,8 +2,10 @@
 a block of red-black sweeps (Algorithm 1) is a map G whose fixed point is the
 solution of Eq. 31, so starting each block from an affine combination of
 earlier images G(x_i) (weights summing to 1) converges to the same phi* --
-here in fewer sweeps.  The mix is written out in numpy on top of the
-oracle's own sweeps and residual; nothing here touches the GPU library."""
+here in fewer sweeps.  The mix (`oracle.solve_anderson`, numpy on top of the
+oracle's own sweeps and residual) gives the reference solutions of grids
+where plain SOR takes too long; here it is pinned against the plain solve.
+Nothing here touches the GPU library."""
 import numpy as np
 import pytest
 
@@ -23,27 +25,7 @@ def _problem(n, seed=2):
 
 
 def _anderson_solve(p, tol, sweeps_per_block=16, m=6, max_sweeps=200000):
-    """Blocks of sweeps mixed over the last m images: x = sum a_i g_i with
-    a = argmin |sum a_i f_i|, sum a_i = 1 (f_i = g_i - x_i)."""
-    x = p.phi[INNER].copy()
-    G, F = [], []
-    sweeps = 0
-    while sweeps < max_sweeps:
-        oracle.rb_iteration(p, sweeps_per_block)
-        sweeps += sweeps_per_block
-        rel = oracle.residual(p)[0]
-        if rel <= tol:
-            return sweeps, rel
-        g = p.phi[INNER].copy()
-        G.append(g)
-        F.append(g - x)
-        G, F = G[-m:], F[-m:]
-        gram = np.array([[np.vdot(a, b) for b in F] for a in F])
-        y = np.linalg.solve(gram + 1e-12 * np.trace(gram) / len(F) * np.eye(len(F)), np.ones(len(F)))
-        a = y / y.sum()
-        x = sum(ai * gi for ai, gi in zip(a, G))
-        p.phi[INNER] = x
-    return sweeps, oracle.residual(p)[0]
+    return oracle.solve_anderson(p, tol, sweeps_per_block=sweeps_per_block, m=m, max_sweeps=max_sweeps)
 
 
 def test_mixed_sweeps_reach_the_same_fixed_point_in_fewer_sweeps():
