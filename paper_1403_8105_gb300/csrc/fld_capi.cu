@@ -1298,12 +1298,36 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
         snap_lo_live = g->lo_live;
         return s2;
     };
+    const bool verify = p->precision == FLD_PREC_MIXED && p->fp64_verify;
+    // A MIXED solve whose single-precision-D residual met tol takes the stop
+    // test of Algorithm 1 in FP64; above tol it continues with FP64 sweeps.
+    auto confirm = [&]() -> fld_status {
+        if (!verify || fam == FAM_F64) {
+            outcome = FLD_OK;
+            return FLD_OK;
+        }
+        double r64 = 0.0;
+        fld_status s2 = fp64_check(g, p, pp, &r64);
+        if (s2 != FLD_OK) return s2;
+        ++res.checks;
+        res.rel_residual_single = rel;
+        rel = r64;
+        fam = FAM_F64;
+        ctl.enter_fp64(r64);
+        if (r64 <= p->tol) outcome = FLD_OK;
+        return FLD_OK;
+    };
     if ((st = residual_now(g, fam, pp, p->residual_margin, &rel)) != FLD_OK) return st;
     ++res.checks;
     Action a = ctl.first(rel);
-    if (a == ACT_CONVERGED) outcome = FLD_OK;
-    else if (a == ACT_DIVERGED) outcome = FLD_ERR_DIVERGED;
-    else if ((st = save()) != FLD_OK) return st;
+    if (a == ACT_CONVERGED) {
+        if ((st = confirm()) != FLD_OK) return st;
+        if (outcome != FLD_OK && (st = save()) != FLD_OK) return st;
+    } else if (a == ACT_DIVERGED) {
+        outcome = FLD_ERR_DIVERGED;
+    } else if ((st = save()) != FLD_OK) {
+        return st;
+    }
     const int warm = warmup_of(g, p);
     // Anderson mixing (fld_solve_params.anderson): after the warm-up, each
     // block of sweeps is one application of the fixed-point map G; the next
@@ -1319,7 +1343,6 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
         *lo = !d && g->lo_live ? g->f.phlo : nullptr;
         *p64 = d ? g->f.phi64 : nullptr;
     };
-    const bool verify = p->precision == FLD_PREC_MIXED && p->fp64_verify;
     while (outcome == FLD_ERR_NOT_CONVERGED && it < p->max_iters) {
         const int k = block_len(it, check_len(fam, p->precision, p->check_every), p->max_iters, warm);
         const bool mixing = am > 0 && it >= warm;
@@ -1352,20 +1375,8 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
         a = (warm > 0 && it == warm) ? ctl.restart(rel) : ctl.next(rel, pp.omega);
         switch (a) {
         case ACT_CONVERGED:
-            if (verify && fam == FAM_FF) {
-                // the stop test of Algorithm 1 in FP64
-                double r64 = 0.0;
-                if ((st = fp64_check(g, p, pp, &r64)) != FLD_OK) return st;
-                ++res.checks;
-                res.rel_residual_single = rel;
-                rel = r64;
-                fam = FAM_F64;
-                ctl.enter_fp64(r64);
-                have_x = false;
-                if (r64 <= p->tol) outcome = FLD_OK;
-            } else {
-                outcome = FLD_OK;
-            }
+            if ((st = confirm()) != FLD_OK) return st;
+            have_x = false;
             break;
         case ACT_DIVERGED: outcome = FLD_ERR_DIVERGED; break;
         case ACT_STALLED: stalled = true; break;
@@ -1638,7 +1649,22 @@ fld_status fld_server_add(fld_server s, fld_grid g, long long tag) {
     e.res.checks = 1;
     e.res.rel_residual = rel;
     e.own_stream = g->stream;
-    const Action a = e.ctl.first(rel);
+    Action a = e.ctl.first(rel);
+    if (a == ACT_CONVERGED && p->precision == FLD_PREC_MIXED && p->fp64_verify && e.fam != FAM_F64) {
+        // the stop test in FP64, as in fld_solve
+        double r64 = 0.0;
+        if ((st = fp64_check(g, p, e.pp, &r64)) != FLD_OK) return st;
+        ++e.res.checks;
+        e.res.rel_residual_single = rel;
+        e.res.rel_residual = rel = r64;
+        e.fam = FAM_F64;
+        e.ctl.enter_fp64(r64);
+        if (r64 <= p->tol) {
+            if ((st = sync_family(g, FAM_FF)) != FLD_OK) return st;
+        } else {
+            a = ACT_SAVE;
+        }
+    }
     if (a == ACT_SAVE) {
         if ((st = snapshot(g, e.fam, true)) != FLD_OK) return st;
         e.snap_fam = e.fam;
@@ -1748,7 +1774,7 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
                                                                          : e.ctl.next(rel, e.pp.omega);
             switch (a) {
             case ACT_CONVERGED:
-                if (p->precision == FLD_PREC_MIXED && p->fp64_verify && e.fam == FAM_FF) {
+                if (p->precision == FLD_PREC_MIXED && p->fp64_verify && e.fam != FAM_F64) {
                     // the stop test in FP64, as in fld_solve
                     double r64 = 0.0;
                     if ((st = fp64_check(g, p, e.pp, &r64)) != FLD_OK) return st;
