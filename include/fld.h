@@ -57,7 +57,10 @@ typedef enum {
     FLD_ERR_STATE = 4,         /* call order: e.g. solve before set_medium      */
     FLD_ERR_NOT_CONVERGED = 5, /* max_iters reached; result still filled        */
     FLD_ERR_DIVERGED = 6,      /* residual became NaN or infinite               */
-    FLD_ERR_NO_DEVICE = 7      /* no CUDA device / extension unusable           */
+    FLD_ERR_NO_DEVICE = 7,     /* no CUDA device / extension unusable           */
+    FLD_ERR_TIMEOUT = 8        /* a bounded wait inside a kernel gave up (a TMA
+                                  copy that never completed); the state is not
+                                  trusted, the grid stays usable                 */
 } fld_status;
 
 /* Flux limiters F(R), Table 2 of the paper, plus the CDA constant 1/3. */
@@ -187,6 +190,20 @@ typedef struct {
                              iterations, until it is at or below tol; the solve
                              then ends in FP64.  0: stop on the single-precision-D
                              residual.                                          */
+    int temporal_depth;   /* single-precision and hi/lo red-black sweeps:
+                             -1: one launch per colour pass (two unknowns per
+                             thread); 1, 2 or 4: temporally blocked launches of
+                             T iterations each (TMA-staged 3-D tiles in shared
+                             memory with a 2T-cell halo, a z-wavefront of the 2T
+                             colour passes; bit-identical to the launched passes,
+                             reading each field once per T iterations; costs a
+                             second copy of phi, D and the low word of phi);
+                             0 (default): chosen by the autotuner (see
+                             fld_tune), launched passes until a choice exists.
+                             Not in the paper.                                 */
+    int tile_y;           /* rows of the blocked tile: 0 (default) or the one
+                             tile of the depth (T = 1: 56 x 32 unknowns, T = 2:
+                             56 x 24, T = 4: 48 x 8)                           */
 } fld_solve_params;
 
 typedef struct {

@@ -22,7 +22,7 @@ from . import _build
 
 __all__ = [
     "FLD_OK", "FLD_ERR_INVALID_ARG", "FLD_ERR_OOM", "FLD_ERR_CUDA", "FLD_ERR_STATE",
-    "FLD_ERR_NOT_CONVERGED", "FLD_ERR_DIVERGED", "FLD_ERR_NO_DEVICE",
+    "FLD_ERR_NOT_CONVERGED", "FLD_ERR_DIVERGED", "FLD_ERR_NO_DEVICE", "FLD_ERR_TIMEOUT",
     "LIMITERS", "PRECISIONS", "FldError", "SolveParams", "SolveResult",
     "load", "library_path", "fld_default_params", "fld_create_grid", "fld_set_medium", "fld_set_source",
     "fld_get_source", "fld_bake_directional", "fld_bake_point", "fld_set_state", "fld_get_state",
@@ -33,7 +33,7 @@ __all__ = [
 ]
 
 FLD_OK, FLD_ERR_INVALID_ARG, FLD_ERR_OOM, FLD_ERR_CUDA, FLD_ERR_STATE = 0, 1, 2, 3, 4
-FLD_ERR_NOT_CONVERGED, FLD_ERR_DIVERGED, FLD_ERR_NO_DEVICE = 5, 6, 7
+FLD_ERR_NOT_CONVERGED, FLD_ERR_DIVERGED, FLD_ERR_NO_DEVICE, FLD_ERR_TIMEOUT = 5, 6, 7, 8
 FLD_MEM_HOST, FLD_MEM_DEVICE = 0, 1
 LIMITERS = {"cda": 0, "sum": 1, "max": 2, "kershaw": 3, "larsen": 4, "lp": 5}
 PRECISIONS = {"fp64": 0, "fp32": 1, "mixed": 2, "pair": 3}
@@ -50,7 +50,8 @@ class SolveParams(ctypes.Structure):
         ("warm_start", ctypes.c_int), ("phi0", ctypes.c_double), ("D0", ctypes.c_double),
         ("phi_b", ctypes.c_double), ("D_b", ctypes.c_double), ("warmup_iters", ctypes.c_int),
         ("medium_bf16", ctypes.c_int), ("scheme", ctypes.c_int), ("nested", ctypes.c_int),
-        ("anderson", ctypes.c_int), ("fp64_verify", ctypes.c_int),
+        ("anderson", ctypes.c_int), ("fp64_verify", ctypes.c_int), ("temporal_depth", ctypes.c_int),
+        ("tile_y", ctypes.c_int),
     ]
 
 
@@ -99,7 +100,8 @@ class FldError(RuntimeError):
 
 
 _STATUS_NAMES = {0: "FLD_OK", 1: "FLD_ERR_INVALID_ARG", 2: "FLD_ERR_OOM", 3: "FLD_ERR_CUDA",
-                 4: "FLD_ERR_STATE", 5: "FLD_ERR_NOT_CONVERGED", 6: "FLD_ERR_DIVERGED", 7: "FLD_ERR_NO_DEVICE"}
+                 4: "FLD_ERR_STATE", 5: "FLD_ERR_NOT_CONVERGED", 6: "FLD_ERR_DIVERGED", 7: "FLD_ERR_NO_DEVICE",
+                 8: "FLD_ERR_TIMEOUT"}
 
 _lib = None
 _lock = threading.Lock()

@@ -15,7 +15,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libfld_gb300.so")
-SOURCES = ["fld_kernels.cu", "fld_capi.cu", "fld_noalloc.cu", "fld_render.cu", "fld_anderson.cu"]
+SOURCES = ["fld_kernels.cu", "fld_capi.cu", "fld_noalloc.cu", "fld_render.cu", "fld_anderson.cu", "fld_tiled.cu",
+           "fld_tiled_hl.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

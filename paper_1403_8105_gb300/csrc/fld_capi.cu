@@ -10,8 +10,13 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <dlfcn.h>
+#include <stdlib.h>
+
 #include <algorithm>
 #include <chrono>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -60,12 +65,14 @@ struct GraphEntry {
     cudaGraphExec_t exec = nullptr;
     int fam = -1;
     int iters = 0;
+    long long kernels = 0;   // kernel launches one replay issues
     PassParams p{};
 };
 
 bool same_params(const PassParams &a, const PassParams &b) {
     return a.lim == b.lim && a.local_iters == b.local_iters && a.larsen_n == b.larsen_n && a.omega == b.omega &&
-           a.inv2h == b.inv2h && a.floor_ == b.floor_ && a.bf16 == b.bf16 && a.h2 == b.h2 && a.scheme == b.scheme;
+           a.inv2h == b.inv2h && a.floor_ == b.floor_ && a.bf16 == b.bf16 && a.h2 == b.h2 && a.scheme == b.scheme &&
+           a.tiled_f32 == b.tiled_f32 && a.tiled_fh == b.tiled_fh;
 }
 
 }  // namespace
@@ -100,6 +107,13 @@ struct fld_grid_s {
     AndersonBuffers anderson{};
     int anderson_slots = 0;
     int nsm = 0;
+    // temporally blocked sweeps: the other buffers of the ping-pong pair, the
+    // kernels' timeout flag and the TMA descriptors (made on first use)
+    float *alt_phi = nullptr, *alt_D = nullptr, *alt_lo = nullptr;
+    int *tiled_status = nullptr;
+    TiledMaps maps[kTiledConfigs][2];    // [config][0: input in phi/D/phlo, 1: input in alt_*]
+    bool maps_ok[kTiledConfigs] = {};
+    bool tiled_used = false;             // blocked launches since the status was last read
 };
 
 namespace {
@@ -287,7 +301,38 @@ PassParams block_params(const PassParams &pp, int it, int warm) {
 
 fld_status read_result(fld_grid_s *g, double out[2]) {
     FLD_CK(cudaMemcpyAsync(out, g->f.result, 2 * sizeof(double), cudaMemcpyDeviceToHost, g->stream));
+    int timeout = 0;
+    if (g->tiled_used)
+        FLD_CK(cudaMemcpyAsync(&timeout, g->tiled_status, sizeof(int), cudaMemcpyDeviceToHost, g->stream));
     FLD_CK(cudaStreamSynchronize(g->stream));
+    if (g->tiled_used) {
+        g->tiled_used = false;
+        if (timeout) {
+            FLD_CK(cudaMemsetAsync(g->tiled_status, 0, sizeof(int), g->stream));
+            return fail(FLD_ERR_TIMEOUT, "a blocked sweep gave up waiting for its tile copies");
+        }
+    }
+    return FLD_OK;
+}
+
+// Buffers and TMA descriptors of blocked configuration `id`.
+fld_status ensure_tiled(fld_grid_s *g, int id) {
+    if (id < 0) return FLD_OK;
+    if (!g->alt_phi) {
+        const size_t nb = sizeof(float) * (size_t)g->L.total;
+        if (cudaMalloc((void **)&g->alt_phi, nb) != cudaSuccess || cudaMalloc((void **)&g->alt_D, nb) != cudaSuccess ||
+            cudaMalloc((void **)&g->alt_lo, nb) != cudaSuccess ||
+            cudaMalloc((void **)&g->tiled_status, sizeof(int)) != cudaSuccess) {
+            (void)cudaGetLastError();
+            return fail(FLD_ERR_OOM, "cudaMalloc of the blocked sweeps' buffers failed");
+        }
+        FLD_CK(cudaMemsetAsync(g->tiled_status, 0, sizeof(int), g->stream));
+    }
+    if (!g->maps_ok[id]) {
+        FLD_CK(tiled_maps(g->L, id, g->f.phi, g->f.D, g->f.phlo, &g->maps[id][0]));
+        FLD_CK(tiled_maps(g->L, id, g->alt_phi, g->alt_D, g->alt_lo, &g->maps[id][1]));
+        g->maps_ok[id] = true;
+    }
     return FLD_OK;
 }
 
@@ -416,7 +461,8 @@ fld_status sync_family(fld_grid_s *g, Family fam) {
     return FLD_OK;
 }
 
-fld_status enqueue_iterations(fld_grid_s *g, Family fam, const PassParams &pp, int iters) {
+fld_status enqueue_iterations(fld_grid_s *g, Family fam, const PassParams &pp, int iters, long long *nk = nullptr) {
+    if (nk) *nk = 2LL * iters;
     if (pp.scheme == FLD_SCHEME_JACOBI) {
         // ping-pong between phi and its second buffer; the second buffer first
         // takes phi whole (its ghosts), and an odd count ends with a copy back
@@ -430,7 +476,34 @@ fld_status enqueue_iterations(fld_grid_s *g, Family fam, const PassParams &pp, i
         if (iters & 1) FLD_CK(cudaMemcpyAsync(a, b, bytes, cudaMemcpyDeviceToDevice, g->stream));
         return FLD_OK;
     }
-    for (int it = 0; it < iters; ++it)
+    // temporally blocked launches (an even number, ping-ponging between the
+    // grid's fields and their second copies, so the state ends where it began),
+    // the remaining iterations as launched colour passes
+    const int id = fam == FAM_F32 ? pp.tiled_f32 : fam == FAM_FH ? pp.tiled_fh : -1;
+    int done = 0;
+    if (id >= 0) {
+        if (!g->maps_ok[id]) return fail(FLD_ERR_STATE, "blocked sweeps were not prepared");
+        const int T = tiled_depth(id);
+        const int nl = (iters / T) & ~1;
+        if (nl > 0) {
+            const size_t nb = sizeof(float) * (size_t)g->L.total;
+            FLD_CK(cudaMemcpyAsync(g->alt_phi, g->f.phi, nb, cudaMemcpyDeviceToDevice, g->stream));
+            FLD_CK(cudaMemcpyAsync(g->alt_D, g->f.D, nb, cudaMemcpyDeviceToDevice, g->stream));
+            if (fam == FAM_FH) FLD_CK(cudaMemcpyAsync(g->alt_lo, g->f.phlo, nb, cudaMemcpyDeviceToDevice, g->stream));
+            for (int i = 0; i < nl; ++i) {
+                const int from_alt = i & 1;
+                float *dphi = from_alt ? g->f.phi : g->alt_phi;
+                float *dD = from_alt ? g->f.D : g->alt_D;
+                float *dlo = from_alt ? g->f.phlo : g->alt_lo;
+                FLD_CK(launch_tiled(fam, id, g->L, g->f, pp, g->maps[id][from_alt], dphi, dD, dlo, g->tiled_status,
+                                    g->nsm, g->stream));
+            }
+            done = nl * T;
+            if (nk) *nk = nl + 2LL * (iters - done);
+            g->tiled_used = true;
+        }
+    }
+    for (int it = done; it < iters; ++it)
         for (int colour = 0; colour < 2; ++colour) FLD_CK(launch_pass(fam, g->L, g->f, pp, colour, g->stream));
     return FLD_OK;
 }
@@ -445,7 +518,8 @@ fld_status run_block(fld_grid_s *g, Family fam, const PassParams &pp, int iters)
         }
         cudaGraph_t graph = nullptr;
         FLD_CK(cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal));
-        fld_status st = enqueue_iterations(g, fam, pp, iters);
+        long long nk = 0;
+        fld_status st = enqueue_iterations(g, fam, pp, iters, &nk);
         cudaError_t ce = cudaStreamEndCapture(g->stream, &graph);
         if (st != FLD_OK) {
             if (graph) cudaGraphDestroy(graph);
@@ -461,9 +535,11 @@ fld_status run_block(fld_grid_s *g, Family fam, const PassParams &pp, int iters)
         e.fam = fam;
         e.iters = iters;
         e.p = pp;
+        e.kernels = nk;
     }
     FLD_CK(cudaGraphLaunch(e.exec, g->stream));
-    g->kernels += 2LL * iters;
+    g->kernels += e.kernels;
+    if (e.p.tiled_f32 >= 0 || e.p.tiled_fh >= 0) g->tiled_used = true;
     return FLD_OK;
 }
 
@@ -499,6 +575,194 @@ void set_valid(fld_grid_s *g, Family fam) {
     g->valid_float = fam != FAM_F64;
 }
 
+// ---------------------------------------------------------------------------
+// Autotuner (not a paper item): for each grid shape, sweep family, limiter and
+// medium it times the launched colour passes against every blocked
+// configuration on the grid itself, and the residual check against one
+// iteration, and keeps
+//   * the fastest sweep launch shape (all of them give the same bits, so the
+//     choice changes the time only), and
+//   * the check interval: the smallest power of two (32 ... 1024) at which a
+//     check costs at most 2 % of the iterations between two checks.
+// Choices are kept for the process and appended to a cache file
+// (FLD_TUNE_CACHE, else fld_tune_cache.txt beside the library), so later
+// processes reuse them.  The candidates read the grid's state and write only
+// its second buffers; the state is not changed.
+// ---------------------------------------------------------------------------
+struct TuneChoice {
+    int tiled = -1;           // blocked configuration id, -1: launched passes
+    int check_every = 64;
+    double us_launched = 0.0, us_best = 0.0, us_check = 0.0;   // measured per iteration / per check
+};
+
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune;
+bool g_tune_loaded = false;
+constexpr double kCheckShare = 0.02;   // a check may cost this share of the iterations between checks
+
+std::string tune_path() {
+    const char *env = getenv("FLD_TUNE_CACHE");
+    if (env && *env) return env;
+    Dl_info info;
+    if (dladdr((void *)&fld_default_params, &info) && info.dli_fname) {
+        const std::string p = info.dli_fname;
+        const size_t k = p.find_last_of('/');
+        if (k != std::string::npos) return p.substr(0, k + 1) + "fld_tune_cache.txt";
+    }
+    return "";
+}
+
+std::string tune_key(const fld_grid_s *g, Family fam, const PassParams &pp) {
+    char b[192];
+    snprintf(b, sizeof(b), "v1 %dx%dx%d fam%d lim%d r%d bf%d sm%d", g->nx, g->ny, g->nz, (int)fam, pp.lim,
+             pp.local_iters, pp.bf16, g->nsm);
+    return b;
+}
+
+void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const std::string path = tune_path();
+    FILE *fp = path.empty() ? nullptr : fopen(path.c_str(), "r");
+    if (!fp) return;
+    char line[512];
+    while (fgets(line, sizeof(line), fp)) {
+        char *bar = strchr(line, '|');
+        if (!bar) continue;
+        *bar = 0;
+        std::string key = line;
+        while (!key.empty() && key.back() == ' ') key.pop_back();
+        TuneChoice c;
+        if (sscanf(bar + 1, "%d %d %lf %lf %lf", &c.tiled, &c.check_every, &c.us_launched, &c.us_best, &c.us_check) == 5 &&
+            c.tiled >= -1 && c.tiled < kTiledConfigs && c.check_every >= 1)
+            g_tune[key] = c;
+    }
+    fclose(fp);
+}
+
+void tune_store_locked(const std::string &key, const TuneChoice &c) {
+    g_tune[key] = c;
+    const std::string path = tune_path();
+    FILE *fp = path.empty() ? nullptr : fopen(path.c_str(), "a");
+    if (!fp) return;
+    fprintf(fp, "%s | %d %d %.4f %.4f %.4f\n", key.c_str(), c.tiled, c.check_every, c.us_launched, c.us_best,
+            c.us_check);
+    fclose(fp);
+}
+
+// Time the candidates of family fam on g (state in the family's fields).
+fld_status tune_family(fld_grid_s *g, const fld_solve_params *p, const PassParams &pp, Family fam, TuneChoice *out) {
+    for (int id = 0; id < kTiledConfigs; ++id) {
+        fld_status st = ensure_tiled(g, id);
+        if (st != FLD_OK) return st;
+        FLD_CK(tiled_prepare(fam, id, pp));
+    }
+    const size_t nb = sizeof(float) * (size_t)g->L.total;
+    FLD_CK(cudaMemcpyAsync(g->alt_phi, g->f.phi, nb, cudaMemcpyDeviceToDevice, g->stream));
+    FLD_CK(cudaMemcpyAsync(g->alt_D, g->f.D, nb, cudaMemcpyDeviceToDevice, g->stream));
+    FLD_CK(cudaMemcpyAsync(g->alt_lo, g->f.phlo, nb, cudaMemcpyDeviceToDevice, g->stream));
+    Fields fa = g->f;   // the launched passes run in place on the second buffers
+    fa.phi = g->alt_phi;
+    fa.D = g->alt_D;
+    fa.phlo = g->alt_lo;
+    const int n = 16;   // iterations per timing, a multiple of every depth
+    TuneChoice c;
+    double best = INFINITY;
+    for (int cand = -1; cand < kTiledConfigs; ++cand) {
+        double t = INFINITY;
+        for (int rep = 0; rep < 3; ++rep) {   // the first is a warm-up
+            FLD_CK(cudaEventRecord(g->evb0, g->stream));
+            if (cand < 0) {
+                for (int it = 0; it < n; ++it)
+                    for (int colour = 0; colour < 2; ++colour) FLD_CK(launch_pass(fam, g->L, fa, pp, colour, g->stream));
+            } else {
+                for (int i = 0; i < n / tiled_depth(cand); ++i)
+                    FLD_CK(launch_tiled(fam, cand, g->L, g->f, pp, g->maps[cand][0], g->alt_phi, g->alt_D, g->alt_lo,
+                                        g->tiled_status, g->nsm, g->stream));
+            }
+            FLD_CK(cudaEventRecord(g->evb1, g->stream));
+            FLD_CK(cudaEventSynchronize(g->evb1));
+            float ms = 0.0f;
+            FLD_CK(cudaEventElapsedTime(&ms, g->evb0, g->evb1));
+            if (rep > 0) t = std::min(t, 1e3 * ms / n);
+        }
+        if (cand < 0) c.us_launched = t;
+        if (t < best) {
+            best = t;
+            c.tiled = cand;
+        }
+    }
+    g->tiled_used = true;   // surface a timeout of the timed blocked launches at the next check
+    c.us_best = best;
+    // one residual check, as the solve takes it (kernels + 16-byte readback)
+    double tc = INFINITY;
+    for (int rep = 0; rep < 3; ++rep) {
+        double rel = 0.0;
+        const auto t0 = std::chrono::steady_clock::now();
+        fld_status st = residual_now(g, fam, pp, p->residual_margin, &rel);
+        if (st != FLD_OK) return st;
+        const double us = std::chrono::duration<double, std::micro>(std::chrono::steady_clock::now() - t0).count();
+        if (rep > 0) tc = std::min(tc, us);
+    }
+    c.us_check = tc;
+    int ce = 32;
+    while (ce < 1024 && tc > kCheckShare * ce * best) ce *= 2;
+    c.check_every = ce;
+    *out = c;
+    return FLD_OK;
+}
+
+// The sweep launch shape of each single-precision family (pp.tiled_f32 /
+// tiled_fh) and the check interval *ce of a solve, from the parameters or
+// the autotuner.  The state must already be initialised.
+fld_status choose_sweeps(fld_grid_s *g, const fld_solve_params *p, PassParams *pp, int *ce) {
+    pp->tiled_f32 = pp->tiled_fh = -1;
+    *ce = p->check_every > 0 ? p->check_every : 64;
+    if (p->scheme != FLD_SCHEME_RED_BLACK || p->precision == FLD_PREC_FP64) return FLD_OK;
+    fld_status st = FLD_OK;
+    if (p->temporal_depth > 0) {
+        const int id = tiled_config_of(p->temporal_depth, p->tile_y);
+        if (id < 0) return fail(FLD_ERR_INVALID_ARG, "no blocked configuration with that temporal_depth / tile_y");
+        if ((st = ensure_tiled(g, id)) != FLD_OK) return st;
+        FLD_CK(tiled_prepare(FAM_F32, id, *pp));
+        FLD_CK(tiled_prepare(FAM_FH, id, *pp));
+        pp->tiled_f32 = pp->tiled_fh = id;
+    }
+    if (p->temporal_depth != 0 && p->check_every > 0) return FLD_OK;
+    const Family fams[2] = {p->precision == FLD_PREC_PAIR ? FAM_FH : FAM_F32, FAM_FH};
+    const int nfam = p->precision == FLD_PREC_MIXED ? 2 : 1;
+    for (int k = 0; k < nfam; ++k) {
+        const Family fam = fams[k];
+        const std::string key = tune_key(g, fam, *pp);
+        TuneChoice c;
+        bool have = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            tune_load_locked();
+            auto it = g_tune.find(key);
+            if (it != g_tune.end()) {
+                c = it->second;
+                have = true;
+            }
+        }
+        if (!have) {
+            if ((st = tune_family(g, p, *pp, fam, &c)) != FLD_OK) return st;
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tune.find(key);   // another thread may have tuned it meanwhile: keep the first
+            if (it != g_tune.end()) c = it->second;
+            else tune_store_locked(key, c);
+        }
+        if (p->temporal_depth == 0) {
+            if ((st = ensure_tiled(g, c.tiled)) != FLD_OK) return st;
+            if (c.tiled >= 0) FLD_CK(tiled_prepare(fam, c.tiled, *pp));
+            if (fam == FAM_F32) pp->tiled_f32 = c.tiled;
+            else pp->tiled_fh = c.tiled;
+        }
+        if (k == 0 && p->check_every <= 0) *ce = c.check_every;
+    }
+    return FLD_OK;
+}
+
 fld_status check_params(const fld_grid_s *g, const fld_solve_params *p) {
     if (!p) return fail(FLD_ERR_INVALID_ARG, "params is NULL");
     if (p->limiter < FLD_LIM_CDA || p->limiter > FLD_LIM_LP) return fail(FLD_ERR_INVALID_ARG, "unknown limiter");
@@ -517,6 +781,9 @@ fld_status check_params(const fld_grid_s *g, const fld_solve_params *p) {
     if (p->anderson > 0 && p->scheme == FLD_SCHEME_JACOBI)
         return fail(FLD_ERR_INVALID_ARG, "Anderson mixing accelerates the red-black scheme only");
     if (p->fp64_verify != 0 && p->fp64_verify != 1) return fail(FLD_ERR_INVALID_ARG, "fp64_verify must be 0 or 1");
+    if (p->temporal_depth < -1 || p->temporal_depth == 3 || p->temporal_depth > 4)
+        return fail(FLD_ERR_INVALID_ARG, "temporal_depth must be -1, 0, 1, 2 or 4");
+    if (p->tile_y < 0) return fail(FLD_ERR_INVALID_ARG, "tile_y must be >= 0");
     if (p->scheme == FLD_SCHEME_JACOBI) {
         if (p->precision != FLD_PREC_FP32 && p->precision != FLD_PREC_FP64)
             return fail(FLD_ERR_INVALID_ARG, "the Jacobi scheme runs in FP32 or FP64 precision");
@@ -727,6 +994,8 @@ void fld_default_params(fld_solve_params *p) {
     p->warmup_iters = -1;
     p->anderson = 0;
     p->fp64_verify = 1;
+    p->temporal_depth = 0;
+    p->tile_y = 0;
 }
 
 const char *fld_status_string(fld_status s) {
@@ -764,6 +1033,7 @@ fld_status fld_create_grid(int nx, int ny, int nz, double h, void *stream, fld_g
     fld_grid_s *g = new (std::nothrow) fld_grid_s();
     if (!g) return fail(FLD_ERR_OOM, "host allocation failed");
     cudaError_t e = cudaGetDevice(&g->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&g->nsm, cudaDevAttrMultiProcessorCount, g->device);
     if (e != cudaSuccess) {
         delete g;
         return cuda_fail(e, "cudaGetDevice");
@@ -835,7 +1105,8 @@ void fld_destroy(fld_grid g) {
     if (g->ev1) cudaEventDestroy(g->ev1);
     if (g->evb0) cudaEventDestroy(g->evb0);
     if (g->evb1) cudaEventDestroy(g->evb1);
-    void *snaps[] = {g->snap_phi, g->snap_lo, g->snap_D, g->snap_phi64, g->snap_D64};
+    void *snaps[] = {g->snap_phi, g->snap_lo, g->snap_D, g->snap_phi64, g->snap_D64, g->alt_phi, g->alt_D,
+                     g->alt_lo, g->tiled_status};
     for (void *p : snaps)
         if (p) cudaFree(p);
     free_anderson(g);
@@ -1123,7 +1394,10 @@ fld_status fld_iterate(fld_grid g, const fld_solve_params *p, int iterations) {
         if ((st = init_state(g, p, fam)) != FLD_OK) return st;
     }
     if ((st = sync_family(g, fam)) != FLD_OK) return st;
-    return enqueue_iterations(g, fam, pass_params(g, p), iterations);
+    PassParams pp = pass_params(g, p);
+    int ce = 0;
+    if ((st = choose_sweeps(g, p, &pp, &ce)) != FLD_OK) return st;
+    return enqueue_iterations(g, fam, pp, iterations);
 }
 
 fld_status fld_residual(fld_grid g, const fld_solve_params *p, double *rel) {
@@ -1150,7 +1424,7 @@ fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r)
     if (st != FLD_OK) return st;
     if ((st = check_params(g, p)) != FLD_OK) return st;
     if (!(p->tol >= 0.0)) return fail(FLD_ERR_INVALID_ARG, "tol must be >= 0");
-    if (p->max_iters < 0 || p->check_every < 1) return fail(FLD_ERR_INVALID_ARG, "bad max_iters / check_every");
+    if (p->max_iters < 0 || p->check_every < 0) return fail(FLD_ERR_INVALID_ARG, "bad max_iters / check_every");
     if (p->nested > 0 && !p->warm_start && p->scheme == FLD_SCHEME_RED_BLACK) return solve_nested(g, p, r);
     return solve_core(g, p, r);
 }
@@ -1273,6 +1547,8 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
     }
     if ((st = sync_family(g, fam)) != FLD_OK) return st;
     PassParams pp = pass_params(g, p);
+    int ce = 0;   // iterations between checks
+    if ((st = choose_sweeps(g, p, &pp, &ce)) != FLD_OK) return st;
     const double sw = p->fp32_switch > 0.0 ? p->fp32_switch : 2e-5;
     res.jbar = g->jbar;
     res.omega = pp.omega;
@@ -1344,7 +1620,7 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
         *p64 = d ? g->f.phi64 : nullptr;
     };
     while (outcome == FLD_ERR_NOT_CONVERGED && it < p->max_iters) {
-        const int k = block_len(it, check_len(fam, p->precision, p->check_every), p->max_iters, warm);
+        const int k = block_len(it, check_len(fam, p->precision, ce), p->max_iters, warm);
         const bool mixing = am > 0 && it >= warm;
         if (mixing && !have_x) {
             float *hi, *lo;
@@ -1473,6 +1749,7 @@ struct ServerEntry {
     Controller ctl;
     Family fam = FAM_F32;
     PassParams pp{};
+    int ce = 64;                  // iterations between checks
     int warm = 0;                 // warm-up iterations at omega = 1
     Family snap_fam = FAM_F32;
     bool snap_lo = false;
@@ -1559,10 +1836,13 @@ fld_status fld_server_create(const fld_solve_params *p, void *stream, fld_server
         return fail(FLD_ERR_INVALID_ARG, "the server runs the FP32 / MIXED / PAIR sweeps; use fld_solve for FP64");
     if (p->anderson != 0) return fail(FLD_ERR_INVALID_ARG, "Anderson mixing runs in fld_solve only");
     if (p->limiter < FLD_LIM_CDA || p->limiter > FLD_LIM_LP) return fail(FLD_ERR_INVALID_ARG, "unknown limiter");
+    if (p->temporal_depth < -1 || p->temporal_depth == 3 || p->temporal_depth > 4 || p->tile_y < 0)
+        return fail(FLD_ERR_INVALID_ARG, "temporal_depth must be -1, 0, 1, 2 or 4 and tile_y >= 0");
+    if (p->fp64_verify != 0 && p->fp64_verify != 1) return fail(FLD_ERR_INVALID_ARG, "fp64_verify must be 0 or 1");
     if (p->limiter == FLD_LIM_LARSEN && !(p->larsen_n > 0.0)) return fail(FLD_ERR_INVALID_ARG, "larsen_n must be > 0");
     if (p->omega > 0.0 && !(p->omega < 2.0)) return fail(FLD_ERR_INVALID_ARG, "omega must lie in (0, 2)");
     if (p->local_iters > 64 || p->residual_margin < 0) return fail(FLD_ERR_INVALID_ARG, "bad local_iters / margin");
-    if (!(p->tol >= 0.0) || p->max_iters < 0 || p->check_every < 1)
+    if (!(p->tol >= 0.0) || p->max_iters < 0 || p->check_every < 0)
         return fail(FLD_ERR_INVALID_ARG, "bad tol / max_iters / check_every");
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev < 1) {
@@ -1635,6 +1915,7 @@ fld_status fld_server_add(fld_server s, fld_grid g, long long tag) {
     }
     if ((st = sync_family(g, e.fam)) != FLD_OK) return st;
     e.pp = pass_params(g, p);
+    if ((st = choose_sweeps(g, p, &e.pp, &e.ce)) != FLD_OK) return st;
     e.warm = warmup_of(g, p);
     e.ctl.precision = p->precision;
     e.ctl.tol = p->tol;
@@ -1700,7 +1981,7 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
         std::vector<int> k(n);
         for (size_t i = 0; i < n; ++i) {
             ServerEntry &e = s->active[i];
-            k[i] = block_len(e.res.iterations, check_len(e.fam, p->precision, p->check_every), p->max_iters, e.warm);
+            k[i] = block_len(e.res.iterations, check_len(e.fam, p->precision, e.ce), p->max_iters, e.warm);
             if (k[i] <= 0) continue;
             e.g->stream = s->side[i % nside];
             st = run_block(e.g, e.fam, block_params(e.pp, e.res.iterations, e.warm), k[i]);
@@ -1850,7 +2131,7 @@ fld_status fld_solve_batch(fld_grid *grids, int count, const fld_solve_params *p
         return fail(FLD_ERR_INVALID_ARG, "batched solves run the FP32 / MIXED sweeps; use fld_solve for FP64");
     if (p->anderson != 0) return fail(FLD_ERR_INVALID_ARG, "Anderson mixing runs in fld_solve only");
     if (!(p->tol >= 0.0)) return fail(FLD_ERR_INVALID_ARG, "tol must be >= 0");
-    if (p->max_iters < 0 || p->check_every < 1) return fail(FLD_ERR_INVALID_ARG, "bad max_iters / check_every");
+    if (p->max_iters < 0 || p->check_every < 0) return fail(FLD_ERR_INVALID_ARG, "bad max_iters / check_every");
     // Grids of one group should keep their per-iteration working set (24 bytes
     // per voxel: sigma', sigma_a', j, phi hi/lo, D) within L2.  Grids are taken
     // in order of size and packed greedily into groups of at most 3/4 of the

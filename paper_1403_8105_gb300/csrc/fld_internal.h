@@ -2,6 +2,7 @@
 // the GB300 FLD solver (not part of the public ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include "fld_device.cuh"
 
@@ -22,6 +23,9 @@ struct PassParams {
     int scheme = 0;  // fld_scheme: red-black SOR or Jacobi
     int bf16 = 0;    // single-precision / hi-lo sweeps read the bfloat16 medium
     double h2 = 0;   // h^2, which scales the bfloat16 sigma_a'
+    // temporally blocked configuration (fld_tiled.cu) of the FP32 and hi/lo
+    // sweeps; -1: one launch per colour pass
+    int tiled_f32 = -1, tiled_fh = -1;
 };
 
 // Device fields of one grid (padded layout unless noted).
@@ -182,6 +186,28 @@ cudaError_t launch_anderson_collect(const AndersonBuffers &b, int n, const float
 // state = x = g_slot + sum_{j != slot} a_j (g_j - g_slot).
 cudaError_t launch_anderson_mix(const AndersonBuffers &b, int n, int slot, int w, const double *a, float *hi,
                                 float *lo, double *p64, int nsm, cudaStream_t s);
+
+// Temporally blocked red-black sweeps (fld_tiled.cu).  Configuration ids
+// 0..kTiledConfigs-1 fix the temporal depth T (iterations per launch) and the
+// x-y tile; tiled_config_of(T, TY) finds one (TY <= 0: the first with that T).
+constexpr int kTiledConfigs = 3;
+struct TiledMaps {
+    CUtensorMap phi, D, lo;    // TMA descriptors of the launch's input buffers
+};
+int tiled_depth(int id);
+void tiled_shape(int id, int *T, int *tx, int *ty);
+int tiled_config_of(int T, int TY);
+// Set up the kernel instance of (fam, id, p) (shared-memory attribute,
+// occupancy); call outside stream capture before launching it.
+cudaError_t tiled_prepare(Family fam, int id, const PassParams &p);
+// Tensor maps of one buffer set (lo may be null) for configuration id.
+cudaError_t tiled_maps(const Layout &L, int id, float *phi, float *D, float *lo, TiledMaps *out);
+// T iterations (FAM_F32 or FAM_FH) from the buffers described by src into
+// dphi / dD / dlo, whose ghosts must already hold the ghost values.  *status
+// is set to 1 if a bounded wait gave up.
+cudaError_t launch_tiled(Family fam, int id, const Layout &L, const Fields &f, const PassParams &p,
+                         const TiledMaps &src, float *dphi, float *dD, float *dlo, int *status, int nsm,
+                         cudaStream_t s);
 
 // Sets the thread-local text that fld_last_error() returns.
 void set_error_text(const char *msg);

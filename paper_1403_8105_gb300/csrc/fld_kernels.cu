@@ -19,12 +19,15 @@
 
 #include <type_traits>
 
+#include "fld_cell.cuh"
 #include "fld_device.cuh"
 #include "fld_internal.h"
 
 namespace fld {
 
 namespace {
+
+using namespace cell;
 
 constexpr int kRedThreads = 256;
 
@@ -252,34 +255,6 @@ __device__ __forceinline__ bool pass_cell(const Layout &L, int c, int t, int J, 
     return true;
 }
 
-// Limiter (Table 2) with approximate reciprocals, for the bulk
-// single-precision sweeps, whose accuracy is bounded by phi stored in float;
-// the correction sweeps and the residual use the correctly rounded forms.
-// The sums below are written with explicit round-to-nearest adds: an
-// operand here can be a product (the approximate quotients are x * rcp(y)),
-// and a plain `+` could then be contracted into an FMA in one kernel and not
-// in another, so kernels sharing this code would differ in the last bit.
-__device__ __forceinline__ float limiter_fast(int kind, float larsen_n, float R) {
-    switch (kind) {
-    case LIM_CDA: return 1.0f / 3.0f;
-    case LIM_SUM: return __fdividef(1.0f, __fadd_rn(3.0f, R));
-    case LIM_MAX: return __fdividef(1.0f, fmaxf(3.0f, R));
-    case LIM_KERSHAW: return __fdividef(2.0f, __fadd_rn(3.0f, hypotf(3.0f, 2.0f * R)));
-    case LIM_LARSEN: {
-        const float m = fmaxf(3.0f, R), s = fminf(3.0f, R);
-        return __fdividef(1.0f, m * __powf(__fadd_rn(1.0f, __powf(__fdividef(s, m), larsen_n)),
-                                           __fdividef(1.0f, larsen_n)));
-    }
-    default: {
-        if (R < 1.0f) return lp_series_f(R);
-        const float r = __fdividef(1.0f, R);
-        // 2e/(1-e), e = exp(-2R), is below 3.4e-8 of (1 - 1/R) once R > 9
-        const float tail = R < 9.0f ? __fdividef(2.0f, __fsub_rn(__expf(2.0f * R), 1.0f)) : 0.0f;
-        return r * __fadd_rn(__fsub_rn(1.0f, r), tail);
-    }
-    }
-}
-
 // Terms of the residual-form update that do not depend on D_p, shared by the
 // sweep and the residual kernel so both evaluate the same discrete equation
 // bit for bit:  A = sum_s d_s,  B = sum_s D_s d_s,  C = sum_s D_s,
@@ -328,41 +303,6 @@ __device__ __forceinline__ float ff_den(const FFTerms &t, float ah, float Dp) {
     return __fadd_rn(__fadd_rn(ah, 3.0f * Dp), 0.5f * t.C);
 }
 
-// Arithmetic of one FP32 point update from its gathered values: the
-// neighbours' phi and D, its own phi and medium; returns the new phi and D.
-template <int LIM, int ROUNDS>
-__device__ __forceinline__ void cell_f32(float p0, const float ps[6], const float Ds[6], float s_, float ah, float jj,
-                                         int lim_rt, float larsen_n, float omega, float inv2h, float floor_,
-                                         int rounds_rt, float &phi_new, float &D_new) {
-    const int lim = LIM >= 0 ? LIM : lim_rt;
-    const int local_iters = ROUNDS > 0 ? ROUNDS : rounds_rt;
-    const float gx = ps[1] - ps[0], gy = ps[3] - ps[2], gz = ps[5] - ps[4];
-    const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-    const float g = g2 > 0.0f ? g2 * rsqrtf(g2) * inv2h : 0.0f;     // |grad phi| (Eq. 34)
-    const float gmax = fmaxf(g, floor_);
-    const float inv_sp = __fdividef(1.0f, s_);
-    float A = 0.0f, B = 0.0f, C = 0.0f;
-#pragma unroll
-    for (int s = 0; s < 6; ++s) {
-        const float d = ps[s] - p0;
-        A += d;
-        B = fmaf(Ds[s], d, B);
-        C += Ds[s];
-    }
-    const float base = fmaf(0.5f, B, fmaf(-ah, p0, jj));
-    const float den0 = fmaf(0.5f, C, ah);
-    float delta = 0.0f, Dp = 0.0f;
-#pragma unroll
-    for (int r = 0; r < (ROUNDS > 0 ? ROUNDS : 64); ++r) {
-        if (ROUNDS == 0 && r >= local_iters) break;
-        const float R = __fdividef(gmax, fmaxf(s_ * __fadd_rn(p0, delta), floor_));     // Eq. 35
-        Dp = limiter_fast(lim, larsen_n, R) * inv_sp;                          // Eq. 33
-        delta = __fdividef(fmaf(0.5f * Dp, A, base), fmaf(3.0f, Dp, den0));   // Eq. 32
-    }
-    phi_new = fmaf(omega, delta, p0);                                          // Eq. 36
-    D_new = Dp;
-}
-
 // Two adjacent unknowns t, t+1 (t even) of one colour in row (J, K) per
 // thread: in the colour-split layout they are one aligned float2 of every
 // field, their x-neighbours three consecutive elements of the other colour's
@@ -407,17 +347,6 @@ __device__ __forceinline__ void gather_pair(const float *f, const Pair &q, float
     v0[2] = ym.x; v0[3] = yp.x; v0[4] = zm.x; v0[5] = zp.x;
     v1[2] = ym.y; v1[3] = yp.y; v1[4] = zm.y; v1[5] = zp.y;
 }
-
-// Programmatic dependent launch (PTX griddepcontrol): a pass lets the next
-// grid in its stream be scheduled as soon as all of its own CTAs are running,
-// and waits for the preceding grid to complete (with its writes visible)
-// before it reads phi, phi_lo or D.  The medium (sigma', sigma_a' h^2, j h^2)
-// is written only by earlier, fully completed kernels and is loaded before
-// the wait.  Without the launch attribute both instructions are no-ops.
-__device__ __forceinline__ void pdl_launch_dependents() {
-    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 
 // sigma' and sigma_a' h^2 of the two cells of a pair: the single-precision
 // fields, or the bfloat16 copies (one 32-bit load each; the first cell is the
@@ -489,49 +418,8 @@ __global__ void __launch_bounds__(256, 4) k_pass2_f32(Layout L, const float *__r
                                            blockIdx.y * blockDim.y + threadIdx.y + 1, blockIdx.z + 1);
 }
 
-// Middle pass: phi kept as a hi/lo pair (no storage floor) but the update
-// summed in plain FP32 with the approximate D of the bulk sweeps -- about the
-// cost of the FP32 pass, reaching residuals a few times above the
-// float-float pass's.  cell_fh is the arithmetic of one point, tile_fh that
-// of a pair of unknowns; k_pass2_fh launches it.
-template <int LIM, int ROUNDS>
-__device__ __forceinline__ void cell_fh(float p0, float p0lo, const float ps[6], const float ls[6],
-                                        const float Ds[6], float s_, float ah, float jj, int lim_rt, float larsen_n,
-                                        float omega, float inv2h, float floor_, int rounds_rt, float &hi_new,
-                                        float &lo_new, float &D_new) {
-    const int lim = LIM >= 0 ? LIM : lim_rt;
-    const int local_iters = ROUNDS > 0 ? ROUNDS : rounds_rt;
-    float d[6];
-#pragma unroll
-    for (int s = 0; s < 6; ++s) d[s] = (ps[s] - p0) + (ls[s] - p0lo);   // phi_s - phi_p
-    const float gx = d[1] - d[0], gy = d[3] - d[2], gz = d[5] - d[4];
-    const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-    const float g = g2 > 0.0f ? g2 * rsqrtf(g2) * inv2h : 0.0f;
-    const float gmax = fmaxf(g, floor_);
-    const float inv_sp = __fdividef(1.0f, s_);
-    float A = 0.0f, B = 0.0f, C = 0.0f;
-#pragma unroll
-    for (int s = 0; s < 6; ++s) {
-        A += d[s];
-        B = fmaf(Ds[s], d[s], B);
-        C += Ds[s];
-    }
-    const float base = fmaf(0.5f, B, fmaf(-ah, p0, fmaf(-ah, p0lo, jj)));
-    const float den0 = fmaf(0.5f, C, ah);
-    float delta = 0.0f, Dp = 0.0f;
-#pragma unroll
-    for (int r = 0; r < (ROUNDS > 0 ? ROUNDS : 64); ++r) {
-        if (ROUNDS == 0 && r >= local_iters) break;
-        const float R = __fdividef(gmax, fmaxf(s_ * __fadd_rn(p0, delta), floor_));
-        Dp = limiter_fast(lim, larsen_n, R) * inv_sp;
-        delta = __fdividef(fmaf(0.5f * Dp, A, base), fmaf(3.0f, Dp, den0));
-    }
-    const ff nw = ff_add_f(ff{p0, p0lo}, __fmul_rn(omega, delta));
-    hi_new = nw.hi;
-    lo_new = nw.lo;
-    D_new = Dp;
-}
-
+// Middle pass (phi as a hi/lo pair, FP32-summed update, cell::cell_fh):
+// tile_fh is the arithmetic of a pair of unknowns; k_pass2_fh launches it.
 template <int LIM, int ROUNDS, bool BF>
 __device__ __forceinline__ void tile_fh(const Layout &L, const float *__restrict__ sp,
                                         const float *__restrict__ ah2, const float *__restrict__ jh2,
