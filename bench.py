@@ -98,7 +98,9 @@ def parse_args():
                     help="c3 workload: edge of the same-recipe solves compared with the FP64 oracle's fixed point")
     ap.add_argument("--scenes", default="nebulae,manix,explosion", help="pipeline workload: scenes")
     ap.add_argument("--factor", type=int, default=4, help="pipeline workload: coarsening of the phi grid")
-    ap.add_argument("--workload", choices=["cloud", "batch", "serve", "c3", "pipeline"], default="cloud",
+    ap.add_argument("--iters", type=int, default=64, help="sweeps workload: iterations timed per configuration")
+    ap.add_argument("--sweep-n", default="128,256", help="sweeps workload: grid edges (the C2 medium tiled)")
+    ap.add_argument("--workload", choices=["cloud", "batch", "serve", "c3", "pipeline", "sweeps"], default="cloud",
                     help="cloud: the 128^3 solve (default); batch: independent solves of uneven size, "
                          "batched in shared launches vs one after another")
     ap.add_argument("--count", type=int, default=16, help="batch workload: number of solves")
@@ -1063,6 +1065,61 @@ def run_pipeline(args):
     print(json.dumps(line), flush=True)
 
 
+def run_sweeps(args):
+    """Every sweep family (single precision, hi/lo, float-float) in every
+    launch shape the library offers (launched colour passes; blocked launches
+    of T = 1, 2, 4 iterations) on the C2 cloud medium tiled to each edge of
+    --sweep-n: CUDA-event time per iteration over --iters iterations after a
+    warm-up, voxel-updates/s, and the algorithmic bytes (28 per update) over
+    that time against the measured HBM peak."""
+    import numpy as np
+    import torch
+
+    import paper_1403_8105_gb300 as fld
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    peaks = measured_peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    base_sig, base_alb = workload_inputs(128, seed=0)
+    out = {}
+    for n in (int(x) for x in args.sweep_n.split(",")):
+        rep = max(1, n // 128)
+        sig = np.tile(base_sig, (rep,) * 3)[:n, :n, :n].copy()
+        alb = np.tile(base_alb, (rep,) * 3)[:n, :n, :n].copy()
+        stream = torch.cuda.Stream(device=dev)
+        g = fld.Grid(n, n, n, 1.0 / n, stream=stream.cuda_stream)
+        try:
+            g.set_medium(sig, alb)
+            g.bake_directional((0.0, 0.0, -1.0), 1.0)
+            with torch.cuda.stream(stream):
+                # a state 512 sweeps into the solve
+                g.solve(fld.params(precision="fp32", tol=0.0, max_iters=512, check_every=256, temporal_depth=-1),
+                        check=False)
+                for fam, prec in (("fp32", "fp32"), ("fh", "pair"), ("ff", "mixed")):
+                    shapes = [(-1, 2)] + ([(-1, 4), (1, 0), (2, 0), (4, 0)] if fam != "ff" else [])
+                    for depth, cells in shapes:
+                        p = fld.params(precision=prec, warm_start=1, temporal_depth=depth, omega=1.9,
+                                       cells_per_thread=cells if depth < 0 else 0)
+                        g.iterate(p, args.iters)
+                        stream.synchronize()
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        g.iterate(p, args.iters)
+                        e1.record(stream)
+                        e1.synchronize()
+                        us = 1e3 * e0.elapsed_time(e1) / args.iters
+                        ach = 28.0 * n ** 3 / (us * 1e-6) / 1e9
+                        name = f"launched, {cells} unknowns per thread" if depth < 0 else f"blocked T={depth}"
+                        out[f"{n} {fam} {name}"] = {
+                            "us_per_iteration": round(us, 3), "voxel_updates_per_s": n ** 3 / (us * 1e-6),
+                            "algorithmic_GBps": round(ach, 1), "frac_of_measured_peak": round(ach / peak, 4)}
+        finally:
+            g.close()
+    print(json.dumps({"workload": "sweeps", "peak_gbs": peak, "bytes_per_update": 28, "results": out}), flush=True)
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -1075,6 +1132,8 @@ def main():
         run_c3(args)
     elif args.workload == "pipeline":
         run_pipeline(args)
+    elif args.workload == "sweeps":
+        run_sweeps(args)
     else:
         run_gpu(args)
 

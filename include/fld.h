@@ -117,7 +117,10 @@ typedef struct {
                              fixed point is the same.                                */
     double tol;           /* stop when Rbar / jbar <= tol (Algorithm 1: 1e-6)        */
     int max_iters;        /* iteration cap (one iteration = red + black pass)        */
-    int check_every;      /* iterations between residual evaluations, >= 1           */
+    int check_every;      /* iterations between residual evaluations, >= 1; 0: the
+                             autotuner's choice (the smallest power of two from
+                             32 to 1024 at which one check costs at most 2 % of
+                             the iterations between two checks)                */
     double sigma_eps;     /* extinction floor; <= 0 selects 1e-3 / L, L the largest
                              grid extent (Sec. 5)                                    */
     double eps;           /* epsilon of Eq. 35; <= 0 selects 1e-20                   */
@@ -198,12 +201,24 @@ typedef struct {
                              colour passes; bit-identical to the launched passes,
                              reading each field once per T iterations; costs a
                              second copy of phi, D and the low word of phi);
-                             0 (default): chosen by the autotuner (see
-                             fld_tune), launched passes until a choice exists.
+                             0 (default): chosen per grid shape, sweep family,
+                             limiter and medium by the library's autotuner,
+                             which times the launched passes (2 and 4 unknowns
+                             per thread) and every blocked configuration on the
+                             grid itself the first time that combination is
+                             solved, keeps the fastest for the process and
+                             appends it to a cache file (FLD_TUNE_CACHE, else
+                             fld_tune_cache.txt beside the library).  The
+                             choice changes the time only, not the result.
                              Not in the paper.                                 */
     int tile_y;           /* rows of the blocked tile: 0 (default) or the one
                              tile of the depth (T = 1: 56 x 32 unknowns, T = 2:
                              56 x 24, T = 4: 48 x 8)                           */
+    int cells_per_thread; /* launched passes (temporal_depth -1): 2 unknowns
+                             per thread (64-bit loads) or 4 (128-bit loads of
+                             every own field and neighbour row; same bits);
+                             0 (default): 2, or the autotuner's choice when
+                             temporal_depth is 0                               */
 } fld_solve_params;
 
 typedef struct {

@@ -72,7 +72,7 @@ struct GraphEntry {
 bool same_params(const PassParams &a, const PassParams &b) {
     return a.lim == b.lim && a.local_iters == b.local_iters && a.larsen_n == b.larsen_n && a.omega == b.omega &&
            a.inv2h == b.inv2h && a.floor_ == b.floor_ && a.bf16 == b.bf16 && a.h2 == b.h2 && a.scheme == b.scheme &&
-           a.tiled_f32 == b.tiled_f32 && a.tiled_fh == b.tiled_fh;
+           a.tiled_f32 == b.tiled_f32 && a.tiled_fh == b.tiled_fh && a.quad_f32 == b.quad_f32 && a.quad_fh == b.quad_fh;
 }
 
 }  // namespace
@@ -590,7 +590,7 @@ void set_valid(fld_grid_s *g, Family fam) {
 // its second buffers; the state is not changed.
 // ---------------------------------------------------------------------------
 struct TuneChoice {
-    int tiled = -1;           // blocked configuration id, -1: launched passes
+    int tiled = -1;           // blocked configuration id; launched passes: -1 two, -2 four unknowns per thread
     int check_every = 64;
     double us_launched = 0.0, us_best = 0.0, us_check = 0.0;   // measured per iteration / per check
 };
@@ -614,7 +614,7 @@ std::string tune_path() {
 
 std::string tune_key(const fld_grid_s *g, Family fam, const PassParams &pp) {
     char b[192];
-    snprintf(b, sizeof(b), "v1 %dx%dx%d fam%d lim%d r%d bf%d sm%d", g->nx, g->ny, g->nz, (int)fam, pp.lim,
+    snprintf(b, sizeof(b), "v2 %dx%dx%d fam%d lim%d r%d bf%d sm%d", g->nx, g->ny, g->nz, (int)fam, pp.lim,
              pp.local_iters, pp.bf16, g->nsm);
     return b;
 }
@@ -634,7 +634,7 @@ void tune_load_locked() {
         while (!key.empty() && key.back() == ' ') key.pop_back();
         TuneChoice c;
         if (sscanf(bar + 1, "%d %d %lf %lf %lf", &c.tiled, &c.check_every, &c.us_launched, &c.us_best, &c.us_check) == 5 &&
-            c.tiled >= -1 && c.tiled < kTiledConfigs && c.check_every >= 1)
+            c.tiled >= -2 && c.tiled < kTiledConfigs && c.check_every >= 1)
             g_tune[key] = c;
     }
     fclose(fp);
@@ -668,13 +668,15 @@ fld_status tune_family(fld_grid_s *g, const fld_solve_params *p, const PassParam
     const int n = 16;   // iterations per timing, a multiple of every depth
     TuneChoice c;
     double best = INFINITY;
-    for (int cand = -1; cand < kTiledConfigs; ++cand) {
+    for (int cand = -2; cand < kTiledConfigs; ++cand) {
         double t = INFINITY;
+        PassParams pc = pp;
+        pc.quad_f32 = pc.quad_fh = cand == -2 ? 1 : 0;
         for (int rep = 0; rep < 3; ++rep) {   // the first is a warm-up
             FLD_CK(cudaEventRecord(g->evb0, g->stream));
             if (cand < 0) {
                 for (int it = 0; it < n; ++it)
-                    for (int colour = 0; colour < 2; ++colour) FLD_CK(launch_pass(fam, g->L, fa, pp, colour, g->stream));
+                    for (int colour = 0; colour < 2; ++colour) FLD_CK(launch_pass(fam, g->L, fa, pc, colour, g->stream));
             } else {
                 for (int i = 0; i < n / tiled_depth(cand); ++i)
                     FLD_CK(launch_tiled(fam, cand, g->L, g->f, pp, g->maps[cand][0], g->alt_phi, g->alt_D, g->alt_lo,
@@ -686,7 +688,7 @@ fld_status tune_family(fld_grid_s *g, const fld_solve_params *p, const PassParam
             FLD_CK(cudaEventElapsedTime(&ms, g->evb0, g->evb1));
             if (rep > 0) t = std::min(t, 1e3 * ms / n);
         }
-        if (cand < 0) c.us_launched = t;
+        if (cand == -1) c.us_launched = t;
         if (t < best) {
             best = t;
             c.tiled = cand;
@@ -717,6 +719,7 @@ fld_status tune_family(fld_grid_s *g, const fld_solve_params *p, const PassParam
 // the autotuner.  The state must already be initialised.
 fld_status choose_sweeps(fld_grid_s *g, const fld_solve_params *p, PassParams *pp, int *ce) {
     pp->tiled_f32 = pp->tiled_fh = -1;
+    pp->quad_f32 = pp->quad_fh = p->cells_per_thread == 4 ? 1 : 0;
     *ce = p->check_every > 0 ? p->check_every : 64;
     if (p->scheme != FLD_SCHEME_RED_BLACK || p->precision == FLD_PREC_FP64) return FLD_OK;
     fld_status st = FLD_OK;
@@ -755,8 +758,15 @@ fld_status choose_sweeps(fld_grid_s *g, const fld_solve_params *p, PassParams *p
         if (p->temporal_depth == 0) {
             if ((st = ensure_tiled(g, c.tiled)) != FLD_OK) return st;
             if (c.tiled >= 0) FLD_CK(tiled_prepare(fam, c.tiled, *pp));
-            if (fam == FAM_F32) pp->tiled_f32 = c.tiled;
-            else pp->tiled_fh = c.tiled;
+            const int shape = c.tiled >= 0 ? c.tiled : -1;
+            const int quad = c.tiled == -2 ? 1 : 0;
+            if (fam == FAM_F32) {
+                pp->tiled_f32 = shape;
+                pp->quad_f32 = quad;
+            } else {
+                pp->tiled_fh = shape;
+                pp->quad_fh = quad;
+            }
         }
         if (k == 0 && p->check_every <= 0) *ce = c.check_every;
     }
@@ -784,6 +794,8 @@ fld_status check_params(const fld_grid_s *g, const fld_solve_params *p) {
     if (p->temporal_depth < -1 || p->temporal_depth == 3 || p->temporal_depth > 4)
         return fail(FLD_ERR_INVALID_ARG, "temporal_depth must be -1, 0, 1, 2 or 4");
     if (p->tile_y < 0) return fail(FLD_ERR_INVALID_ARG, "tile_y must be >= 0");
+    if (p->cells_per_thread != 0 && p->cells_per_thread != 2 && p->cells_per_thread != 4)
+        return fail(FLD_ERR_INVALID_ARG, "cells_per_thread must be 0, 2 or 4");
     if (p->scheme == FLD_SCHEME_JACOBI) {
         if (p->precision != FLD_PREC_FP32 && p->precision != FLD_PREC_FP64)
             return fail(FLD_ERR_INVALID_ARG, "the Jacobi scheme runs in FP32 or FP64 precision");
@@ -996,6 +1008,7 @@ void fld_default_params(fld_solve_params *p) {
     p->fp64_verify = 1;
     p->temporal_depth = 0;
     p->tile_y = 0;
+    p->cells_per_thread = 0;
 }
 
 const char *fld_status_string(fld_status s) {

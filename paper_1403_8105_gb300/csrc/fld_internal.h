@@ -26,6 +26,8 @@ struct PassParams {
     // temporally blocked configuration (fld_tiled.cu) of the FP32 and hi/lo
     // sweeps; -1: one launch per colour pass
     int tiled_f32 = -1, tiled_fh = -1;
+    // launched passes: four unknowns per thread (128-bit loads) instead of two
+    int quad_f32 = 0, quad_fh = 0;
 };
 
 // Device fields of one grid (padded layout unless noted).

@@ -472,6 +472,147 @@ __global__ void __launch_bounds__(256, 4) k_pass2_fh(Layout L, const float *__re
                                           blockIdx.y * blockDim.y + threadIdx.y + 1, blockIdx.z + 1);
 }
 
+// Four adjacent unknowns t .. t+3 (t a multiple of 4) of one colour in row
+// (J, K) per thread: one aligned 128-bit load per own field and per y/z
+// neighbour row/plane, the x-neighbours five consecutive elements of the other
+// colour's row (a 128-bit load and one scalar).  Same per-cell arithmetic as
+// the pair passes (cell::cell_f32 / cell::cell_fh), so the results agree bit
+// for bit; more independent cells per thread, fewer loads and address
+// computations per cell.
+struct Quad {
+    int own, xv, ym, yp, zm, zp;              // offsets of the float4s (own colour at own, the other at the rest)
+    int n;                                    // unknowns among the four (1 .. 4)
+    bool left;                                // x-neighbours at xv-1 .. xv+3 (else xv .. xv+4)
+};
+
+__device__ __forceinline__ bool quad_cells(const Layout &L, int c, int t, int J, int K, Quad &q) {
+    const int par = (J + K + 1 + c) & 1;
+    const int I0 = 2 * t + 2 - par;                 // padded I of cell t
+    if (I0 > L.nx) return false;
+    q.n = min(4, (L.nx - I0) / 2 + 1);
+    const int row = (K * L.py + J) * L.hpx + kXoff + 1;   // element of the row's first unknown
+    const int ob = (1 - c) * L.cs;
+    q.own = c * L.cs + row + t;
+    q.left = par == 1;
+    q.xv = ob + row + t;
+    q.ym = ob + row - L.hpx + t;
+    q.yp = ob + row + L.hpx + t;
+    q.zm = ob + row - L.hpx * L.py + t;
+    q.zp = ob + row + L.hpx * L.py + t;
+    return true;
+}
+
+__device__ __forceinline__ float4 ld4(const float *__restrict__ p, int off) {
+    return *reinterpret_cast<const float4 *>(p + off);
+}
+
+__device__ __forceinline__ float f4_at(const float4 &v, int m) {
+    return m == 0 ? v.x : m == 1 ? v.y : m == 2 ? v.z : v.w;
+}
+
+// The six neighbours of the four cells of a quad from one field: v[m][s].
+__device__ __forceinline__ void gather_quad(const float *f, const Quad &q, float v[4][6]) {
+    const float4 xv = ld4(f, q.xv);
+    const float xe = q.left ? f[q.xv - 1] : f[q.xv + 4];
+    const float x5[5] = {q.left ? xe : xv.x, q.left ? xv.x : xv.y, q.left ? xv.y : xv.z, q.left ? xv.z : xv.w,
+                         q.left ? xv.w : xe};
+    const float4 ym = ld4(f, q.ym), yp = ld4(f, q.yp), zm = ld4(f, q.zm), zp = ld4(f, q.zp);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+        v[m][0] = x5[m];
+        v[m][1] = x5[m + 1];
+        v[m][2] = f4_at(ym, m);
+        v[m][3] = f4_at(yp, m);
+        v[m][4] = f4_at(zm, m);
+        v[m][5] = f4_at(zp, m);
+    }
+}
+
+template <bool BF>
+__device__ __forceinline__ void medium_quad(const float *__restrict__ sp, const float *__restrict__ ah2,
+                                            const uint16_t *__restrict__ spb, const uint16_t *__restrict__ sab,
+                                            float h2, int off, float s4[4], float a4[4]) {
+    if (BF) {
+        const uint2 us = *reinterpret_cast<const uint2 *>(spb + off);
+        const uint2 ua = *reinterpret_cast<const uint2 *>(sab + off);
+        const uint32_t w[4] = {us.x << 16, us.x & 0xFFFF0000u, us.y << 16, us.y & 0xFFFF0000u};
+        const uint32_t z[4] = {ua.x << 16, ua.x & 0xFFFF0000u, ua.y << 16, ua.y & 0xFFFF0000u};
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            s4[m] = __uint_as_float(w[m]);
+            a4[m] = __fmul_rn(__uint_as_float(z[m]), h2);
+        }
+    } else {
+        const float4 s = ld4(sp, off), a = ld4(ah2, off);
+        s4[0] = s.x; s4[1] = s.y; s4[2] = s.z; s4[3] = s.w;
+        a4[0] = a.x; a4[1] = a.y; a4[2] = a.z; a4[3] = a.w;
+    }
+}
+
+__device__ __forceinline__ void store_quad(float *p, const Quad &q, const float v[4]) {
+    if (q.n == 4) {
+        *reinterpret_cast<float4 *>(p + q.own) = make_float4(v[0], v[1], v[2], v[3]);
+    } else {
+        // the element after the last unknown is a ghost: left untouched
+        for (int m = 0; m < q.n; ++m) p[q.own + m] = v[m];
+    }
+}
+
+// Four unknowns per thread, single precision (k_pass4_f32) or hi/lo (HL,
+// k_pass4_fh).
+template <int LIM, int ROUNDS, bool BF, bool HL>
+__device__ __forceinline__ void tile4(const Layout &L, const float *__restrict__ sp, const float *__restrict__ ah2,
+                                      const float *__restrict__ jh2, const uint16_t *__restrict__ spb,
+                                      const uint16_t *__restrict__ sab, float h2, float *phi, float *phlo, float *D,
+                                      int colour, int lim_rt, float larsen_n, float omega, float inv2h, float floor_,
+                                      int rounds_rt, int t, int J, int K) {
+    if (J > L.ny) return;
+    Quad q;
+    if (!quad_cells(L, colour, t, J, K, q)) return;
+    float s4[4], a4[4];
+    medium_quad<BF>(sp, ah2, spb, sab, h2, q.own, s4, a4);
+    const float4 j4 = ld4(jh2, q.own);
+    const float jj[4] = {j4.x, j4.y, j4.z, j4.w};
+    pdl_wait();
+    float ps[4][6], Ds[4][6];
+    gather_quad(phi, q, ps);
+    gather_quad(D, q, Ds);
+    const float4 p4 = ld4(phi, q.own);
+    const float p0[4] = {p4.x, p4.y, p4.z, p4.w};
+    float pn[4], dn[4], ln[4];
+    if (HL) {
+        float ls[4][6];
+        gather_quad(phlo, q, ls);
+        const float4 l4 = ld4(phlo, q.own);
+        const float l0[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            cell_fh<LIM, ROUNDS>(p0[m], l0[m], ps[m], ls[m], Ds[m], s4[m], a4[m], jj[m], lim_rt, larsen_n, omega,
+                                 inv2h, floor_, rounds_rt, pn[m], ln[m], dn[m]);
+    } else {
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            cell_f32<LIM, ROUNDS>(p0[m], ps[m], Ds[m], s4[m], a4[m], jj[m], lim_rt, larsen_n, omega, inv2h, floor_,
+                                  rounds_rt, pn[m], dn[m]);
+    }
+    store_quad(phi, q, pn);
+    store_quad(D, q, dn);
+    if (HL) store_quad(phlo, q, ln);
+}
+
+template <int LIM, int ROUNDS, bool BF, bool HL>
+__global__ void __launch_bounds__(128) k_pass4(Layout L, const float *__restrict__ sp, const float *__restrict__ ah2,
+                                               const float *__restrict__ jh2, const uint16_t *__restrict__ spb,
+                                               const uint16_t *__restrict__ sab, float h2, float *__restrict__ phi,
+                                               float *__restrict__ phlo, float *__restrict__ D, int colour,
+                                               int lim_rt, float larsen_n, float omega, float inv2h, float floor_,
+                                               int rounds_rt) {
+    pdl_launch_dependents();
+    tile4<LIM, ROUNDS, BF, HL>(L, sp, ah2, jh2, spb, sab, h2, phi, phlo, D, colour, lim_rt, larsen_n, omega, inv2h,
+                               floor_, rounds_rt, 4 * (blockIdx.x * blockDim.x + threadIdx.x),
+                               blockIdx.y * blockDim.y + threadIdx.y + 1, blockIdx.z + 1);
+}
+
 // Float-float correction pass: phi kept as a hi/lo pair, S summed so the
 // update is accurate to the pair's precision; correctly rounded D (the same
 // function the residual kernel evaluates).
@@ -502,7 +643,14 @@ __device__ __forceinline__ void pass_ff_body(const Layout &L, const float *__res
 #pragma unroll
     for (int r = 0; r < (ROUNDS > 0 ? ROUNDS : 64); ++r) {
         if (ROUNDS == 0 && r >= local_iters) break;
-        Dp = D_of_f(gmax, s_, __fadd_rn(p0, delta), floor_, lim, larsen_n);
+        // the rounds before the last only move the point at which D_p is
+        // taken: the bulk sweeps' fast limiter serves there; the last round's
+        // D_p, which is stored, is the correctly rounded one the residual
+        // evaluates
+        const bool last = ROUNDS > 0 ? r == ROUNDS - 1 : r == local_iters - 1;
+        const float pt = __fadd_rn(p0, delta);
+        Dp = last ? D_of_f(gmax, s_, pt, floor_, lim, larsen_n)
+                  : limiter_fast(lim, larsen_n, __fdividef(gmax, fmaxf(s_ * pt, floor_))) * __fdividef(1.0f, s_);
         const ff S = ff_S(T, Dp);
         // delta is a correction: its rounding does not move the fixed point
         delta = __fdividef(__fadd_rn(S.hi, S.lo), ff_den(T, ah, Dp));
@@ -957,6 +1105,12 @@ inline dim3 pass2_grid(const Layout &L, dim3 blk) {
     return dim3((pairs + blk.x - 1) / blk.x, (L.ny + blk.y - 1) / blk.y, L.nz);
 }
 
+// four unknowns per thread (k_pass4): ceil(half / 4) threads per half row
+inline dim3 pass4_grid(const Layout &L, dim3 blk) {
+    const int quads = ((L.nx + 1) / 2 + 3) / 4;
+    return dim3((quads + blk.x - 1) / blk.x, (L.ny + blk.y - 1) / blk.y, L.nz);
+}
+
 inline dim3 vox_block() { return dim3(32, 8, 1); }
 inline dim3 vox_grid(const Layout &L) {
     return dim3((L.nx + 31) / 32, (L.ny + 7) / 8, L.nz);
@@ -1047,7 +1201,25 @@ cudaError_t launch_pass(Family fam, const Layout &L, const Fields &f, const Pass
     const dim3 grd = pass_grid(L, blk);
     const dim3 grd2 = pass2_grid(L, blk);
     switch (fam) {
-    case FAM_F32: {
+    case FAM_F32:
+    case FAM_FH:
+        if (fam == FAM_F32 ? p.quad_f32 : p.quad_fh) {
+            const dim3 blk4(32, 4, 1);
+            const dim3 grd4 = pass4_grid(L, blk4);
+            auto pick4 = [&](auto bf, auto hl) {
+                constexpr bool B = decltype(bf)::value, H = decltype(hl)::value;
+                auto k = k_pass4<-1, 0, B, H>;
+                if (p.local_iters == 2 && p.lim == LIM_LP) k = k_pass4<LIM_LP, 2, B, H>;
+                return launch_pdl(k, grd4, blk4, s, L, f.sp, f.ah2, f.jh2, f.spb, f.sab, (float)p.h2, f.phi, f.phlo,
+                                  f.D, colour, p.lim, (float)p.larsen_n, (float)p.omega, (float)p.inv2h,
+                                  (float)p.floor_, p.local_iters);
+            };
+            if (fam == FAM_FH)
+                return p.bf16 ? pick4(std::true_type{}, std::true_type{}) : pick4(std::false_type{}, std::true_type{});
+            return p.bf16 ? pick4(std::true_type{}, std::false_type{}) : pick4(std::false_type{}, std::false_type{});
+        }
+        if (fam == FAM_FH) break;
+        {
         auto pick = [&](auto bf) {
             constexpr bool B = decltype(bf)::value;
             auto k = k_pass2_f32<-1, 0, B>;
@@ -1059,7 +1231,11 @@ cudaError_t launch_pass(Family fam, const Layout &L, const Fields &f, const Pass
                               p.local_iters);
         };
         return p.bf16 ? pick(std::true_type{}) : pick(std::false_type{});
+        }
+    default:
+        break;
     }
+    switch (fam) {
     case FAM_FF: {
         auto k = k_pass_ff<-1, 0>;
         if (p.local_iters == 2 && p.lim == LIM_LP) k = k_pass_ff<LIM_LP, 2>;

@@ -232,8 +232,10 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
                     float ps[RMAX][6], Ds[RMAX][6], ls[RMAX][6], p0[RMAX], l0[RMAX];
                     int own[RMAX];
                     bool ok[RMAX];
+                    const int nk = (rg.Jr1 - rg.Jr0 - warp) / kTiledWarps + 1;   // this warp's rows (warp-uniform)
 #pragma unroll
                     for (int k = 0; k < RMAX; ++k) {              // gather
+                        if (k >= nk) break;
                         const int J = rg.Jr0 + warp + kTiledWarps * k;
                         const int pI = (c + J + K + 1) & 1;        // parity of this row's colour-c cells
                         const int I = rg.Ir0 + ((rg.Ir0 - pI) & 1) + 2 * lane;
@@ -271,6 +273,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
                     float pn[RMAX], dn[RMAX], ln[RMAX];
 #pragma unroll
                     for (int k = 0; k < RMAX; ++k) {              // compute
+                        if (k >= nk) break;
                         if (HL)
                             cell_fh<LIM, ROUNDS>(p0[k], l0[k], ps[k], ls[k], Ds[k], cur_s[k], cur_a[k], cur_j[k], lim,
                                                  a.larsen_n, a.omega, a.inv2h, a.floor_, a.rounds, pn[k], ln[k], dn[k]);
@@ -280,6 +283,7 @@ __global__ void __launch_bounds__(kTiledThreads, 1)
                     }
 #pragma unroll
                     for (int k = 0; k < RMAX; ++k) {              // store
+                        if (k >= nk) break;
                         if (!ok[k]) continue;
                         pc[own[k]] = pn[k];
                         pc[PL + own[k]] = dn[k];

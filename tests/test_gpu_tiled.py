@@ -173,3 +173,26 @@ def test_invalid_blocking_parameters_are_rejected():
             with pytest.raises(fld.FldError) as e:
                 g.solve(fld.params(**bad))
             assert e.value.status == fld.FLD_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("shape", SHAPES + [(5, 7, 127), (3, 4, 9)])
+@pytest.mark.parametrize("precision", ["fp32", "pair"])
+@pytest.mark.parametrize("bf16", [0, 1])
+def test_four_cells_per_thread_equals_two_bit_for_bit(shape, precision, bf16):
+    # the launched passes with 128-bit loads (four unknowns per thread, ragged
+    # row tails stored element by element) against the two-unknown passes
+    sig, alb, j, h = random_case(shape, 29)
+    ref = oracle.make_problem(sig, alb, j.astype(np.float64), h, omega=1.6, local_iters=2, nthreads=1)
+    oracle.init_state(ref)
+    oracle.rb_iteration(ref, 3)
+    phi0, D0 = ref.phi.copy(), ref.D.copy()
+    out = []
+    for cells in (2, 4):
+        for lim in ("lp", "kershaw"):
+            with gpu_grid(sig, alb, j, h) as g:
+                g.set_state(phi0, D0)
+                g.iterate(fld.params(limiter=lim, precision=precision, omega=1.6, local_iters=2, warm_start=1,
+                                     temporal_depth=-1, cells_per_thread=cells, medium_bf16=bf16), 5)
+                out.append(g.get_state())
+    for a, b in ((0, 2), (1, 3)):
+        assert np.array_equal(out[a][0], out[b][0]) and np.array_equal(out[a][1], out[b][1])
