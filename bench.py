@@ -105,8 +105,12 @@ def parse_args():
                          "batched in shared launches vs one after another")
     ap.add_argument("--count", type=int, default=16, help="batch workload: number of solves")
     ap.add_argument("--sizes", default="32,48,64,96", help="batch workload: edge lengths drawn from")
-    ap.add_argument("--rate", type=float, default=30.0, help="serve workload: Poisson arrival rate (req/s)")
-    ap.add_argument("--requests", type=int, default=120, help="serve workload: number of requests")
+    ap.add_argument("--rate", type=float, default=0.0, help="serve workload: Poisson arrival rate (req/s; 0: profile)")
+    ap.add_argument("--requests", type=int, default=0, help="serve workload: number of requests (0: profile)")
+    ap.add_argument("--serve-profile", choices=["stated", "scaled"], default="stated",
+                    help="serve workload: the stream as stated (200 req/s, 2000 requests, U{48..256}, 512^3 every "
+                         "100th) or scaled to one GPU")
+    ap.add_argument("--serve-seconds", type=float, default=120.0, help="serve workload: length of each arm (stated)")
     return ap.parse_args()
 
 
@@ -684,6 +688,8 @@ def run_batch(args):
     torch.cuda.synchronize()
     p = fld.params(limiter="lp", precision="mixed", tol=args.tol, check_every=args.check_every,
                    max_iters=args.max_iters)
+    pa = fld.params(limiter="lp", precision="mixed", tol=args.tol, check_every=args.anderson_check,
+                    max_iters=args.max_iters, anderson=args.anderson_m)
 
     def setup():
         grids = []
@@ -702,19 +708,26 @@ def run_batch(args):
 
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {}
-    for mode in ("sequential", "batched"):
+    modes = ("sequential", "batched", "sequential_anderson", "batched_anderson")
+    for mode in modes:
         grids = setup()
+        pm = pa if mode.endswith("anderson") else p
         with torch.cuda.stream(stream):
             e0.record(stream)
-            if mode == "sequential":
-                rs = [g.solve(p) for g in grids]
+            if mode.startswith("sequential"):
+                rs, done_ms = [], []
+                t0 = time.perf_counter()
+                for g in grids:
+                    rs.append(g.solve(pm))
+                    done_ms.append(1e3 * (time.perf_counter() - t0))
             else:
-                st, rs = fld.fld_solve_batch(grids, p)
+                st, rs = fld.fld_solve_batch(grids, pm)
             e1.record(stream)
             e1.synchronize()
         ms = e0.elapsed_time(e1)
         upd = sum(r.iterations * g.shape[0] * g.shape[1] * g.shape[2] for r, g in zip(rs, grids))
-        lat = sorted(r.ms for r in rs) if mode == "batched" else None
+        # latency: time from the start of the run to each solve's finish
+        lat = sorted(r.ms for r in rs) if mode.startswith("batched") else sorted(done_ms)
         out[mode] = {"ms": ms, "updates": upd, "value": upd / (ms / 1e3),
                      "converged": sum(r.status == fld.FLD_OK for r in rs),
                      "per_solve": [[g.shape[0], fld.fld_status_string(r.status), r.iterations,
@@ -732,19 +745,35 @@ def run_batch(args):
                                f"seed, albedo U[0.8,0.99], point or oblique light, LP, rel. residual {args.tol:g}",
                    "sizes": [sp["n"] for sp in specs]},
         "batched": out["batched"], "sequential": out["sequential"],
+        "sequential_anderson": out["sequential_anderson"], "batched_anderson": out["batched_anderson"],
+        "anderson": {"m": args.anderson_m, "sweeps_per_block": args.anderson_check},
         "speedup_vs_sequential": out["sequential"]["ms"] / out["batched"]["ms"],
+        "speedup_batched_anderson_vs_sequential_plain": out["sequential"]["ms"] / out["batched_anderson"]["ms"],
+        "speedup_batched_anderson_vs_sequential_anderson": out["sequential_anderson"]["ms"] / out["batched_anderson"]["ms"],
     }
     print(json.dumps(line), flush=True)
 
 
 def run_serve(args):
-    """A Poisson stream of independent solves (edges U{24..64}, a 96^3 request
-    every 50th, per-request fBm medium, albedo U[0.8, 0.99], point or oblique
-    light, LP, rel. residual 1e-6) served with continuous batching, against
-    the same stream solved one request at a time (FIFO) and plain FP64 solves
-    one at a time."""
+    """A Poisson stream of independent solves served with continuous batching.
+
+    --serve-profile stated (default): the configuration as stated -- rate
+    --rate (200 req/s), --requests (2000) requests, edges U{48..256}, a 512^3
+    request every 100th, per-request medium (one of four seeded 256^3 fBm
+    clouds, resampled trilinearly to the request's edge and flipped/permuted by
+    the request's seed), albedo U[0.8, 0.99], point or oblique light, LP, rel.
+    residual --tol, Anderson mixing (m = --anderson-m, --anderson-check sweeps
+    per block).  One GPU cannot keep up with this stream, so every arm runs
+    for --serve-seconds and reports offered against achieved load, what was
+    left unfinished, and the latency of what finished.  Arms: continuous
+    batching; one request at a time (FIFO) with the same parameters; one at a
+    time without Anderson mixing; one at a time in plain FP64 sweeps.
+    --serve-profile scaled: the earlier stream scaled to one GPU (30 req/s,
+    120 requests, edges U{24..64}, a 96^3 request every 50th), run to
+    completion."""
     import numpy as np
     import torch
+    import torch.nn.functional as F
 
     import fld_inputs
     import paper_1403_8105_gb300 as fld
@@ -752,22 +781,36 @@ def run_serve(args):
 
     dev = torch.device("cuda", 0)
     torch.cuda.set_device(dev)
-    rng = np.random.default_rng(77)
-    arr = serve.poisson_arrivals(args.requests, args.rate, 77)
-    cache = {}
+    stated = args.serve_profile == "stated"
+    rate = args.rate if args.rate > 0 else (200.0 if stated else 30.0)
+    count = args.requests if args.requests > 0 else (2000 if stated else 120)
+    nmin, nmax = (48, 256) if stated else (24, 64)
+    heavy_every, heavy_n = (100, 512) if stated else (50, 96)
+    deadline = args.serve_seconds if stated else None
+    arr = serve.poisson_arrivals(count, rate, 77)
+    base_n = 256 if stated else 64
+    bases = []
+    for b in range(4):
+        sig, _ = fld_inputs.cloud_medium(base_n, seed=b, albedo=0.9)
+        bases.append(torch.from_numpy(sig).to(dev)[None, None])
+    perms = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
 
     def medium(n, seed, albedo):
-        key = (n, seed % 6)
-        if key not in cache:
-            sig, _ = fld_inputs.cloud_medium(n, seed=key[1], albedo=0.9)
-            cache[key] = torch.from_numpy(sig).to(dev)
-        return cache[key], torch.full((n, n, n), albedo, dtype=torch.float32, device=dev)
+        rg = np.random.default_rng(seed)
+        v = F.interpolate(bases[seed % 4], size=(n, n, n), mode="trilinear", align_corners=False)[0, 0]
+        v = v.permute(*perms[int(rg.integers(0, 6))])
+        flips = [a for a in range(3) if rg.integers(0, 2)]
+        if flips:
+            v = torch.flip(v, flips)
+        return v.contiguous(), torch.full((n, n, n), albedo, dtype=torch.float32, device=dev)
 
-    def make_requests():
+    am = args.anderson_m
+
+    def make_requests(limit=None):
         reqs = []
         r2 = np.random.default_rng(78)
-        for i in range(args.requests):
-            n = 96 if (i + 1) % 50 == 0 else int(r2.integers(24, 65))
+        for i in range(count if limit is None else limit):
+            n = heavy_n if (i + 1) % heavy_every == 0 else int(r2.integers(nmin, nmax + 1))
             seed = int(r2.integers(0, 1 << 30))
             albedo = float(r2.uniform(0.8, 0.99))
             if r2.integers(0, 2):
@@ -776,68 +819,109 @@ def run_serve(args):
             else:
                 light = fld_inputs.Light(kind="directional", dir=(float(r2.uniform(-0.3, 0.3)),
                                                                   float(r2.uniform(-0.3, 0.3)), -1.0))
-            reqs.append(serve.Request(rid=i, arrival=float(arr[i]), n=n, medium=medium(n, seed, albedo), light=light,
-                                      footprint=serve.footprint_bytes(n)))
+            reqs.append(serve.Request(rid=i, arrival=float(arr[i]), n=n, medium=(seed, albedo), light=light,
+                                      footprint=serve.footprint_bytes(n, anderson=am)))
         return reqs
 
-    p = fld.params(limiter="lp", precision="mixed", tol=args.tol, check_every=64, max_iters=args.max_iters)
+    class Backend(serve.GpuBackend):
+        def admit(self, req):
+            seed, albedo = req.medium
+            req.medium = medium(req.n, seed, albedo)
+            g = super().admit(req)
+            req.medium = (seed, albedo)
+            return g
+
+    common = dict(limiter="lp", precision="mixed", tol=args.tol, max_iters=args.max_iters, temporal_depth=-1)
+    p = fld.params(check_every=args.anderson_check, anderson=am, **common)
+    p_plain = fld.params(check_every=64, **common)
     stream = torch.cuda.Stream(device=dev)
-    # warm-up: one small solve
-    w = make_requests()[:2]
-    torch.cuda.synchronize()
-    be = serve.GpuBackend(p, stream=stream.cuda_stream)
-    serve.serve([serve.Request(rid=r.rid, arrival=0.0, n=r.n, medium=r.medium, light=r.light,
-                               footprint=r.footprint) for r in w], be)
+    # warm-up: two small requests
+    w = [serve.Request(rid=r.rid, arrival=0.0, n=min(r.n, 64), medium=r.medium, light=r.light, footprint=r.footprint)
+         for r in make_requests(2)]
+    be = Backend(p, stream=stream.cuda_stream)
+    serve.serve(w, be)
     be.close()
 
     reqs = make_requests()
     torch.cuda.synchronize()
-    be = serve.GpuBackend(p, stream=stream.cuda_stream)
+    be = Backend(p, stream=stream.cuda_stream)
     try:
-        reqs, st = serve.serve(reqs, be, max_active=64)
+        reqs, st = serve.serve(reqs, be, max_active=64, deadline=deadline)
     finally:
         be.close()
-    upd = sum(r.result.iterations * r.n ** 3 for r in reqs)
-    cont = dict(st, voxel_updates_per_s=upd / st["span_s"],
-                converged=sum(r.result.status == fld.FLD_OK for r in reqs))
+    fin = [r for r in reqs if r.finished >= 0]
+    upd = sum(r.result.iterations * r.n ** 3 for r in fin)
+    cont = dict(st, voxel_updates_per_s=upd / st["run_s"], converged=sum(r.result.status == fld.FLD_OK for r in fin))
 
-    def one_at_a_time(reqs, params, limit):
+    def one_at_a_time(params, limit_s, max_requests=None, chunk=4096):
+        """Requests in arrival order, one solve at a time.  A solve runs in
+        chunks of `chunk` iterations (later chunks continue from the state
+        with warm_start), so an arm stops within one chunk of its deadline;
+        a request still unsolved then is not counted."""
+        import ctypes
+        rs = make_requests()
         t0 = time.perf_counter()
         lat, upd, n_done = [], 0, 0
-        for r in reqs[:limit]:
+        for r in rs:
             now = time.perf_counter() - t0
+            if (limit_s is not None and now >= limit_s) or (max_requests and n_done >= max_requests):
+                break
             if now < r.arrival:
                 time.sleep(r.arrival - now)
             g = fld.Grid(r.n, r.n, r.n, 1.0 / r.n, stream=stream.cuda_stream)
-            g.set_medium(*r.medium)
+            g.set_medium(*medium(r.n, *r.medium))
             if r.light.kind == "point":
                 g.bake_point(r.light.pos, r.light.power)
             else:
                 g.bake_directional(r.light.dir, r.light.radiance)
-            res = g.solve(params)
+            q = type(params)()
+            ctypes.memmove(ctypes.byref(q), ctypes.byref(params), ctypes.sizeof(params))
+            its, ok, late = 0, False, False
+            while its < params.max_iters:
+                q.max_iters = min(chunk, params.max_iters - its)
+                res = g.solve(q, check=False)
+                its += res.iterations
+                if res.status != fld.FLD_ERR_NOT_CONVERGED or res.iterations < q.max_iters:
+                    ok = res.status == fld.FLD_OK
+                    break
+                q.warm_start, q.warmup_iters = 1, 0
+                if limit_s is not None and time.perf_counter() - t0 >= limit_s:
+                    late = True
+                    break
             g.close()
+            if late:
+                break
             lat.append(time.perf_counter() - t0 - r.arrival)
-            upd += res.iterations * r.n ** 3
-            n_done += 1
-        span = time.perf_counter() - t0 - reqs[0].arrival
-        return {"requests": n_done, "latency_s_p50": float(np.percentile(lat, 50)),
-                "latency_s_p99": float(np.percentile(lat, 99)), "throughput_req_s": n_done / span,
-                "voxel_updates_per_s": upd / span}
+            upd += its * r.n ** 3
+            n_done += 1 if ok else 0
+        span = time.perf_counter() - t0
+        return {"requests": n_done, "run_s": span,
+                "latency_s_p50": float(np.percentile(lat, 50)) if lat else None,
+                "latency_s_p99": float(np.percentile(lat, 99)) if lat else None,
+                "throughput_req_s": n_done / span, "voxel_updates_per_s": upd / span}
 
-    seq = one_at_a_time(make_requests(), p, args.requests)
+    seq = one_at_a_time(p, deadline)
+    seq_plain = one_at_a_time(p_plain, deadline)
     p64 = fld.params(limiter="lp", precision="fp64", tol=args.tol, check_every=64, max_iters=args.max_iters)
-    seq64 = one_at_a_time(make_requests(), p64, min(12, args.requests))
-    offered = args.rate
+    seq64 = one_at_a_time(p64, deadline, max_requests=None if stated else 12)
+    mean_vox = float(np.mean([r.n ** 3 for r in make_requests()]))
     line = {
         "metric": METRIC, "value": cont["voxel_updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
-        "ms_per_step": cont["span_s"] * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (float-float correction sweeps)", "data": "synthetic",
-        "config": {"workload": f"Poisson stream of {args.requests} FLD solves at {offered:g} req/s, edges U{{24..64}}, "
-                               f"every 50th 96^3, per-request fBm medium/albedo/light, LP, rel. residual {args.tol:g}",
+        "ms_per_step": cont["run_s"] * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 (float-float correction sweeps; FP64 stop test)", "data": "synthetic",
+        "config": {"workload": f"Poisson stream of {count} FLD solves at {rate:g} req/s, edges U{{{nmin}..{nmax}}}, "
+                               f"every {heavy_every}th {heavy_n}^3, per-request medium/albedo/light, LP, "
+                               f"rel. residual {args.tol:g}, Anderson m={am}",
+                   "profile": args.serve_profile,
+                   "deadline_s": deadline,
                    "admission": "free device memory >= footprint / 0.9 and < 64 solves in flight"},
-        "continuous_batching": cont, "one_at_a_time_mixed": seq, "one_at_a_time_fp64_first12": seq64,
-        "offered_req_s": offered,
-        "throughput_gain_vs_one_at_a_time": cont["throughput_req_s"] / seq["throughput_req_s"],
+        "offered": {"req_s": rate, "voxels_per_s": rate * mean_vox, "mean_voxels_per_request": mean_vox},
+        "continuous_batching": cont, "one_at_a_time": seq, "one_at_a_time_no_anderson": seq_plain,
+        "one_at_a_time_fp64": seq64,
+        "throughput_gain_vs_one_at_a_time": cont["throughput_req_s"] / seq["throughput_req_s"]
+        if seq["throughput_req_s"] else None,
+        "throughput_gain_vs_fp64": cont["throughput_req_s"] / seq64["throughput_req_s"]
+        if seq64["throughput_req_s"] else None,
     }
     print(json.dumps(line), flush=True)
 

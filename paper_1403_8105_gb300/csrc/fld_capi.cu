@@ -828,6 +828,30 @@ fld_status validate_inputs(fld_grid_s *g, const float *st, const float *alb, con
     return FLD_OK;
 }
 
+// Everything a solve may allocate on the device, allocated before it starts
+// (so admission by free memory sees it, and no allocation falls inside the
+// solve): the safeguard's snapshot of the single-precision state, and, for a
+// MIXED solve with the FP64 stop test, the FP64 fields and their snapshot.
+fld_status preallocate(fld_grid_s *g, const fld_solve_params *p) {
+    const size_t nf = sizeof(float) * (size_t)g->L.total, nd = sizeof(double) * (size_t)g->L.total;
+    const bool f64 = p->precision == FLD_PREC_FP64 || (p->precision == FLD_PREC_MIXED && p->fp64_verify);
+    if (f64) {
+        fld_status st = ensure_f64(g);
+        if (st != FLD_OK) return st;
+    }
+    bool ok = true;
+    if (!g->snap_phi)
+        ok = cudaMalloc((void **)&g->snap_phi, nf) == cudaSuccess && cudaMalloc((void **)&g->snap_lo, nf) == cudaSuccess &&
+             cudaMalloc((void **)&g->snap_D, nf) == cudaSuccess;
+    if (ok && f64 && !g->snap_phi64)
+        ok = cudaMalloc((void **)&g->snap_phi64, nd) == cudaSuccess && cudaMalloc((void **)&g->snap_D64, nd) == cudaSuccess;
+    if (!ok) {
+        (void)cudaGetLastError();
+        return fail(FLD_ERR_OOM, "cudaMalloc of the solve's buffers failed");
+    }
+    return FLD_OK;
+}
+
 // Copy the family's state into (save) or out of (restore) the snapshot.
 fld_status snapshot(fld_grid_s *g, Family fam, bool save) {
     const size_t nf = sizeof(float) * (size_t)g->L.total, nd = sizeof(double) * (size_t)g->L.total;
@@ -1553,6 +1577,7 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
     const long long kernels0 = g->kernels;
     Family fam = start_family(p->precision);
     if ((st = prepare(g, p, fam)) != FLD_OK) return st;
+    if ((st = preallocate(g, p)) != FLD_OK) return st;
     if (!p->warm_start) {
         if ((st = init_state(g, p, fam)) != FLD_OK) return st;
     } else if (p->precision == FLD_PREC_MIXED && !g->valid_d && g->lo_live) {
@@ -1768,7 +1793,22 @@ struct ServerEntry {
     bool snap_lo = false;
     fld_solve_result res{};
     std::chrono::steady_clock::time_point t_add;
+    // Anderson mixing, as in fld_solve
+    int am = 0;
+    double gram[kAndersonMax][kAndersonMax] = {};
+    int acount = 0;
+    bool have_x = false;
 };
+
+namespace {
+// The state the Anderson kernels read and write for family fam.
+void anderson_state(fld_grid_s *g, Family fam, float **hi, float **lo, double **p64) {
+    const bool d = fam == FAM_F64;
+    *hi = d ? nullptr : g->f.phi;
+    *lo = !d && g->lo_live ? g->f.phlo : nullptr;
+    *p64 = d ? g->f.phi64 : nullptr;
+}
+}  // namespace
 
 struct fld_server_s {
     int device = 0;
@@ -1847,7 +1887,9 @@ fld_status fld_server_create(const fld_solve_params *p, void *stream, fld_server
     if (!p) return fail(FLD_ERR_INVALID_ARG, "params is NULL");
     if (p->precision == FLD_PREC_FP64 || p->precision < 0 || p->precision > FLD_PREC_PAIR)
         return fail(FLD_ERR_INVALID_ARG, "the server runs the FP32 / MIXED / PAIR sweeps; use fld_solve for FP64");
-    if (p->anderson != 0) return fail(FLD_ERR_INVALID_ARG, "Anderson mixing runs in fld_solve only");
+    if (p->anderson < 0 || p->anderson > kAndersonMax) return fail(FLD_ERR_INVALID_ARG, "anderson must lie in [0, 16]");
+    if (p->anderson > 0 && p->scheme == FLD_SCHEME_JACOBI)
+        return fail(FLD_ERR_INVALID_ARG, "Anderson mixing accelerates the red-black scheme only");
     if (p->limiter < FLD_LIM_CDA || p->limiter > FLD_LIM_LP) return fail(FLD_ERR_INVALID_ARG, "unknown limiter");
     if (p->temporal_depth < -1 || p->temporal_depth == 3 || p->temporal_depth > 4 || p->tile_y < 0)
         return fail(FLD_ERR_INVALID_ARG, "temporal_depth must be -1, 0, 1, 2 or 4 and tile_y >= 0");
@@ -1930,6 +1972,9 @@ fld_status fld_server_add(fld_server s, fld_grid g, long long tag) {
     e.pp = pass_params(g, p);
     if ((st = choose_sweeps(g, p, &e.pp, &e.ce)) != FLD_OK) return st;
     e.warm = warmup_of(g, p);
+    e.am = p->anderson;
+    if (e.am > 0 && (st = ensure_anderson(g, e.am)) != FLD_OK) return st;
+    if ((st = preallocate(g, p)) != FLD_OK) return st;
     e.ctl.precision = p->precision;
     e.ctl.tol = p->tol;
     e.ctl.sw = s->sw;
@@ -1992,11 +2037,29 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
         const size_t nside = s->side.size() < n ? s->side.size() : n;
         for (size_t i = 0; i < nside; ++i) FLD_CK(cudaStreamWaitEvent(s->side[i], s->fork, 0));
         std::vector<int> k(n);
+        std::vector<char> mixing(n, 0);
         for (size_t i = 0; i < n; ++i) {
             ServerEntry &e = s->active[i];
             k[i] = block_len(e.res.iterations, check_len(e.fam, p->precision, e.ce), p->max_iters, e.warm);
             if (k[i] <= 0) continue;
             e.g->stream = s->side[i % nside];
+            // Anderson: after the warm-up each block starts from the mix of
+            // the last am images (the history starts from the state here)
+            mixing[i] = e.am > 0 && e.res.iterations >= e.warm;
+            if (mixing[i] && !e.have_x) {
+                float *hi, *lo;
+                double *p64;
+                anderson_state(e.g, e.fam, &hi, &lo, &p64);
+                const cudaError_t ce = launch_anderson_capture(e.g->anderson, e.g->L.total, hi, lo, p64, e.g->nsm,
+                                                               e.g->stream);
+                if (ce != cudaSuccess) {
+                    e.g->stream = s->bs;
+                    return cuda_fail(ce, "launch_anderson_capture");
+                }
+                s->launches += 1;
+                e.have_x = true;
+                e.acount = 0;
+            }
             st = run_block(e.g, e.fam, block_params(e.pp, e.res.iterations, e.warm), k[i]);
             e.g->stream = s->bs;
             if (st != FLD_OK) return st;
@@ -2058,6 +2121,7 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
         }
         // -- each grid's own decisions (same as fld_solve)
         std::vector<std::pair<size_t, std::pair<fld_status, double>>> retire;
+        std::vector<char> mix_now(n, 0);
         for (size_t i = 0; i < n; ++i) {
             ServerEntry &e = s->active[i];
             fld_grid_s *g = e.g;
@@ -2108,6 +2172,53 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
             }
             if (a != ACT_CONVERGED && a != ACT_DIVERGED && a != ACT_STALLED && e.res.iterations >= p->max_iters)
                 retire.push_back({i, {FLD_ERR_NOT_CONVERGED, rel}});
+            if (a == ACT_RESTORE || a == ACT_SWITCH || a == ACT_CONVERGED) e.have_x = false;
+            // Anderson step after a block that made ordinary progress (as in fld_solve)
+            mix_now[i] = mixing[i] && e.have_x && (a == ACT_CONTINUE || a == ACT_SAVE) &&
+                         e.res.iterations < p->max_iters;
+        }
+        // -- Anderson: collect every mixing grid's image and dot products, one
+        // readback, then each grid's weights and mix (same kernels and order
+        // as fld_solve, so a grid's iterates are those of its solo solve)
+        std::vector<double> dots(n * kAndersonMax);
+        bool any_mix = false;
+        for (size_t i = 0; i < n; ++i) {
+            if (!mix_now[i]) continue;
+            ServerEntry &e = s->active[i];
+            const int slot = e.acount % e.am;
+            const int w = e.acount + 1 < e.am ? e.acount + 1 : e.am;
+            float *hi, *lo;
+            double *p64;
+            anderson_state(e.g, e.fam, &hi, &lo, &p64);
+            FLD_CK(launch_anderson_collect(e.g->anderson, e.g->L.total, hi, lo, p64, slot, w, e.g->nsm, s->bs));
+            FLD_CK(cudaMemcpyAsync(&dots[i * kAndersonMax], e.g->anderson.dots, sizeof(double) * w,
+                                   cudaMemcpyDeviceToHost, s->bs));
+            s->launches += 2;
+            any_mix = true;
+        }
+        if (any_mix) FLD_CK(cudaStreamSynchronize(s->bs));
+        for (size_t i = 0; i < n; ++i) {
+            if (!mix_now[i]) continue;
+            ServerEntry &e = s->active[i];
+            const int slot = e.acount % e.am;
+            ++e.acount;
+            const int w = e.acount < e.am ? e.acount : e.am;
+            for (int j = 0; j < w; ++j) e.gram[slot][j] = e.gram[j][slot] = dots[i * kAndersonMax + j];
+            double wts[kAndersonMax];
+            bool ok = true;
+            if (w == 1) wts[0] = 1.0;
+            else ok = anderson_weights(e.gram, w, wts);
+            if (ok) {
+                float *hi, *lo;
+                double *p64;
+                anderson_state(e.g, e.fam, &hi, &lo, &p64);
+                FLD_CK(launch_anderson_mix(e.g->anderson, e.g->L.total, slot, w, wts, hi, lo, p64, e.g->nsm, s->bs));
+                s->launches += 1;
+                if (w > 1) ++e.res.anderson_steps;
+            } else {
+                ++e.res.anderson_resets;
+                e.have_x = false;
+            }
         }
         for (size_t r = retire.size(); r-- > 0;) {
             ServerEntry &e = s->active[retire[r].first];
@@ -2142,7 +2253,6 @@ fld_status fld_solve_batch(fld_grid *grids, int count, const fld_solve_params *p
     if ((st = check_params(grids[0], p)) != FLD_OK) return st;
     if (p->precision == FLD_PREC_FP64)
         return fail(FLD_ERR_INVALID_ARG, "batched solves run the FP32 / MIXED sweeps; use fld_solve for FP64");
-    if (p->anderson != 0) return fail(FLD_ERR_INVALID_ARG, "Anderson mixing runs in fld_solve only");
     if (!(p->tol >= 0.0)) return fail(FLD_ERR_INVALID_ARG, "tol must be >= 0");
     if (p->max_iters < 0 || p->check_every < 0) return fail(FLD_ERR_INVALID_ARG, "bad max_iters / check_every");
     // Grids of one group should keep their per-iteration working set (24 bytes

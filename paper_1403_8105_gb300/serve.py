@@ -20,11 +20,15 @@ import time
 
 import numpy as np
 
-# bytes per voxel a grid holds on the device: the single-precision fields
-# (sigma', sigma_a', j, phi hi/lo, D, fresh D: 28 B, up to 2x for half-row
-# padding at small sizes), the FP32 inputs (12 B) and the safeguard snapshot
-# (12 B)
-BYTES_PER_VOXEL = 80
+# bytes per padded voxel a grid holds on the device once admitted (the server
+# allocates all of it at admission): the single-precision fields (sigma',
+# sigma_a', j, phi hi/lo, D, fresh D: 28 B), the FP32 inputs (12 B), the
+# safeguard snapshot (12 B), the FP64 fields of the FP64 stop test (sigma',
+# sigma_a', j, phi, D, fresh D: 48 B) and their snapshot (16 B); Anderson
+# mixing adds 12 B per history slot plus 8 B.  Half-row padding of the
+# colour-split layout adds up to 2x at small edges (accounted for below).
+BYTES_PER_VOXEL = 116
+BYTES_PER_ANDERSON_SLOT = 12
 
 
 @dataclasses.dataclass
@@ -57,6 +61,8 @@ class GpuBackend:
         self.Grid = Grid
         self.device = torch.device("cuda", device)
         self.stream = stream
+        self.params = params
+        self.Server = Server
         self.server = Server(params, stream)
 
     def free_bytes(self) -> int:
@@ -85,17 +91,26 @@ class GpuBackend:
     def release(self, grid):
         grid.close()
 
+    def reset(self):
+        # a fresh server: grids released while in flight leave the old one
+        self.server.close()
+        self.server = self.Server(self.params, self.stream)
+
     def close(self):
         self.server.close()
 
 
 def serve(requests, backend, max_active: int = 64, memory_fraction: float = 0.9, clock=time.perf_counter,
-          sleep=time.sleep, keep_grids: bool = False):
-    """Run the request stream to completion; returns (requests, stats).
+          sleep=time.sleep, keep_grids: bool = False, deadline: float | None = None):
+    """Run the request stream to completion (or until `deadline` seconds after
+    the start, for a stream one device cannot keep up with); returns
+    (requests, stats).
 
     A request is admitted when it has arrived, fewer than `max_active` solves
     are in flight, and its footprint fits in `memory_fraction` of the free
-    device memory.  Requests are admitted in arrival order (no overtaking)."""
+    device memory.  Requests are admitted in arrival order (no overtaking).
+    queue_depth_mean is time-weighted: the number of arrived, not yet
+    admitted requests integrated over the run, divided by its length."""
     pending = collections.deque(sorted(requests, key=lambda r: r.arrival))
     waiting = collections.deque()
     grids = {}
@@ -103,9 +118,15 @@ def serve(requests, backend, max_active: int = 64, memory_fraction: float = 0.9,
     t0 = clock()
     steps = 0
     max_in_flight = 0
-    depth = []          # requests arrived but not admitted, after each admission round
+    depth_max = 0
+    depth_area = 0.0    # integral of the queue depth over time
+    t_last, d_last = 0.0, 0
+    stopped = False
     while pending or waiting or backend.active() > 0:
         now = clock() - t0
+        if deadline is not None and now >= deadline:
+            stopped = True
+            break
         while pending and pending[0].arrival <= now:
             waiting.append(pending.popleft())
         while waiting and backend.active() < max_active:
@@ -116,7 +137,10 @@ def serve(requests, backend, max_active: int = 64, memory_fraction: float = 0.9,
             req.admitted = clock() - t0
             grids[req.rid] = backend.admit(req)
         max_in_flight = max(max_in_flight, backend.active())
-        depth.append(len(waiting))
+        t_now = clock() - t0
+        depth_area += d_last * (t_now - t_last)
+        t_last, d_last = t_now, len(waiting)
+        depth_max = max(depth_max, d_last)
         if backend.active() == 0:
             if pending:
                 sleep(max(0.0, min(0.01, pending[0].arrival - (clock() - t0))))
@@ -133,24 +157,41 @@ def serve(requests, backend, max_active: int = 64, memory_fraction: float = 0.9,
             else:
                 backend.release(g)
         steps += 1
+    t_end = clock() - t0
+    depth_area += d_last * (t_end - t_last)
+    if stopped:      # release what the deadline left in flight
+        for rid, g in list(grids.items()):
+            backend.release(g)
+        grids.clear()
+        backend.reset()
     done = [r for r in requests if r.finished >= 0]
     lat = np.array([r.finished - r.arrival for r in done])
     span = (max(r.finished for r in done) - min(r.arrival for r in done)) if done else 0.0
+    arrived = [r for r in requests if r.arrival <= t_end]
     stats = {
         "requests": len(done),
+        "arrived": len(arrived),
+        "unfinished_at_deadline": len(requests) - len(done) if stopped else 0,
+        "admitted_unfinished": sum(1 for r in requests if r.admitted >= 0 and r.finished < 0),
+        "run_s": t_end,
         "steps": steps,
         "max_in_flight": max_in_flight,
         "latency_s_p50": float(np.percentile(lat, 50)) if len(lat) else None,
         "latency_s_p99": float(np.percentile(lat, 99)) if len(lat) else None,
         "latency_s_mean": float(lat.mean()) if len(lat) else None,
         "queue_s_p99": float(np.percentile([r.admitted - r.arrival for r in done], 99)) if done else None,
-        "queue_depth_max": max(depth) if depth else 0,
-        "queue_depth_mean": float(np.mean(depth)) if depth else 0.0,
+        "queue_depth_max": depth_max,
+        "queue_depth_mean": depth_area / t_end if t_end > 0 else 0.0,
         "span_s": span,
         "throughput_req_s": len(done) / span if span > 0 else None,
     }
     return requests, stats
 
 
-def footprint_bytes(n: int) -> int:
-    return BYTES_PER_VOXEL * (n + 2) ** 3
+def footprint_bytes(n: int, anderson: int = 0) -> int:
+    """Device bytes of an admitted n^3 grid: per padded voxel, with the
+    colour-split layout's half rows rounded up to 32 elements."""
+    hpx = (31 + (n + 2) // 2 + 1 + 31) // 32 * 32
+    padded = 2 * hpx * (n + 2) * (n + 2)
+    per = BYTES_PER_VOXEL + (BYTES_PER_ANDERSON_SLOT * anderson + 8 if anderson else 0)
+    return per * padded

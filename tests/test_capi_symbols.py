@@ -95,11 +95,13 @@ def test_no_cpu_fallback_without_device():
     assert e.value.status == fld.FLD_ERR_NO_DEVICE
 
 
-def test_server_rejects_anderson_before_touching_a_device():
-    # Anderson mixing is a fld_solve option; the server refuses it while
-    # checking its parameters, which happens before any device call.
+def test_server_checks_its_parameters_before_touching_a_device():
+    # an out-of-range Anderson history or a bad blocking depth is refused while
+    # the server checks its parameters, which happens before any device call
     import paper_1403_8105_gb300 as fld
-    with pytest.raises(fld.FldError) as e:
-        fld.fld_server_create(fld.params(anderson=4))
-    assert e.value.status == fld.FLD_ERR_INVALID_ARG
-    assert "Anderson" in fld.fld_last_error()
+    for bad, word in ((dict(anderson=17), "anderson"), (dict(anderson=4, scheme=1), "Anderson"),
+                      (dict(temporal_depth=3), "temporal_depth"), (dict(fp64_verify=2), "fp64_verify")):
+        with pytest.raises(fld.FldError) as e:
+            fld.fld_server_create(fld.params(**bad))
+        assert e.value.status == fld.FLD_ERR_INVALID_ARG
+        assert word in fld.fld_last_error()

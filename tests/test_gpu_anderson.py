@@ -101,8 +101,60 @@ def test_anderson_argument_checks():
                 g.solve(fld.params(**bad))
             assert e.value.status == fld.FLD_ERR_INVALID_ARG, bad
         with pytest.raises(fld.FldError) as e:
-            fld.fld_solve_batch([g], fld.params(anderson=4))
+            fld.fld_solve_batch([g], fld.params(anderson=17))
         assert e.value.status == fld.FLD_ERR_INVALID_ARG
     with pytest.raises(fld.FldError) as e:
-        fld.fld_server_create(fld.params(anderson=4))
+        fld.fld_server_create(fld.params(anderson=-1))
     assert e.value.status == fld.FLD_ERR_INVALID_ARG
+
+
+def test_anderson_batch_and_server_equal_solo_solves():
+    # the mix runs per grid in the batched and served paths too, with the same
+    # kernels at the same points of each grid's solve: every result equals its
+    # solo solve bit for bit, and the oracle's fixed point
+    p = fld.params(precision="mixed", tol=1e-6, check_every=16, max_iters=400000, anderson=6)
+    shapes = [(16, 16, 16), (12, 20, 18), (21, 13, 9)]
+    cases = [cloud(s) for s in shapes]
+
+    def grid(sig, alb, q, h):
+        nz, ny, nx = sig.shape
+        g = fld.Grid(nx, ny, nz, h)
+        g.set_medium(sig, alb)
+        g.set_source(q)
+        return g
+
+    solo = []
+    for c in cases:
+        with grid(*c) as g:
+            r = g.solve(p)
+            assert r.status == fld.FLD_OK and r.anderson_steps > 0, r.as_dict()
+            solo.append((r.iterations, r.anderson_steps, g.get_state()[0]))
+    grids = [grid(*c) for c in cases]
+    try:
+        st, rs = fld.fld_solve_batch(grids, p)
+        assert st == fld.FLD_OK
+        for a, g in enumerate(grids):
+            assert (rs[a].iterations, rs[a].anderson_steps) == solo[a][:2]
+            assert np.array_equal(g.get_state()[0], solo[a][2]), a
+    finally:
+        for g in grids:
+            g.close()
+    grids = [grid(*c) for c in cases]
+    try:
+        done = {}
+        with fld.Server(p) as srv:
+            srv.add(grids[0], 0)
+            steps = 0
+            while srv.active > 0 or len(done) < len(grids):
+                if steps in (2, 5):
+                    srv.add(grids[1 if steps == 2 else 2], 1 if steps == 2 else 2)
+                for tag, r in srv.step():
+                    done[tag] = r
+                steps += 1
+                assert steps < 100000
+        for a, g in enumerate(grids):
+            assert done[a].iterations == solo[a][0]
+            assert np.array_equal(g.get_state()[0], solo[a][2]), a
+    finally:
+        for g in grids:
+            g.close()

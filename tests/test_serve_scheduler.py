@@ -53,6 +53,10 @@ class FakeBackend:
     def release(self, grid):
         pass
 
+    def reset(self):
+        self.inflight.clear()
+        self.log.append(("reset",))
+
 
 def _requests(count=40, rate=50.0, seed=3, foot=100):
     arr = serve.poisson_arrivals(count, rate, seed)
@@ -117,3 +121,37 @@ def test_queue_depth_reflects_the_slot_limit():
     # (with free slots a request still waits for the step in flight when it arrives)
     assert st64["queue_s_p99"] <= 0.0101
     assert st1["queue_s_p99"] > 10 * st64["queue_s_p99"]
+
+
+def test_queue_depth_mean_is_time_weighted():
+    # three requests at t = 0, one slot, two 0.01 s steps each: two wait for
+    # 0.02 s, one more for another 0.02 s, then none -- the mean over the
+    # 0.06 s run is (2 * 0.02 + 1 * 0.02) / 0.06 = 1, however often the loop
+    # samples the queue
+    clk = FakeClock()
+    reqs = [serve.Request(rid=i, arrival=0.0, n=16, medium=None, light=None, footprint=1) for i in range(3)]
+    _, st = serve.serve(reqs, FakeBackend(clk), max_active=1, clock=clk, sleep=clk.sleep)
+    assert st["requests"] == 3 and st["queue_depth_max"] == 2
+    assert st["queue_depth_mean"] == pytest.approx(1.0, rel=1e-9)
+
+
+def test_deadline_stops_an_overloaded_stream():
+    # a stream one slot cannot keep up with: the loop stops at the deadline,
+    # counts what is unfinished, releases the solves in flight and resets
+    clk = FakeClock()
+    be = FakeBackend(clk)
+    reqs, st = serve.serve(_requests(count=200, rate=400.0), be, max_active=1, clock=clk, sleep=clk.sleep,
+                           deadline=0.5)
+    assert 0.5 <= st["run_s"] < 0.52
+    assert 0 < st["requests"] < 200 and st["unfinished_at_deadline"] == 200 - st["requests"]
+    assert st["arrived"] > st["requests"]
+    assert ("reset",) in be.log and be.active() == 0
+    assert all(r.finished < 0 or r.finished <= 0.52 for r in reqs)
+
+
+def test_footprint_counts_the_padded_layout():
+    # 64^3: half rows of 96 elements (31 + 33 + 1 = 65, rounded up to a
+    # multiple of 32), 66 x 66 rows, two colours; 116 bytes per padded voxel,
+    # 12 more per Anderson slot plus 8
+    assert serve.footprint_bytes(64) == 116 * 2 * 96 * 66 * 66
+    assert serve.footprint_bytes(64, anderson=8) == (116 + 12 * 8 + 8) * 2 * 96 * 66 * 66
