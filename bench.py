@@ -900,8 +900,11 @@ def run_serve(args):
                 "latency_s_p99": float(np.percentile(lat, 99)) if lat else None,
                 "throughput_req_s": n_done / span, "voxel_updates_per_s": upd / span}
 
+    print(f"serve: continuous batching done ({cont['requests']} requests)", file=sys.stderr, flush=True)
     seq = one_at_a_time(p, deadline)
+    print(f"serve: one at a time done ({seq['requests']} requests)", file=sys.stderr, flush=True)
     seq_plain = one_at_a_time(p_plain, deadline)
+    print(f"serve: one at a time, no Anderson, done ({seq_plain['requests']} requests)", file=sys.stderr, flush=True)
     p64 = fld.params(limiter="lp", precision="fp64", tol=args.tol, check_every=64, max_iters=args.max_iters)
     seq64 = one_at_a_time(p64, deadline, max_requests=None if stated else 12)
     mean_vox = float(np.mean([r.n ** 3 for r in make_requests()]))

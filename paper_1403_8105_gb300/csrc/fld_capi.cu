@@ -53,6 +53,7 @@ constexpr int kSwitchChecks = 24;             // ... before single precision han
 constexpr double kGuardGrowth = 1e3;          // residual growth (vs the best) read as divergence
 constexpr int kSlowDivergeChecks = 32;        // ... or checks without a new minimum while above 4x the best
 constexpr int kFlatWindow = 8;                // single-precision floor: checks compared ...
+constexpr int kFlatWindowMax = 64;            // (the window in checks after scaling, at most)
 constexpr double kFlatGain = 0.05;            // ... and the smallest relative decrease that is progress
 constexpr double kFlatBelow = 0.1;            // ... below this fraction of the starting residual
 constexpr int kMaxBackoffs = 8;               // omega reductions before reporting divergence
@@ -897,8 +898,29 @@ struct Controller {
     double initial = INFINITY;
     int since_best = 0;       // checks without a new minimum
     int backoffs = 0;
-    double recent[kFlatWindow + 1] = {};   // residuals of the last checks of this phase
+    double recent[kFlatWindowMax + 1] = {};   // residuals of the last checks of this phase
     int nrecent = 0;
+    // Windows of the decisions below, in checks.  The constants above are
+    // checks at 256 iterations per check on a 128-voxel edge; a solve keeps
+    // the same windows in iterations per voxel of its largest edge, i.e.
+    // 2 n / check_every checks per constant (never fewer than the constant),
+    // so a shorter check interval or a larger grid does not make it give up
+    // sooner.  The FP64 sweeps that end a MIXED solve keep the constants.
+    int stall_w = kStallChecks, switch_w = kSwitchChecks, slow_w = kSlowDivergeChecks, flat_w = kFlatWindow;
+
+    void scale_windows(int n, int check_every) {
+        auto sc = [&](int base, int cap) {
+            const long long it = 2LL * base * n;
+            long long w = (it + check_every - 1) / check_every;
+            if (w < base) w = base;
+            if (w > cap) w = cap;
+            return (int)w;
+        };
+        stall_w = sc(kStallChecks, 1 << 20);
+        switch_w = sc(kSwitchChecks, 1 << 20);
+        slow_w = sc(kSlowDivergeChecks, 1 << 20);
+        flat_w = sc(kFlatWindow, kFlatWindowMax);
+    }
 
     void begin_phase() {
         since_best = 0;
@@ -918,10 +940,10 @@ struct Controller {
     // kFlatGain over the last kFlatWindow checks.  (Right after omega rises
     // the residual also hovers, but near its start.)
     bool flat(double rel) {
-        recent[nrecent % (kFlatWindow + 1)] = rel;
+        recent[nrecent % (flat_w + 1)] = rel;
         ++nrecent;
-        if (nrecent <= kFlatWindow) return false;
-        const double then = recent[(nrecent - 1 - kFlatWindow) % (kFlatWindow + 1)];
+        if (nrecent <= flat_w) return false;
+        const double then = recent[(nrecent - 1 - flat_w) % (flat_w + 1)];
         return rel > (1.0 - kFlatGain) * then && rel < 1.1 * best && rel < kFlatBelow * initial;
     }
     // The float-float phase met tol on its single-precision-D residual and the
@@ -930,6 +952,10 @@ struct Controller {
     void enter_fp64(double rel) {
         fam = FAM_F64;
         best = rel;
+        stall_w = kStallChecks;
+        switch_w = kSwitchChecks;
+        slow_w = kSlowDivergeChecks;
+        flat_w = kFlatWindow;
         begin_phase();
     }
     // First check (before any iteration): the state is kept as the fallback of
@@ -947,7 +973,7 @@ struct Controller {
         // block that blows up is not taken for the best state
         const double ref = best < initial ? best : initial;
         const bool diverging = !isfinite(rel) || rel > kGuardGrowth * ref ||
-                               (since_best >= kSlowDivergeChecks && rel > 4.0 * best);
+                               (since_best >= slow_w && rel > 4.0 * best);
         if (diverging) {
             if (backoffs >= kMaxBackoffs || omega <= 1.0) return ACT_DIVERGED;
             ++backoffs;
@@ -964,7 +990,7 @@ struct Controller {
         } else {
             ++since_best;
         }
-        const bool no_progress = since_best >= kSwitchChecks;
+        const bool no_progress = since_best >= switch_w;
         // No new minimum for a while and the residual above where the
         // over-relaxed iteration started: that is omega cycling the nonlinear
         // iteration (seen with omega 1.97 at 128^3: 4-6 against a start of
@@ -995,7 +1021,7 @@ struct Controller {
             nrecent = 0;
             return ACT_RESTORE;
         }
-        if (since_best >= kStallChecks && !(precision == FLD_PREC_MIXED && fam != FAM_FF)) return ACT_STALLED;
+        if (since_best >= stall_w && !(precision == FLD_PREC_MIXED && fam != FAM_FF)) return ACT_STALLED;
         return a;
     }
 };
@@ -1593,6 +1619,7 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
     FLD_CK(cudaEventRecord(g->ev0, g->stream));
     Controller ctl;
     ctl.precision = p->precision;
+    ctl.scale_windows(std::max(g->nx, std::max(g->ny, g->nz)), ce);
     ctl.tol = p->tol;
     ctl.sw = sw;
     ctl.fam = fam;
@@ -1976,6 +2003,7 @@ fld_status fld_server_add(fld_server s, fld_grid g, long long tag) {
     if (e.am > 0 && (st = ensure_anderson(g, e.am)) != FLD_OK) return st;
     if ((st = preallocate(g, p)) != FLD_OK) return st;
     e.ctl.precision = p->precision;
+    e.ctl.scale_windows(std::max(g->nx, std::max(g->ny, g->nz)), e.ce);
     e.ctl.tol = p->tol;
     e.ctl.sw = s->sw;
     e.ctl.fam = e.fam;

@@ -159,11 +159,11 @@ def serve(requests, backend, max_active: int = 64, memory_fraction: float = 0.9,
         steps += 1
     t_end = clock() - t0
     depth_area += d_last * (t_end - t_last)
-    if stopped:      # release what the deadline left in flight
+    if stopped:      # release what the deadline left in flight: the server
+        backend.reset()  # first (it hands its grids back), then the grids
         for rid, g in list(grids.items()):
             backend.release(g)
         grids.clear()
-        backend.reset()
     done = [r for r in requests if r.finished >= 0]
     lat = np.array([r.finished - r.arrival for r in done])
     span = (max(r.finished for r in done) - min(r.arrival for r in done)) if done else 0.0

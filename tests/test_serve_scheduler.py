@@ -51,7 +51,8 @@ class FakeBackend:
         return out
 
     def release(self, grid):
-        pass
+        # a grid may only be released once the server no longer holds it
+        assert grid not in self.inflight, "released a grid the server still holds"
 
     def reset(self):
         self.inflight.clear()
