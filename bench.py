@@ -851,17 +851,21 @@ def run_serve(args):
         be.close()
     fin = [r for r in reqs if r.finished >= 0]
     upd = sum(r.result.iterations * r.n ** 3 for r in fin)
-    cont = dict(st, voxel_updates_per_s=upd / st["run_s"], converged=sum(r.result.status == fld.FLD_OK for r in fin))
+    cont = dict(st, voxel_updates_per_s=(st["voxel_updates"] or upd) / st["run_s"],
+                voxel_updates_per_s_finished=upd / st["run_s"],
+                converged=sum(r.result.status == fld.FLD_OK for r in fin))
 
-    def one_at_a_time(params, limit_s, max_requests=None, chunk=4096):
-        """Requests in arrival order, one solve at a time.  A solve runs in
-        chunks of `chunk` iterations (later chunks continue from the state
-        with warm_start), so an arm stops within one chunk of its deadline;
-        a request still unsolved then is not counted."""
+    def one_at_a_time(params, limit_s, max_requests=None, chunk=None):
+        """Requests in arrival order, one solve at a time, until `limit_s`.
+        With `chunk`, a solve runs in chunks of that many iterations (later
+        chunks continue from the state with warm_start), so the arm stops
+        within one chunk of its deadline (the plain FP64 arm, whose single
+        solves can take many minutes); a request still unsolved then is not
+        counted, its partial work is."""
         import ctypes
         rs = make_requests()
         t0 = time.perf_counter()
-        lat, upd, n_done = [], 0, 0
+        lat, upd, n_done, work, failed = [], 0, 0, 0, 0
         for r in rs:
             now = time.perf_counter() - t0
             if (limit_s is not None and now >= limit_s) or (max_requests and n_done >= max_requests):
@@ -878,9 +882,10 @@ def run_serve(args):
             ctypes.memmove(ctypes.byref(q), ctypes.byref(params), ctypes.sizeof(params))
             its, ok, late = 0, False, False
             while its < params.max_iters:
-                q.max_iters = min(chunk, params.max_iters - its)
+                q.max_iters = min(chunk or params.max_iters, params.max_iters - its)
                 res = g.solve(q, check=False)
                 its += res.iterations
+                work += res.iterations * r.n ** 3
                 if res.status != fld.FLD_ERR_NOT_CONVERGED or res.iterations < q.max_iters:
                     ok = res.status == fld.FLD_OK
                     break
@@ -891,14 +896,18 @@ def run_serve(args):
             g.close()
             if late:
                 break
-            lat.append(time.perf_counter() - t0 - r.arrival)
-            upd += its * r.n ** 3
-            n_done += 1 if ok else 0
+            if ok:
+                lat.append(time.perf_counter() - t0 - r.arrival)
+                upd += its * r.n ** 3
+                n_done += 1
+            else:
+                failed += 1
         span = time.perf_counter() - t0
-        return {"requests": n_done, "run_s": span,
+        return {"requests": n_done, "not_converged": failed, "run_s": span,
                 "latency_s_p50": float(np.percentile(lat, 50)) if lat else None,
                 "latency_s_p99": float(np.percentile(lat, 99)) if lat else None,
-                "throughput_req_s": n_done / span, "voxel_updates_per_s": upd / span}
+                "throughput_req_s": n_done / span, "voxel_updates_per_s": work / span,
+                "voxel_updates_per_s_finished": upd / span}
 
     print(f"serve: continuous batching done ({cont['requests']} requests)", file=sys.stderr, flush=True)
     seq = one_at_a_time(p, deadline)
@@ -906,7 +915,7 @@ def run_serve(args):
     seq_plain = one_at_a_time(p_plain, deadline)
     print(f"serve: one at a time, no Anderson, done ({seq_plain['requests']} requests)", file=sys.stderr, flush=True)
     p64 = fld.params(limiter="lp", precision="fp64", tol=args.tol, check_every=64, max_iters=args.max_iters)
-    seq64 = one_at_a_time(p64, deadline, max_requests=None if stated else 12)
+    seq64 = one_at_a_time(p64, deadline, max_requests=None if stated else 12, chunk=4096)
     mean_vox = float(np.mean([r.n ** 3 for r in make_requests()]))
     line = {
         "metric": METRIC, "value": cont["voxel_updates_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,

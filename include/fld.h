@@ -365,6 +365,12 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
 /* Number of grids still iterating. */
 fld_status fld_server_active(fld_server s, int *count);
 
+/* Voxel updates (one phi_p update each; one red-black iteration of an
+ * nx*ny*nz grid is nx*ny*nz of them) the server's steps have performed so far,
+ * over all grids, finished or not: the work a loaded server gets done, which
+ * its finished results alone understate. */
+fld_status fld_server_updates(fld_server s, long long *updates);
+
 /* Destroy the server (grids still inside return to their own streams, their
  * state as left by the last step). */
 void fld_server_destroy(fld_server s);

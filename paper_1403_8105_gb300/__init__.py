@@ -28,6 +28,7 @@ __all__ = [
     "fld_get_source", "fld_bake_directional", "fld_bake_point", "fld_set_state", "fld_get_state",
     "fld_iterate", "fld_solve", "fld_solve_batch", "fld_residual", "fld_residual_noalloc", "fld_destroy",
     "fld_server_create", "fld_server_add", "fld_server_step", "fld_server_active", "fld_server_destroy",
+    "fld_server_updates",
     "Server", "fld_status_string",
     "fld_last_error", "Grid", "params",
 ]
@@ -145,6 +146,7 @@ def load(build_if_missing: bool = True):
             "fld_server_step": (c_int, [_vp, ctypes.POINTER(ctypes.c_longlong), R, c_int,
                                         ctypes.POINTER(c_int)]),
             "fld_server_active": (c_int, [_vp, ctypes.POINTER(c_int)]),
+            "fld_server_updates": (c_int, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
             "fld_server_destroy": (None, [_vp]),
             "fld_residual": (c_int, [_vp, P, ctypes.POINTER(c_double)]),
             "fld_residual_noalloc": (c_int, [c_int, c_int, c_int, c_double, P, _vp, _vp, _vp, _vp, _vp,
@@ -321,6 +323,12 @@ def fld_server_step(s, capacity: int = 256):
     return [(int(tags[i]), res[i]) for i in range(n.value)]
 
 
+def fld_server_updates(s) -> int:
+    n = ctypes.c_longlong(0)
+    _check(load().fld_server_updates(s, ctypes.byref(n)), "fld_server_updates")
+    return n.value
+
+
 def fld_server_active(s) -> int:
     n = ctypes.c_int(0)
     _check(load().fld_server_active(s, ctypes.byref(n)), "fld_server_active")
@@ -347,6 +355,10 @@ class Server:
     @property
     def active(self) -> int:
         return fld_server_active(self.handle)
+
+    @property
+    def updates(self) -> int:
+        return fld_server_updates(self.handle)
 
     def close(self):
         if self.handle:

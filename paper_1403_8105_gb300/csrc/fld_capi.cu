@@ -1853,6 +1853,7 @@ struct fld_server_s {
     std::vector<cudaEvent_t> join;
     cudaEvent_t fork = nullptr;
     long long launches = 0;
+    long long updates = 0;              // voxel updates of all steps so far
 };
 
 namespace {
@@ -2045,6 +2046,12 @@ fld_status fld_server_add(fld_server s, fld_grid g, long long tag) {
     return FLD_OK;
 }
 
+fld_status fld_server_updates(fld_server s, long long *updates) {
+    if (!s || !updates) return fail(FLD_ERR_INVALID_ARG, "server or updates is NULL");
+    *updates = s->updates;
+    return FLD_OK;
+}
+
 fld_status fld_server_active(fld_server s, int *count) {
     if (!s || !count) return fail(FLD_ERR_INVALID_ARG, "server or count is NULL");
     *count = (int)s->active.size();
@@ -2092,6 +2099,7 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
             e.g->stream = s->bs;
             if (st != FLD_OK) return st;
             s->launches += 2LL * k[i];
+            s->updates += (long long)k[i] * nvox(e.g);
             e.res.iterations += k[i];
             if (e.fam == FAM_F32) e.res.iterations_fp32 += k[i];
             else if (e.fam == FAM_FH) e.res.iterations_mid += k[i];

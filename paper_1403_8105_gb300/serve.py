@@ -88,6 +88,9 @@ class GpuBackend:
     def step(self):
         return self.server.step()
 
+    def updates(self) -> int:
+        return self.server.updates
+
     def release(self, grid):
         grid.close()
 
@@ -159,6 +162,7 @@ def serve(requests, backend, max_active: int = 64, memory_fraction: float = 0.9,
         steps += 1
     t_end = clock() - t0
     depth_area += d_last * (t_end - t_last)
+    work = backend.updates() if hasattr(backend, "updates") else None
     if stopped:      # release what the deadline left in flight: the server
         backend.reset()  # first (it hands its grids back), then the grids
         for rid, g in list(grids.items()):
@@ -174,6 +178,7 @@ def serve(requests, backend, max_active: int = 64, memory_fraction: float = 0.9,
         "unfinished_at_deadline": len(requests) - len(done) if stopped else 0,
         "admitted_unfinished": sum(1 for r in requests if r.admitted >= 0 and r.finished < 0),
         "run_s": t_end,
+        "voxel_updates": work,
         "steps": steps,
         "max_in_flight": max_in_flight,
         "latency_s_p50": float(np.percentile(lat, 50)) if len(lat) else None,
