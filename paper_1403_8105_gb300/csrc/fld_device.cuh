@@ -195,6 +195,21 @@ __device__ __forceinline__ ff ff_mul_f(ff a, float b) {
 
 __device__ __forceinline__ double ff_to_d(ff a) { return (double)a.hi + (double)a.lo; }
 
+// a / b rounded to single precision (b > 0): the quotient of the high word,
+// corrected by the exact remainder (FMA) and the low word.
+__device__ __forceinline__ float ff_div_f(ff a, float b) {
+    const float q = __fdiv_rn(a.hi, b);
+    const float r = __fadd_rn(fmaf(-q, b, a.hi), a.lo);
+    return __fadd_rn(q, __fdiv_rn(r, b));
+}
+
+// a / b (b.hi > 0) to single precision, likewise.
+__device__ __forceinline__ float ff_div(ff a, ff b) {
+    const float q = __fdiv_rn(a.hi, b.hi);
+    const float r = __fsub_rn(__fadd_rn(fmaf(-q, b.hi, a.hi), a.lo), __fmul_rn(q, b.lo));
+    return __fadd_rn(q, __fdiv_rn(r, b.hi));
+}
+
 // bfloat16 bit pattern -> float (exact: the pattern is the float's upper half)
 __device__ __forceinline__ float bf16_bits_to_f(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
 

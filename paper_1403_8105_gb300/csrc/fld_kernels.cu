@@ -993,10 +993,17 @@ __global__ void __launch_bounds__(256) k_validate(long long n, const float *__re
 // Single-scatter source.
 // ---------------------------------------------------------------------------
 
+// exp(-(t.hi + t.lo)) for an optical depth held as a float-float pair
+// (|t.lo| <= ulp(t.hi)/2, so exp(-t.lo) = 1 - t.lo to single precision)
+__device__ __forceinline__ float transmittance(ff t) { return expf(-t.hi) * (1.0f - t.lo); }
+
 // Light along -z with step h/2: the samples at quarter-voxel offsets blend the
 // two nearest centres 3:1 and 1:3, so the optical depth above voxel k is the
 // trapezoid sum over the centres above it plus half a voxel of the top
-// centre -- an exclusive scan down each column.
+// centre -- an exclusive scan down each column.  Each trapezoid term
+// (h/2)(s + s_above) is formed exactly as a float-float pair (TwoSum, then
+// TwoProd by h/2) and summed in float-float, so the depth is as accurate as
+// a double-precision sum without double-precision arithmetic.
 __global__ void k_bake_scan_negz(Layout L, const float *__restrict__ st, const float *__restrict__ alb,
                                  float *__restrict__ js, float h, float radiance, int accumulate) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1004,14 +1011,17 @@ __global__ void k_bake_scan_negz(Layout L, const float *__restrict__ st, const f
     if (i >= L.nx || j >= L.ny) return;
     const long long col = (long long)j * L.nx + i;
     const long long sk = (long long)L.nx * L.ny;
-    double tau = 0.0;
+    const float hh = 0.5f * h;
+    ff tau = {0.0f, 0.0f};
     float above = 0.0f;
     for (int k = L.nz - 1; k >= 0; --k) {
         const long long v = col + (long long)k * sk;
         const float s = st[v];
-        tau += (k == L.nz - 1) ? 0.5 * (double)h * (double)s : 0.5 * (double)h * ((double)s + (double)above);
+        const ff sum = (k == L.nz - 1) ? ff{s, 0.0f} : two_sum(s, above);
+        const ff p = two_prod(sum.hi, hh);
+        tau = ff_add(tau, fast_two_sum(p.hi, fmaf(sum.lo, hh, p.lo)));
         above = s;
-        const float q = radiance * (alb[v] * s) * expf(-(float)tau);
+        const float q = radiance * (alb[v] * s) * transmittance(tau);
         js[v] = accumulate ? js[v] + q : q;
     }
 }
@@ -1073,18 +1083,20 @@ __global__ void __launch_bounds__(256) k_bake_march(Layout L, const float *__res
         else if (w[a] < 0.0f) len = fminf(len, (0.0f - x[a]) / w[a]);
     }
     if (point) len = (r > 0.0f) ? fminf(len, r) : 0.0f;
-    double tau = 0.0;
+    // optical depth: the single-precision samples sigma * step summed in
+    // float-float (TwoSum), as accurate as a double-precision sum
+    ff tau = {0.0f, 0.0f};
     const int m_full = (int)floorf(len / step);
     for (int m = 0; m < m_full; ++m) {
         const float t = ((float)m + 0.5f) * step;
-        tau += (double)(sigma_trilinear(L, st, h, x[0] + t * w[0], x[1] + t * w[1], x[2] + t * w[2]) * step);
+        tau = ff_add_f(tau, sigma_trilinear(L, st, h, x[0] + t * w[0], x[1] + t * w[1], x[2] + t * w[2]) * step);
     }
     const float rem = len - (float)m_full * step;
     if (rem > 1e-6f * step) {
         const float t = (float)m_full * step + 0.5f * rem;
-        tau += (double)(sigma_trilinear(L, st, h, x[0] + t * w[0], x[1] + t * w[1], x[2] + t * w[2]) * rem);
+        tau = ff_add_f(tau, sigma_trilinear(L, st, h, x[0] + t * w[0], x[1] + t * w[1], x[2] + t * w[2]) * rem);
     }
-    float q = value * (alb[v] * st[v]) * expf(-(float)tau);
+    float q = value * (alb[v] * st[v]) * transmittance(tau);
     if (point) {
         const float rr = fmaxf(r, 0.5f * h);
         q = q / (4.0f * 3.14159265358979f * rr * rr);

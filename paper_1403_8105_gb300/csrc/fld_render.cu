@@ -93,7 +93,7 @@ __global__ void k_prolong(Layout L, float *__restrict__ phi, float *__restrict__
 
 // Box averages over f^3 blocks (the voxels that exist): sigma_t, albedo =
 // mean(albedo sigma_t) / mean(sigma_t) (0 in vacuum) and the source of the
-// coarse grid, accumulated in double.
+// coarse grid, accumulated in float-float.
 __global__ void k_downsample(int nx, int ny, int nz, int f, int cx, int cy, int cz, const float *__restrict__ st,
                              const float *__restrict__ alb, const float *__restrict__ q, float *__restrict__ st_c,
                              float *__restrict__ alb_c, float *__restrict__ q_c) {
@@ -101,22 +101,24 @@ __global__ void k_downsample(int nx, int ny, int nz, int f, int cx, int cy, int 
     const int J = blockIdx.y * blockDim.y + threadIdx.y;
     const int K = blockIdx.z;
     if (I >= cx || J >= cy) return;
-    double s = 0.0, ss = 0.0, qq = 0.0;
+    // float-float sums (TwoSum; the albedo products exact by TwoProd), as
+    // accurate as double-precision sums, then one division each
+    ff s = {0.0f, 0.0f}, ss = {0.0f, 0.0f}, qq = {0.0f, 0.0f};
     int cnt = 0;
     for (int k = K * f; k < K * f + f && k < nz; ++k)
         for (int j = J * f; j < J * f + f && j < ny; ++j)
             for (int i = I * f; i < I * f + f && i < nx; ++i) {
                 const long long v = ((long long)k * ny + j) * nx + i;
-                const double sv = (double)st[v];
-                s += sv;
-                ss += (double)alb[v] * sv;
-                qq += (double)q[v];
+                const float sv = st[v];
+                s = ff_add_f(s, sv);
+                ss = ff_add(ss, two_prod(alb[v], sv));
+                qq = ff_add_f(qq, q[v]);
                 ++cnt;
             }
     const long long c = ((long long)K * cy + J) * cx + I;
-    st_c[c] = (float)(s / cnt);
-    alb_c[c] = s > 0.0 ? (float)(ss / s) : 0.0f;
-    q_c[c] = (float)(qq / cnt);
+    st_c[c] = ff_div_f(s, (float)cnt);
+    alb_c[c] = s.hi > 0.0f ? ff_div(ss, s) : 0.0f;
+    q_c[c] = ff_div_f(qq, (float)cnt);
 }
 
 __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float w) {

@@ -75,3 +75,32 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
                                          *[ctypes.c_void_p(one.data_ptr())] * 5, ctypes.byref(rel), None)
     assert st == fld.FLD_ERR_INVALID_ARG
     assert "FLD_NOALLOC_MAX_BLOCKS" in fld.fld_last_error()
+
+
+def test_noalloc_allocates_nothing_and_runs_on_a_given_stream():
+    # the entry point's claim itself: after a first call, further calls leave
+    # the device's free memory unchanged (no cudaMalloc, no pool growth), and
+    # the call is ordered on the stream it is given
+    shape = (18, 21, 25)
+    sig, alb, j, phi, D, h = _state(shape, 5)
+    nz, ny, nx = shape
+    p = fld.params(precision="fp64")
+    dev = torch.device("cuda", 0)
+    bufs = [torch.from_numpy(a).to(dev) for a in (sig, alb, j, phi, D)]
+    torch.cuda.synchronize()
+    fn = fld.load().fld_residual_noalloc
+    args = [ctypes.c_void_p(b.data_ptr()) for b in bufs]
+    rel = ctypes.c_double(-1.0)
+    assert fn(nx, ny, nz, h, ctypes.byref(p), *args, ctypes.byref(rel), None) == fld.FLD_OK
+    first = rel.value
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info(dev)
+    side = torch.cuda.Stream(device=dev)
+    for k in range(6):
+        rel = ctypes.c_double(-1.0)
+        stream = ctypes.c_void_p(side.cuda_stream) if k % 2 else None
+        assert fn(nx, ny, nz, h, ctypes.byref(p), *args, ctypes.byref(rel), stream) == fld.FLD_OK
+        assert rel.value == first
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info(dev)
+    assert free1 == free0, (free0, free1)
