@@ -550,12 +550,8 @@ fld_status residual_now(fld_grid_s *g, Family fam, const PassParams &pp, int mar
     double r[2];
     fld_status st = read_result(g, r);
     if (st != FLD_OK) return st;
-    long long ex = g->nx - 2LL * margin, ey = g->ny - 2LL * margin, ez = g->nz - 2LL * margin;
-    const long long cnt = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
     // r[0] = sum (R_p h^2)^2 over the margin set, r[1] = sum (j_p h^2)^2
-    const double rbar_h2 = cnt > 0 ? sqrt(r[0] / (double)cnt) : 0.0;
-    const double jbar_h2 = sqrt(r[1] / (double)nvox(g));
-    *rel = jbar_h2 > 0.0 ? rbar_h2 / jbar_h2 : rbar_h2 / (g->h * g->h);
+    *rel = rel_residual_from_sums(g->nx, g->ny, g->nz, g->h, margin, r[0], r[1]);
     return FLD_OK;
 }
 
@@ -776,13 +772,12 @@ fld_status choose_sweeps(fld_grid_s *g, const fld_solve_params *p, PassParams *p
 
 fld_status check_params(const fld_grid_s *g, const fld_solve_params *p) {
     if (!p) return fail(FLD_ERR_INVALID_ARG, "params is NULL");
-    if (p->limiter < FLD_LIM_CDA || p->limiter > FLD_LIM_LP) return fail(FLD_ERR_INVALID_ARG, "unknown limiter");
-    if (p->limiter == FLD_LIM_LARSEN && !(p->larsen_n > 0.0)) return fail(FLD_ERR_INVALID_ARG, "larsen_n must be > 0");
+    if (const char *bad = check_limiter_margin(p->limiter, p->larsen_n, p->residual_margin))
+        return fail(FLD_ERR_INVALID_ARG, bad);
     if (p->omega > 0.0 && !(p->omega < 2.0)) return fail(FLD_ERR_INVALID_ARG, "omega must lie in (0, 2)");
     if (p->precision < FLD_PREC_FP64 || p->precision > FLD_PREC_PAIR)
         return fail(FLD_ERR_INVALID_ARG, "unknown precision");
     if (p->local_iters > 64) return fail(FLD_ERR_INVALID_ARG, "local_iters must be <= 64");
-    if (p->residual_margin < 0) return fail(FLD_ERR_INVALID_ARG, "residual_margin must be >= 0");
     if (p->medium_bf16 != 0 && p->medium_bf16 != 1) return fail(FLD_ERR_INVALID_ARG, "medium_bf16 must be 0 or 1");
     if (p->warmup_iters < -1) return fail(FLD_ERR_INVALID_ARG, "warmup_iters must be >= -1");
     if (p->scheme != FLD_SCHEME_RED_BLACK && p->scheme != FLD_SCHEME_JACOBI)
@@ -1886,11 +1881,7 @@ fld_status server_workspace(fld_server_s *s, int grids, int res) {
 }
 
 double rel_from_sums(const fld_grid_s *g, int margin, double r2, double j2) {
-    const long long ex = g->nx - 2LL * margin, ey = g->ny - 2LL * margin, ez = g->nz - 2LL * margin;
-    const long long cnt = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
-    const double rb = cnt > 0 ? sqrt(r2 / (double)cnt) : 0.0;
-    const double jb = sqrt(j2 / (double)nvox(g));
-    return jb > 0.0 ? rb / jb : rb / (g->h * g->h);
+    return rel_residual_from_sums(g->nx, g->ny, g->nz, g->h, margin, r2, j2);
 }
 
 void server_retire(fld_server_s *s, size_t i, fld_status st, double rel) {
@@ -1918,13 +1909,13 @@ fld_status fld_server_create(const fld_solve_params *p, void *stream, fld_server
     if (p->anderson < 0 || p->anderson > kAndersonMax) return fail(FLD_ERR_INVALID_ARG, "anderson must lie in [0, 16]");
     if (p->anderson > 0 && p->scheme == FLD_SCHEME_JACOBI)
         return fail(FLD_ERR_INVALID_ARG, "Anderson mixing accelerates the red-black scheme only");
-    if (p->limiter < FLD_LIM_CDA || p->limiter > FLD_LIM_LP) return fail(FLD_ERR_INVALID_ARG, "unknown limiter");
+    if (const char *bad = check_limiter_margin(p->limiter, p->larsen_n, p->residual_margin))
+        return fail(FLD_ERR_INVALID_ARG, bad);
     if (p->temporal_depth < -1 || p->temporal_depth == 3 || p->temporal_depth > 4 || p->tile_y < 0)
         return fail(FLD_ERR_INVALID_ARG, "temporal_depth must be -1, 0, 1, 2 or 4 and tile_y >= 0");
     if (p->fp64_verify != 0 && p->fp64_verify != 1) return fail(FLD_ERR_INVALID_ARG, "fp64_verify must be 0 or 1");
-    if (p->limiter == FLD_LIM_LARSEN && !(p->larsen_n > 0.0)) return fail(FLD_ERR_INVALID_ARG, "larsen_n must be > 0");
     if (p->omega > 0.0 && !(p->omega < 2.0)) return fail(FLD_ERR_INVALID_ARG, "omega must lie in (0, 2)");
-    if (p->local_iters > 64 || p->residual_margin < 0) return fail(FLD_ERR_INVALID_ARG, "bad local_iters / margin");
+    if (p->local_iters > 64) return fail(FLD_ERR_INVALID_ARG, "local_iters must be <= 64");
     if (!(p->tol >= 0.0) || p->max_iters < 0 || p->check_every < 0)
         return fail(FLD_ERR_INVALID_ARG, "bad tol / max_iters / check_every");
     int ndev = 0;

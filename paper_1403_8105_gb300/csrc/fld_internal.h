@@ -4,6 +4,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <math.h>
 #include "fld_device.cuh"
 
 namespace fld {
@@ -210,6 +211,28 @@ cudaError_t tiled_maps(const Layout &L, int id, float *phi, float *D, float *lo,
 cudaError_t launch_tiled(Family fam, int id, const Layout &L, const Fields &f, const PassParams &p,
                          const TiledMaps &src, float *dphi, float *dD, float *dlo, int *status, int nsm,
                          cudaStream_t s);
+
+// Relative residual Rbar / jbar of Eq. 37 from the device sums r2 = sum of
+// (R_p h^2)^2 over the unknowns at least `margin` voxels from the faces and
+// j2 = sum of (j_p h^2)^2 over all unknowns (both RMS, so rel = ||R|| / ||j||
+// over their sets); with no emission at all the absolute RMS residual.  Shared
+// by every entry point that reports a residual.
+inline double rel_residual_from_sums(int nx, int ny, int nz, double h, int margin, double r2, double j2) {
+    const long long ex = nx - 2LL * margin, ey = ny - 2LL * margin, ez = nz - 2LL * margin;
+    const long long cnt = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
+    const double rbar_h2 = cnt > 0 ? sqrt(r2 / (double)cnt) : 0.0;
+    const double jbar_h2 = sqrt(j2 / ((double)nx * ny * nz));
+    return jbar_h2 > 0.0 ? rbar_h2 / jbar_h2 : rbar_h2 / (h * h);
+}
+
+// Checks of the limiter (Table 2 or CDA), Larsen's n and the residual margin
+// shared by the entry points: null if valid, else the message.
+inline const char *check_limiter_margin(int limiter, double larsen_n, int margin) {
+    if (limiter < LIM_CDA || limiter > LIM_LP) return "unknown limiter";
+    if (limiter == LIM_LARSEN && !(larsen_n > 0.0)) return "larsen_n must be > 0";
+    if (margin < 0) return "residual_margin must be >= 0";
+    return nullptr;
+}
 
 // Sets the thread-local text that fld_last_error() returns.
 void set_error_text(const char *msg);

@@ -203,10 +203,8 @@ extern "C" fld_status fld_residual_noalloc(int nx, int ny, int nz, double h, con
     if (!(h > 0.0) || !isfinite(h)) return na_fail(FLD_ERR_INVALID_ARG, "h must be a positive finite number");
     if (!p || !sigma_t || !albedo || !j || !phi || !D || !rel)
         return na_fail(FLD_ERR_INVALID_ARG, "a required pointer is NULL");
-    if (p->limiter < FLD_LIM_CDA || p->limiter > FLD_LIM_LP) return na_fail(FLD_ERR_INVALID_ARG, "unknown limiter");
-    if (p->limiter == FLD_LIM_LARSEN && !(p->larsen_n > 0.0))
-        return na_fail(FLD_ERR_INVALID_ARG, "larsen_n must be > 0");
-    if (p->residual_margin < 0) return na_fail(FLD_ERR_INVALID_ARG, "residual_margin must be >= 0");
+    if (const char *bad = fld::check_limiter_margin(p->limiter, p->larsen_n, p->residual_margin))
+        return na_fail(FLD_ERR_INVALID_ARG, bad);
     const dim3 blk(32, 8, 1);
     const dim3 grd((nx + 31) / 32, (ny + 7) / 8, nz);
     const long long nblocks = (long long)grd.x * grd.y * grd.z;
@@ -245,11 +243,6 @@ extern "C" fld_status fld_residual_noalloc(int nx, int ny, int nz, double h, con
         (void)cudaGetLastError();
         return na_fail(FLD_ERR_CUDA, cudaGetErrorString(e));
     }
-    const long long m = a.margin;
-    const long long ex = nx - 2 * m, ey = ny - 2 * m, ez = nz - 2 * m;
-    const long long cnt = (ex > 0 && ey > 0 && ez > 0) ? ex * ey * ez : 0;
-    const double rbar_h2 = cnt > 0 ? sqrt(r[0] / (double)cnt) : 0.0;
-    const double jbar_h2 = sqrt(r[1] / ((double)nx * ny * nz));
-    *rel = jbar_h2 > 0.0 ? rbar_h2 / jbar_h2 : rbar_h2 / (h * h);
+    *rel = fld::rel_residual_from_sums(nx, ny, nz, h, a.margin, r[0], r[1]);
     return FLD_OK;
 }
