@@ -13,6 +13,17 @@
 namespace fld {
 namespace cell {
 
+// The hardware's approximate reciprocal (PTX rcp.approx.ftz.f32, one
+// special-function-unit instruction, within 1 ulp).  Its operands here are
+// floored well above the denormal range (sigma' >= sigma_eps, the Knudsen
+// denominators >= eps jbar, the update's denominator > 0), so flushing
+// denormals changes nothing.
+__device__ __forceinline__ float fast_rcp(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 // Limiter (Table 2) with approximate reciprocals, for the bulk
 // single-precision sweeps, whose accuracy is bounded by phi stored in float;
 // the correction sweeps and the residual use the correctly rounded forms.
@@ -23,19 +34,18 @@ namespace cell {
 __device__ __forceinline__ float limiter_fast(int kind, float larsen_n, float R) {
     switch (kind) {
     case LIM_CDA: return 1.0f / 3.0f;
-    case LIM_SUM: return __fdividef(1.0f, __fadd_rn(3.0f, R));
-    case LIM_MAX: return __fdividef(1.0f, fmaxf(3.0f, R));
-    case LIM_KERSHAW: return __fdividef(2.0f, __fadd_rn(3.0f, hypotf(3.0f, 2.0f * R)));
+    case LIM_SUM: return fast_rcp(__fadd_rn(3.0f, R));
+    case LIM_MAX: return fast_rcp(fmaxf(3.0f, R));
+    case LIM_KERSHAW: return 2.0f * fast_rcp(__fadd_rn(3.0f, hypotf(3.0f, 2.0f * R)));
     case LIM_LARSEN: {
         const float m = fmaxf(3.0f, R), s = fminf(3.0f, R);
-        return __fdividef(1.0f, m * __powf(__fadd_rn(1.0f, __powf(__fdividef(s, m), larsen_n)),
-                                           __fdividef(1.0f, larsen_n)));
+        return fast_rcp(m * __powf(__fadd_rn(1.0f, __powf(s * fast_rcp(m), larsen_n)), fast_rcp(larsen_n)));
     }
     default: {
         if (R < 1.0f) return lp_series_f(R);
-        const float r = __fdividef(1.0f, R);
+        const float r = fast_rcp(R);
         // 2e/(1-e), e = exp(-2R), is below 3.4e-8 of (1 - 1/R) once R > 9
-        const float tail = R < 9.0f ? __fdividef(2.0f, __fsub_rn(__expf(2.0f * R), 1.0f)) : 0.0f;
+        const float tail = R < 9.0f ? 2.0f * fast_rcp(__fsub_rn(__expf(2.0f * R), 1.0f)) : 0.0f;
         return r * __fadd_rn(__fsub_rn(1.0f, r), tail);
     }
     }
@@ -53,7 +63,7 @@ __device__ __forceinline__ void cell_f32(float p0, const float ps[6], const floa
     const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
     const float g = g2 > 0.0f ? g2 * rsqrtf(g2) * inv2h : 0.0f;     // |grad phi| (Eq. 34)
     const float gmax = fmaxf(g, floor_);
-    const float inv_sp = __fdividef(1.0f, s_);
+    const float inv_sp = fast_rcp(s_);
     float A = 0.0f, B = 0.0f, C = 0.0f;
 #pragma unroll
     for (int s = 0; s < 6; ++s) {
@@ -68,9 +78,9 @@ __device__ __forceinline__ void cell_f32(float p0, const float ps[6], const floa
 #pragma unroll
     for (int r = 0; r < (ROUNDS > 0 ? ROUNDS : 64); ++r) {
         if (ROUNDS == 0 && r >= local_iters) break;
-        const float R = __fdividef(gmax, fmaxf(s_ * __fadd_rn(p0, delta), floor_));     // Eq. 35
+        const float R = gmax * fast_rcp(fmaxf(s_ * __fadd_rn(p0, delta), floor_));     // Eq. 35
         Dp = limiter_fast(lim, larsen_n, R) * inv_sp;                          // Eq. 33
-        delta = __fdividef(fmaf(0.5f * Dp, A, base), fmaf(3.0f, Dp, den0));   // Eq. 32
+        delta = fmaf(0.5f * Dp, A, base) * fast_rcp(fmaf(3.0f, Dp, den0));   // Eq. 32
     }
     phi_new = fmaf(omega, delta, p0);                                          // Eq. 36
     D_new = Dp;
@@ -94,7 +104,7 @@ __device__ __forceinline__ void cell_fh(float p0, float p0lo, const float ps[6],
     const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
     const float g = g2 > 0.0f ? g2 * rsqrtf(g2) * inv2h : 0.0f;
     const float gmax = fmaxf(g, floor_);
-    const float inv_sp = __fdividef(1.0f, s_);
+    const float inv_sp = fast_rcp(s_);
     float A = 0.0f, B = 0.0f, C = 0.0f;
 #pragma unroll
     for (int s = 0; s < 6; ++s) {
@@ -108,9 +118,9 @@ __device__ __forceinline__ void cell_fh(float p0, float p0lo, const float ps[6],
 #pragma unroll
     for (int r = 0; r < (ROUNDS > 0 ? ROUNDS : 64); ++r) {
         if (ROUNDS == 0 && r >= local_iters) break;
-        const float R = __fdividef(gmax, fmaxf(s_ * __fadd_rn(p0, delta), floor_));
+        const float R = gmax * fast_rcp(fmaxf(s_ * __fadd_rn(p0, delta), floor_));
         Dp = limiter_fast(lim, larsen_n, R) * inv_sp;
-        delta = __fdividef(fmaf(0.5f * Dp, A, base), fmaf(3.0f, Dp, den0));
+        delta = fmaf(0.5f * Dp, A, base) * fast_rcp(fmaf(3.0f, Dp, den0));
     }
     const ff nw = ff_add_f(ff{p0, p0lo}, __fmul_rn(omega, delta));
     hi_new = nw.hi;

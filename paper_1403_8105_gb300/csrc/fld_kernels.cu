@@ -650,10 +650,10 @@ __device__ __forceinline__ void pass_ff_body(const Layout &L, const float *__res
         const bool last = ROUNDS > 0 ? r == ROUNDS - 1 : r == local_iters - 1;
         const float pt = __fadd_rn(p0, delta);
         Dp = last ? D_of_f(gmax, s_, pt, floor_, lim, larsen_n)
-                  : limiter_fast(lim, larsen_n, __fdividef(gmax, fmaxf(s_ * pt, floor_))) * __fdividef(1.0f, s_);
+                  : limiter_fast(lim, larsen_n, gmax * fast_rcp(fmaxf(s_ * pt, floor_))) * fast_rcp(s_);
         const ff S = ff_S(T, Dp);
         // delta is a correction: its rounding does not move the fixed point
-        delta = __fdividef(__fadd_rn(S.hi, S.lo), ff_den(T, ah, Dp));
+        delta = __fadd_rn(S.hi, S.lo) * fast_rcp(ff_den(T, ah, Dp));
     }
     const ff nw = ff_add_f(ff{p0, p0lo}, __fmul_rn(omega, delta));
     phi[o.own] = nw.hi;
