@@ -896,11 +896,13 @@ struct Controller {
     double recent[kFlatWindowMax + 1] = {};   // residuals of the last checks of this phase
     int nrecent = 0;
     // Windows of the decisions below, in checks.  The constants above are
-    // checks at 256 iterations per check on a 128-voxel edge; a solve keeps
-    // the same windows in iterations per voxel of its largest edge, i.e.
-    // 2 n / check_every checks per constant (never fewer than the constant),
-    // so a shorter check interval or a larger grid does not make it give up
-    // sooner.  The FP64 sweeps that end a MIXED solve keep the constants.
+    // checks at 256 iterations per check on a 128-voxel edge; a plain SOR
+    // solve keeps the same windows in iterations per voxel of its largest
+    // edge, i.e. 2 n / check_every checks per constant (never fewer than the
+    // constant), so a shorter check interval or a larger grid does not make it
+    // give up sooner.  An Anderson-mixed solve, which progresses many times
+    // faster per iteration, and the FP64 sweeps that end a MIXED solve keep
+    // the constants.
     int stall_w = kStallChecks, switch_w = kSwitchChecks, slow_w = kSlowDivergeChecks, flat_w = kFlatWindow;
 
     void scale_windows(int n, int check_every) {
@@ -1614,7 +1616,7 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
     FLD_CK(cudaEventRecord(g->ev0, g->stream));
     Controller ctl;
     ctl.precision = p->precision;
-    ctl.scale_windows(std::max(g->nx, std::max(g->ny, g->nz)), ce);
+    if (p->anderson <= 1) ctl.scale_windows(std::max(g->nx, std::max(g->ny, g->nz)), ce);
     ctl.tol = p->tol;
     ctl.sw = sw;
     ctl.fam = fam;
@@ -1995,7 +1997,7 @@ fld_status fld_server_add(fld_server s, fld_grid g, long long tag) {
     if (e.am > 0 && (st = ensure_anderson(g, e.am)) != FLD_OK) return st;
     if ((st = preallocate(g, p)) != FLD_OK) return st;
     e.ctl.precision = p->precision;
-    e.ctl.scale_windows(std::max(g->nx, std::max(g->ny, g->nz)), e.ce);
+    if (p->anderson <= 1) e.ctl.scale_windows(std::max(g->nx, std::max(g->ny, g->nz)), e.ce);
     e.ctl.tol = p->tol;
     e.ctl.sw = s->sw;
     e.ctl.fam = e.fam;

@@ -643,17 +643,10 @@ __device__ __forceinline__ void pass_ff_body(const Layout &L, const float *__res
 #pragma unroll
     for (int r = 0; r < (ROUNDS > 0 ? ROUNDS : 64); ++r) {
         if (ROUNDS == 0 && r >= local_iters) break;
-        // the rounds before the last only move the point at which D_p is
-        // taken: the bulk sweeps' fast limiter serves there; the last round's
-        // D_p, which is stored, is the correctly rounded one the residual
-        // evaluates
-        const bool last = ROUNDS > 0 ? r == ROUNDS - 1 : r == local_iters - 1;
-        const float pt = __fadd_rn(p0, delta);
-        Dp = last ? D_of_f(gmax, s_, pt, floor_, lim, larsen_n)
-                  : limiter_fast(lim, larsen_n, gmax * fast_rcp(fmaxf(s_ * pt, floor_))) * fast_rcp(s_);
+        Dp = D_of_f(gmax, s_, __fadd_rn(p0, delta), floor_, lim, larsen_n);
         const ff S = ff_S(T, Dp);
         // delta is a correction: its rounding does not move the fixed point
-        delta = __fadd_rn(S.hi, S.lo) * fast_rcp(ff_den(T, ah, Dp));
+        delta = __fdividef(__fadd_rn(S.hi, S.lo), ff_den(T, ah, Dp));
     }
     const ff nw = ff_add_f(ff{p0, p0lo}, __fmul_rn(omega, delta));
     phi[o.own] = nw.hi;
