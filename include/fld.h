@@ -175,7 +175,10 @@ typedef struct {
                              The fixed point is the same; SOR's slow smooth
                              error is removed much faster.  The history restarts
                              after the warm-up, at precision switches and when
-                             the safeguard returns to its best state.  Costs
+                             the safeguard returns to its best state.  If the
+                             mixed iteration stalls above tol, the solve returns
+                             to its best state and continues with plain sweeps
+                             (fld_solve, batch and server alike).  Costs
                              12 bytes per voxel per slot plus 8.  Red-black
                              scheme only (mixed Jacobi sweeps, whose error
                              modes near -1 the mix amplifies, diverged on the
@@ -243,7 +246,9 @@ typedef struct {
     double ms_coarse;      /* nested: their device time (included in ms)          */
     long long updates_coarse; /* nested: their voxel updates                      */
     int anderson_steps;    /* anderson: blocks whose successor started from a mix */
-    int anderson_resets;   /* anderson: history restarts (ill-conditioned weights) */
+    int anderson_resets;   /* anderson: history restarts (ill-conditioned weights),
+                              plus 1 if the mixed iteration stalled above tol and
+                              the solve went on without mixing                */
     int iterations_fp64;   /* MIXED with fp64_verify: FP64 sweeps after the
                               float-float phase (counted in iterations too)   */
     double ms_sweep_fp64;  /* device time inside those sweeps                 */

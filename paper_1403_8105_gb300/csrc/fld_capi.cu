@@ -1675,6 +1675,7 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
     double gram[kAndersonMax][kAndersonMax] = {};
     int acount = 0;          // blocks collected since the history (re)started
     bool have_x = false;     // the Anderson x holds the state the next block starts from
+    bool mix_off = false;    // mixing given up after a stall: plain sweeps from the best state
     auto state_ptrs = [&](float **hi, float **lo, double **p64) {
         const bool d = fam == FAM_F64;
         *hi = d ? nullptr : g->f.phi;
@@ -1683,7 +1684,7 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
     };
     while (outcome == FLD_ERR_NOT_CONVERGED && it < p->max_iters) {
         const int k = block_len(it, check_len(fam, p->precision, ce), p->max_iters, warm);
-        const bool mixing = am > 0 && it >= warm;
+        const bool mixing = am > 0 && it >= warm && !mix_off;
         if (mixing && !have_x) {
             float *hi, *lo;
             double *p64;
@@ -1717,7 +1718,26 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
             have_x = false;
             break;
         case ACT_DIVERGED: outcome = FLD_ERR_DIVERGED; break;
-        case ACT_STALLED: stalled = true; break;
+        case ACT_STALLED:
+            if (am > 1 && !mix_off && it < p->max_iters) {
+                // the mixed iteration stalled above tol: continue with plain
+                // sweeps (and the plain solve's windows) from the best state
+                if ((st = snapshot(g, snap_fam, false)) != FLD_OK) return st;
+                fam = snap_fam;
+                ctl.fam = fam;
+                set_valid(g, fam);
+                g->lo_live = snap_lo_live;
+                rel = ctl.best;
+                mix_off = true;
+                have_x = false;
+                if (fam != FAM_F64) ctl.scale_windows(std::max(g->nx, std::max(g->ny, g->nz)), ce);
+                ctl.backoffs = 0;   // a fresh omega back-off budget for the plain sweeps
+                ctl.begin_phase();
+                ++res.anderson_resets;
+            } else {
+                stalled = true;
+            }
+            break;
         case ACT_SAVE:
             if ((st = save()) != FLD_OK) return st;
             break;
@@ -1822,6 +1842,7 @@ struct ServerEntry {
     double gram[kAndersonMax][kAndersonMax] = {};
     int acount = 0;
     bool have_x = false;
+    bool mix_off = false;         // mixing given up after a stall
 };
 
 namespace {
@@ -2073,7 +2094,7 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
             e.g->stream = s->side[i % nside];
             // Anderson: after the warm-up each block starts from the mix of
             // the last am images (the history starts from the state here)
-            mixing[i] = e.am > 0 && e.res.iterations >= e.warm;
+            mixing[i] = e.am > 0 && e.res.iterations >= e.warm && !e.mix_off;
             if (mixing[i] && !e.have_x) {
                 float *hi, *lo;
                 double *p64;
@@ -2177,7 +2198,25 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
                 }
                 break;
             case ACT_DIVERGED: retire.push_back({i, {FLD_ERR_DIVERGED, rel}}); break;
-            case ACT_STALLED: retire.push_back({i, {FLD_ERR_NOT_CONVERGED, rel}}); break;
+            case ACT_STALLED:
+                if (e.am > 1 && !e.mix_off && e.res.iterations < p->max_iters) {
+                    // as fld_solve: plain sweeps from the best state
+                    if ((st = snapshot(g, e.snap_fam, false)) != FLD_OK) return st;
+                    e.fam = e.snap_fam;
+                    e.ctl.fam = e.fam;
+                    set_valid(g, e.fam);
+                    g->lo_live = e.snap_lo;
+                    e.res.rel_residual = rel = e.ctl.best;
+                    e.mix_off = true;
+                    e.have_x = false;
+                    if (e.fam != FAM_F64) e.ctl.scale_windows(std::max(g->nx, std::max(g->ny, g->nz)), e.ce);
+                    e.ctl.backoffs = 0;
+                    e.ctl.begin_phase();
+                    ++e.res.anderson_resets;
+                } else {
+                    retire.push_back({i, {FLD_ERR_NOT_CONVERGED, rel}});
+                }
+                break;
             case ACT_SAVE:
                 if ((st = snapshot(g, e.fam, true)) != FLD_OK) return st;
                 e.snap_fam = e.fam;
