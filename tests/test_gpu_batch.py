@@ -63,12 +63,20 @@ def test_batch_equals_solo_solves_bitwise():
 def test_batch_matches_oracle_fixed_points():
     p = fld.params(limiter="kershaw", precision="mixed", tol=1e-7, check_every=32, max_iters=200000)
     ins = _inputs()[:3]
-    grids = [_grid(sig, alb, h, 0) for sig, alb, h in ins]
+    # the oracle's bake of each grid's light, given to both sides
+    qs = [oracle.bake_directional(sig, alb, h, (0.0, 0.0, -1.0), 1.0).astype(np.float32).astype(np.float64)
+          for sig, alb, h in ins]
+    grids = []
+    for (sig, alb, h), q in zip(ins, qs):
+        nz, ny, nx = sig.shape
+        g = fld.Grid(nx, ny, nz, h)
+        g.set_medium(sig, alb)
+        g.set_source(q.astype(np.float32))
+        grids.append(g)
     try:
         st, rs = fld.fld_solve_batch(grids, p)
         assert st == fld.FLD_OK
-        for (sig, alb, h), g in zip(ins, grids):
-            q = g.get_source().astype(np.float64)
+        for (sig, alb, h), g, q in zip(ins, grids, qs):
             ref = oracle.make_problem(sig, alb, q, h, limiter="kershaw", omega=1.6, local_iters=2)
             oracle.init_state(ref)
             it, rel, _ = oracle.solve(ref, tol=1e-11, max_iters=400000, check_every=20)

@@ -1,7 +1,9 @@
 """Full-size checks on the 128^3 cloud (the benchmark workload), in the
 benchmark's launch configuration: properties the oracle can check at any size
 (its FP64 residual of the GPU solution, |E| <= phi, positivity, per-voxel
-residuals computed one by one) and one-iteration parity from a shared state."""
+residuals computed one by one), one-iteration parity from a shared seeded
+state, and sampled pixels of the full-size render.  The source is the oracle's
+bake, given to the GPU grid; no oracle input comes from the GPU."""
 import numpy as np
 import pytest
 
@@ -22,12 +24,25 @@ INNER = (slice(1, -1),) * 3
 @pytest.fixture(scope="module")
 def c2():
     case = fld_inputs.cloud_case(N, seed=0, albedo=0.95)
+    j = oracle.bake_directional(case.sigma_t, case.alb, case.h, (0.0, 0.0, -1.0), 1.0).astype(np.float32)
     g = fld.Grid(N, N, N, case.h)
     g.set_medium(case.sigma_t, case.alb)
-    g.bake_directional((0.0, 0.0, -1.0), 1.0)
-    j = g.get_source()
+    g.set_source(j)
     yield case, g, j
     g.close()
+
+
+def _seeded_state(seed):
+    """A smooth positive phi (a product of cosines over the padded grid) and a
+    positive D, both seeded: a state for one-iteration parity and the render."""
+    rng = np.random.default_rng(seed)
+    ax = [np.linspace(0.0, 1.0, N + 2)] * 3
+    kz, ky, kx = rng.uniform(1.0, 3.0, 3)
+    z, y, x = np.meshgrid(*ax, indexing="ij")
+    phi = 0.05 + np.cos(kx * x) ** 2 * np.cos(ky * y) ** 2 * np.cos(kz * z) ** 2
+    phi *= 1.0 + 0.05 * rng.standard_normal(phi.shape)
+    D = rng.uniform(0.002, 0.3, phi.shape)
+    return np.abs(phi), D
 
 
 def test_converged_solution_satisfies_the_fp64_discrete_equation(c2):
@@ -59,14 +74,9 @@ def test_converged_solution_satisfies_the_fp64_discrete_equation(c2):
 
 
 def test_one_iteration_parity_at_full_size(c2):
-    # From a shared state 2048 sweeps into the solve.  (Earlier, SOR's
-    # overshoot leaves phi transiently negative in a few vacuum cells, where
-    # the floor of Eq. 35 makes D jump as phi crosses zero and single and
-    # double precision take different, equally valid, updates.)
+    # from a seeded smooth positive state, in the bench's launch configuration
     case, g, j = c2
-    p = fld.params(limiter="lp", precision="mixed", tol=0.0, check_every=2048, max_iters=2048, fp32_switch=1e30)
-    g.solve(p, check=False)                     # a cold start and 2048 sweeps
-    phi0, D0 = g.get_state()
+    phi0, D0 = _seeded_state(17)
     D0 = D0.astype(np.float32).astype(np.float64)
     ref = oracle.make_problem(case.sigma_t, case.alb, j.astype(np.float64), case.h, limiter="lp",
                               omega=1.93, local_iters=2)
@@ -83,16 +93,15 @@ def test_one_iteration_parity_at_full_size(c2):
 
 
 def test_render_at_full_size_matches_oracle_pixels(c2):
-    # the bench's 1024^2 view of the solved 128^3 cloud, sampled pixels
-    # rendered one by one by the oracle from the same fields
+    # the bench's 1024^2 view of the 128^3 cloud, sampled pixels rendered one
+    # by one by the oracle from the same fields
     case, g, j = c2
-    p = fld.params(limiter="lp", precision="mixed", tol=1e-6, check_every=256, max_iters=600000)
-    r = g.solve(p)
-    assert r.status == fld.FLD_OK, r.as_dict()
     cam = dict(eye=(0.5, 1.1, -1.3), target=(0.5, 0.45, 0.5), up=(0.0, 1.0, 0.0), fov_deg=40.0, width=1024,
                height=1024, background=0.05)
+    # the render of a seeded phi (the oracle's renderer reads no GPU output)
+    phi, D = _seeded_state(5)
+    g.set_state(phi, D)
     rad, codes = g.render(fld.camera(**cam), exposure=2.0, codes=True)
-    phi, _ = g.get_state()
     rng = np.random.default_rng(3)
     pix = [(int(x), int(y)) for x, y in rng.integers(0, 1024, size=(300, 2))]
     pix += [(512, 512), (0, 0), (1023, 1023), (300, 700)]
@@ -102,7 +111,8 @@ def test_render_at_full_size_matches_oracle_pixels(c2):
     assert np.abs(got - want).max() <= 1e-4 * scale
     # the cloud covers part of the view (seen from below it is darker than the background)
     assert (np.abs(rad - cam["background"]) > 0.01 * cam["background"]).mean() > 0.05
-    # tone map: the GPU's 8-bit codes are the gamma compression of its own radiance
-    mine = oracle.tonemap(rad.astype(np.float64), exposure=2.0)
-    assert np.abs(mine.astype(int) - codes.astype(int)).max() <= 1
-    assert (mine != codes).mean() < 1e-3
+    # tone map at the sampled pixels: the oracle's codes of its own radiance
+    # (+-1 where the two radiances straddle a half-integer code boundary)
+    mine = oracle.tonemap(want, exposure=2.0)
+    got_codes = np.array([codes[y, x] for x, y in pix])
+    assert np.abs(mine.astype(int) - got_codes.astype(int)).max() <= 1

@@ -1,6 +1,7 @@
 """GPU parity of the primary ray march (fld_render, Sec. 3) against the
-oracle's renderer on the same fields: the grid's medium, its source field and
-its solved phi."""
+oracle's renderer on the same fields: the medium, the oracle's baked source
+and the oracle's solved phi, given to the GPU grid (set_source / set_state),
+so nothing the oracle reads comes from the GPU."""
 import math
 
 import numpy as np
@@ -18,27 +19,30 @@ if not torch.cuda.is_available():  # pragma: no cover
 
 
 def solved_cloud(n, seed, shape=None):
+    """A GPU grid holding the oracle's source and the oracle's fixed point."""
     nz, ny, nx = shape or (n, n, n)
     sig, alb = fld_inputs.cloud_medium(nx, seed=seed, albedo=0.9, ny=ny, nz=nz)
     h = 1.0 / max(nx, ny, nz)
+    q = oracle.bake_directional(sig, alb, h, (0.3, -0.2, -1.0), 1.0)
+    ref = oracle.make_problem(sig, alb, q, h, omega=1.6, local_iters=2)
+    oracle.init_state(ref)
+    _, rel, _ = oracle.solve(ref, tol=1e-9, max_iters=200000, check_every=20)
+    assert rel <= 1e-9
     g = fld.Grid(nx, ny, nz, h)
     g.set_medium(sig, alb)
-    g.bake_directional((0.3, -0.2, -1.0), 1.0)
-    r = g.solve(fld.params(tol=1e-6, check_every=64, max_iters=200000))
-    assert r.status == fld.FLD_OK, r.as_dict()
-    return g, sig, alb, h
+    g.set_source(q.astype(np.float32))
+    g.set_state(ref.phi, ref.D)
+    return g, sig, alb, h, q.astype(np.float32).astype(np.float64), ref.phi
 
 
 @pytest.mark.parametrize("shape", [(24, 24, 24), (17, 23, 29)])
 @pytest.mark.parametrize("step_frac,t_min", [(0.5, 1e-6), (0.37, 0.0), (1.3, 1e-3)])
 def test_render_matches_oracle(shape, step_frac, t_min):
-    g, sig, alb, h = solved_cloud(0, 8, shape)
+    g, sig, alb, h, q, phi = solved_cloud(0, 8, shape)
     try:
         cam = dict(eye=(0.35, 1.2, -1.1), target=(0.5, 0.4, 0.55), up=(0.1, 1.0, 0.0), fov_deg=45.0, width=48,
                    height=40, step=step_frac * h, background=0.3, t_min=t_min)
         rad, _ = g.render(fld.camera(**cam))
-        phi, _ = g.get_state()
-        q = g.get_source().astype(np.float64)
     finally:
         g.close()
     want = oracle.render(sig, alb, q, phi, h, **cam)
@@ -64,7 +68,7 @@ def test_homogeneous_axis_ray_closed_form():
 
 
 def test_device_outputs_codes_and_errors():
-    g, sig, alb, h = solved_cloud(16, 2)
+    g, sig, alb, h, q, phi = solved_cloud(16, 2)
     try:
         cam = fld.camera(eye=(0.5, 0.5, -1.5), target=(0.5, 0.5, 0.5), width=33, height=17, background=0.1)
         rad, codes = g.render(cam, exposure=3.0, gamma=2.2, codes=True)
@@ -74,7 +78,11 @@ def test_device_outputs_codes_and_errors():
         torch.cuda.synchronize()
         assert np.array_equal(drad.cpu().numpy(), rad)
         assert np.array_equal(dcod.cpu().numpy(), codes)
-        mine = oracle.tonemap(rad.astype(np.float64), exposure=3.0, gamma=2.2)
+        # the codes against the oracle's tone map of its own radiance: +-1 where
+        # the two radiances straddle a half-integer code boundary
+        want = oracle.render(sig, alb, q, phi, h, eye=(0.5, 0.5, -1.5), target=(0.5, 0.5, 0.5), width=33,
+                             height=17, background=0.1)
+        mine = oracle.tonemap(want, exposure=3.0, gamma=2.2)
         assert np.abs(mine.astype(int) - codes.astype(int)).max() <= 1
         for bad in (dict(width=0), dict(fov_deg=180.0), dict(eye=(0.5, 0.5, 0.5)), dict(up=(0.0, 0.0, 1.0))):
             kw = dict(eye=(0.5, 0.5, -1.5), target=(0.5, 0.5, 0.5), width=8, height=8)
@@ -100,10 +108,10 @@ def test_quarter_resolution_pipeline_matches_oracle():
     sig, alb = fld_inputs.cloud_medium(nx, seed=12, albedo=0.9, ny=ny, nz=nz)
     h = 1.0 / max(nx, ny, nz)
     cx, cy, cz = (nx + f - 1) // f, (ny + f - 1) // f, (nz + f - 1) // f
+    q = oracle.bake_directional(sig, alb, h, (0.2, -0.3, -1.0), 1.0).astype(np.float32).astype(np.float64)
     with fld.Grid(nx, ny, nz, h) as g, fld.Grid(cx, cy, cz, f * h) as c:
         g.set_medium(sig, alb)
-        g.bake_directional((0.2, -0.3, -1.0), 1.0)
-        q = g.get_source().astype(np.float64)
+        g.set_source(q.astype(np.float32))
         g.downsample_to(c, f)
         qc_gpu = c.get_source()
         r = c.solve(fld.params(tol=1e-7, check_every=32, max_iters=200000))
@@ -111,17 +119,18 @@ def test_quarter_resolution_pipeline_matches_oracle():
         phic, _ = c.get_state()
         cam = dict(eye=(0.4, 1.1, -1.2), target=(0.5, 0.4, 0.4), fov_deg=45.0, width=40, height=32, background=0.2)
         rad, _ = g.render(fld.camera(**cam), phi_grid=c)
+    # the oracle's own chain: downsample, coarse fixed point, upsample, render
     stc, alc, qc = oracle.downsample(sig, alb, q, f)
     assert np.abs(qc_gpu - qc).max() <= 1e-6 * np.abs(qc).max()
-    ref = oracle.make_problem(stc.astype(np.float32), alc.astype(np.float32), qc_gpu.astype(np.float64), f * h,
-                              omega=1.6, local_iters=2)
+    ref = oracle.make_problem(stc.astype(np.float32), alc.astype(np.float32), qc.astype(np.float32).astype(np.float64),
+                              f * h, omega=1.6, local_iters=2)
     oracle.init_state(ref)
     it, rel, _ = oracle.solve(ref, tol=1e-11, max_iters=400000, check_every=20)
     assert rel <= 1e-11
     inner = (slice(1, -1),) * 3
     err = np.linalg.norm(phic[inner] - ref.phi[inner]) / np.linalg.norm(ref.phi[inner])
     assert err <= 1e-5
-    up = oracle.upsample(phic, (nz, ny, nx), h, f)
+    up = oracle.upsample(ref.phi, (nz, ny, nx), h, f)
     want = oracle.render(sig, alb, q, up, h, **cam)
     assert np.abs(rad - want).max() <= 2e-5 * np.abs(want).max()
 
