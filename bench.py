@@ -1211,7 +1211,12 @@ def run_sweeps(args):
                         e1.synchronize()
                         us = 1e3 * e0.elapsed_time(e1) / args.iters
                         ach = 28.0 * n ** 3 / (us * 1e-6) / 1e9
-                        name = f"launched, {cells} unknowns per thread" if depth < 0 else f"blocked T={depth}"
+                        if depth >= 0:
+                            name = f"blocked T={depth}"
+                        elif fam == "ff":
+                            name = "launched, 1 unknown per thread"
+                        else:
+                            name = f"launched, {cells} unknowns per thread"
                         out[f"{n} {fam} {name}"] = {
                             "us_per_iteration": round(us, 3), "voxel_updates_per_s": n ** 3 / (us * 1e-6),
                             "algorithmic_GBps": round(ach, 1), "frac_of_measured_peak": round(ach / peak, 4)}
