@@ -105,6 +105,9 @@ def parse_args():
                          "batched in shared launches vs one after another")
     ap.add_argument("--count", type=int, default=16, help="batch workload: number of solves")
     ap.add_argument("--sizes", default="32,48,64,96", help="batch workload: edge lengths drawn from")
+    ap.add_argument("--batch-modes", default="sequential,batched,batched_multi,sequential_anderson,batched_anderson",
+                    help="batch workload: arms to run (sequential, batched, batched_multi, sequential_anderson, "
+                         "batched_anderson, batched_anderson_multi; 'multi': batch_launch = 1)")
     ap.add_argument("--rate", type=float, default=0.0, help="serve workload: Poisson arrival rate (req/s; 0: profile)")
     ap.add_argument("--requests", type=int, default=0, help="serve workload: number of requests (0: profile)")
     ap.add_argument("--serve-profile", choices=["stated", "scaled"], default="stated",
@@ -708,10 +711,13 @@ def run_batch(args):
 
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {}
-    modes = ("sequential", "batched", "sequential_anderson", "batched_anderson")
+    modes = tuple(m for m in args.batch_modes.split(",") if m)
     for mode in modes:
         grids = setup()
-        pm = pa if mode.endswith("anderson") else p
+        pm = pa if "anderson" in mode else p
+        if mode.endswith("multi"):
+            # one multi-grid launch per colour pass for the grids of a table
+            pm = fld.params(**{**{k: getattr(pm, k) for k, _ in pm._fields_}, "batch_launch": 1})
         with torch.cuda.stream(stream):
             e0.record(stream)
             if mode.startswith("sequential"):
@@ -737,20 +743,22 @@ def run_batch(args):
             out[mode]["latency_ms_p99"] = float(np.percentile(lat, 99))
         for g in grids:
             g.close()
+    head = out.get("batched") or next(iter(out.values()))
     line = {
-        "metric": METRIC, "value": out["batched"]["value"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
-        "ms_per_step": out["batched"]["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "metric": METRIC, "value": head["value"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": head["ms"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 (float-float correction sweeps)", "data": "synthetic",
         "config": {"workload": f"batch of {args.count} independent solves, edges from {sizes}, per-solve fBm "
                                f"seed, albedo U[0.8,0.99], point or oblique light, LP, rel. residual {args.tol:g}",
                    "sizes": [sp["n"] for sp in specs]},
-        "batched": out["batched"], "sequential": out["sequential"],
-        "sequential_anderson": out["sequential_anderson"], "batched_anderson": out["batched_anderson"],
+        **out,
         "anderson": {"m": args.anderson_m, "sweeps_per_block": args.anderson_check},
-        "speedup_vs_sequential": out["sequential"]["ms"] / out["batched"]["ms"],
-        "speedup_batched_anderson_vs_sequential_plain": out["sequential"]["ms"] / out["batched_anderson"]["ms"],
-        "speedup_batched_anderson_vs_sequential_anderson": out["sequential_anderson"]["ms"] / out["batched_anderson"]["ms"],
     }
+    for a, b in (("sequential", "batched"), ("sequential", "batched_anderson"),
+                 ("sequential_anderson", "batched_anderson"), ("batched", "batched_multi"),
+                 ("batched_anderson", "batched_anderson_multi")):
+        if a in out and b in out:
+            line[f"speedup_{b}_vs_{a}"] = out[a]["ms"] / out[b]["ms"]
     print(json.dumps(line), flush=True)
 
 

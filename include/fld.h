@@ -222,6 +222,21 @@ typedef struct {
                              every own field and neighbour row; same bits);
                              0 (default): 2, or the autotuner's choice when
                              temporal_depth is 0                               */
+    int batch_launch;     /* fld_solve_batch and fld_server.  0 (default): each
+                             grid replays its own block graph (the one fld_solve
+                             uses) on a stream of a pool of 16, so independent
+                             grids run concurrently.  1: in each step the grids
+                             in single-precision or hi/lo red-black sweeps whose
+                             blocks have the same length run as multi-grid
+                             launches: each colour pass is one launch of a
+                             persistent kernel whose CTAs walk the work items of
+                             every grid in a device table (up to 128 grids a
+                             table, up to 8 tables on their own streams), and a
+                             block of k iterations is one CUDA graph of 2k such
+                             launches, captured once per table and k and replayed
+                             whatever grids the table holds.  The same bits
+                             either way; on GB300 the per-grid graphs measured
+                             faster.  Not in the paper.                        */
 } fld_solve_params;
 
 typedef struct {

@@ -52,7 +52,7 @@ class SolveParams(ctypes.Structure):
         ("phi_b", ctypes.c_double), ("D_b", ctypes.c_double), ("warmup_iters", ctypes.c_int),
         ("medium_bf16", ctypes.c_int), ("scheme", ctypes.c_int), ("nested", ctypes.c_int),
         ("anderson", ctypes.c_int), ("fp64_verify", ctypes.c_int), ("temporal_depth", ctypes.c_int),
-        ("tile_y", ctypes.c_int), ("cells_per_thread", ctypes.c_int),
+        ("tile_y", ctypes.c_int), ("cells_per_thread", ctypes.c_int), ("batch_launch", ctypes.c_int),
     ]
 
 

@@ -161,6 +161,37 @@ struct alignas(16) BatchDesc {
 };
 static_assert(sizeof(BatchDesc) % 16 == 0, "BatchDesc is read with 16-byte loads");
 
+// One grid of a multi-grid colour pass (launch_pass_multi): its layout,
+// fields and pass parameters, and where its work items start.  An item is
+// the 32 x 8 pairs of unknowns a CTA of the solo pair pass covers (one
+// z-plane); the grid's items are numbered x fastest, then y, then z.
+struct alignas(16) SweepDesc {
+    Layout L;
+    float *sp, *ah2, *jh2, *phi, *phlo, *D;
+    const uint16_t *spb, *sab;        // bfloat16 medium, or null
+    float h2, omega, inv2h, floor_, larsen_n;
+    int lim, local_iters;
+    int hl;                           // 0: FP32 sweeps, 1: hi/lo sweeps
+    int first;                        // first item of this grid
+    int bx, by;                       // items per plane in x and y
+    int pad_;
+};
+static_assert(sizeof(SweepDesc) % 16 == 0, "SweepDesc is read with 16-byte loads");
+
+// Grids one multi-grid table holds.
+constexpr int kMultiMaxGrids = 128;
+// Item grid of a layout for the multi-grid pass (the solo pair pass's CTAs).
+void multi_dims(const Layout &L, int *bx, int *by);
+// One colour pass of every grid in descs[0 .. counts[0]) (counts[1] items in
+// all), all of family hl (0: FP32, 1: hi/lo) with medium bf16, limiter lim
+// and local_iters rounds, each with its own omega and state: a persistent
+// grid of nctas CTAs walks the items.  Both counts are read on the device, so
+// a captured graph of these launches serves any table contents.
+cudaError_t launch_pass_multi(const SweepDesc *descs, const int *counts, int hl, int bf16, int lim, int local_iters,
+                              int colour, int nctas, cudaStream_t s);
+// CTAs of that persistent pass resident at once on a device of nsm SMs.
+int multi_ctas(int nsm, int hl, int bf16, int lim, int local_iters);
+
 // Batched residual: per grid g, result[2g] = sum (R h^2)^2, result[2g+1] = sum (j h^2)^2,
 // summed in the same order as launch_residual.
 cudaError_t launch_residual_batch(const BatchDesc *descs, const int *cta_grid, int nctas, int ngrids,

@@ -613,6 +613,66 @@ __global__ void __launch_bounds__(128) k_pass4(Layout L, const float *__restrict
                                blockIdx.y * blockDim.y + threadIdx.y + 1, blockIdx.z + 1);
 }
 
+// Multi-grid colour pass: one launch updates one colour of every grid in a
+// table of SweepDescs.  The CTAs are persistent (all resident) and walk the
+// work items of all grids with a grid-wide stride; item i belongs to the last
+// grid whose first item is <= i (binary search over the firsts, staged in
+// shared memory).  An item is what a CTA of the solo pair pass covers and its
+// unknowns go through tile_f32 / tile_fh with the grid's own parameters, so
+// every grid gets the bits of its solo passes.  The table and both counts
+// are read on the device: one captured graph of these launches serves any
+// set of grids.
+__device__ __forceinline__ SweepDesc load_sweep_desc(const SweepDesc *__restrict__ p) {
+    SweepDesc d;
+    const int4 *src = reinterpret_cast<const int4 *>(p);
+    int4 *dst = reinterpret_cast<int4 *>(&d);
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(SweepDesc) / 16); ++i) dst[i] = __ldg(src + i);
+    return d;
+}
+
+constexpr int kMultiThreadsX = 32, kMultiThreadsY = 8;
+
+// One instantiation per limiter fast path, medium and family (a table holds
+// grids of one family; limiter and medium are the batch's own).
+template <int LIM, int ROUNDS, bool BF, bool HL>
+__global__ void __launch_bounds__(kMultiThreadsX * kMultiThreadsY, 4)
+    k_pass2_multi(const SweepDesc *__restrict__ descs, const int *__restrict__ counts, int colour) {
+    __shared__ int first[kMultiMaxGrids];
+    pdl_launch_dependents();
+    const int ng = min(__ldg(counts), kMultiMaxGrids), total = __ldg(counts + 1);
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    for (int g = tid; g < ng; g += blockDim.x * blockDim.y) first[g] = __ldg(&descs[g].first);
+    __syncthreads();
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        int lo = 0, hi = ng - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (first[mid] <= item) lo = mid;
+            else hi = mid - 1;
+        }
+        const SweepDesc d = load_sweep_desc(descs + lo);
+        const int local = item - d.first;
+        const int bx = local % d.bx, rest = local / d.bx;
+        const int by = rest % d.by, bz = rest / d.by;
+        if (bz >= d.L.nz) continue;
+        const int t = 2 * (bx * kMultiThreadsX + threadIdx.x);
+        const int J = by * kMultiThreadsY + threadIdx.y + 1;
+        if (HL)
+            tile_fh<LIM, ROUNDS, BF>(d.L, d.sp, d.ah2, d.jh2, d.spb, d.sab, d.h2, d.phi, d.phlo, d.D, colour, d.lim,
+                                     d.larsen_n, d.omega, d.inv2h, d.floor_, d.local_iters, t, J, bz + 1);
+        else
+            tile_f32<LIM, ROUNDS, BF>(d.L, d.sp, d.ah2, d.jh2, d.spb, d.sab, d.h2, d.phi, d.D, colour, d.lim,
+                                      d.larsen_n, d.omega, d.inv2h, d.floor_, d.local_iters, t, J, bz + 1);
+    }
+}
+
+template <bool BF, bool HL>
+auto multi_kernel(int lim, int local_iters) {
+    if (local_iters == 2 && lim == LIM_LP) return k_pass2_multi<LIM_LP, 2, BF, HL>;
+    return k_pass2_multi<-1, 0, BF, HL>;
+}
+
 // Float-float correction pass: phi kept as a hi/lo pair, S summed so the
 // update is accurate to the pair's precision; correctly rounded D (the same
 // function the residual kernel evaluates).
@@ -1284,6 +1344,33 @@ cudaError_t launch_residual_batch(const BatchDesc *descs, const int *cta_grid, i
     k_residual_batch<<<nctas, vox_block(), 0, s>>>(descs, cta_grid, margin, partials);
     k_finalize_batch<<<ngrids, kRedThreads, 0, s>>>(descs, res_count, partials, result);
     return cudaGetLastError();
+}
+
+void multi_dims(const Layout &L, int *bx, int *by) {
+    const dim3 g = pass2_grid(L, dim3(kMultiThreadsX, kMultiThreadsY, 1));
+    *bx = (int)g.x;
+    *by = (int)g.y;
+}
+
+int multi_ctas(int nsm, int hl, int bf16, int lim, int local_iters) {
+    auto k = hl ? (bf16 ? multi_kernel<true, true>(lim, local_iters) : multi_kernel<false, true>(lim, local_iters))
+                : (bf16 ? multi_kernel<true, false>(lim, local_iters) : multi_kernel<false, false>(lim, local_iters));
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kMultiThreadsX * kMultiThreadsY, 0) !=
+            cudaSuccess ||
+        per_sm < 1) {
+        (void)cudaGetLastError();
+        per_sm = 1;
+    }
+    return per_sm * (nsm > 0 ? nsm : 1);
+}
+
+cudaError_t launch_pass_multi(const SweepDesc *descs, const int *counts, int hl, int bf16, int lim, int local_iters,
+                              int colour, int nctas, cudaStream_t s) {
+    if (nctas <= 0) return cudaSuccess;
+    auto k = hl ? (bf16 ? multi_kernel<true, true>(lim, local_iters) : multi_kernel<false, true>(lim, local_iters))
+                : (bf16 ? multi_kernel<true, false>(lim, local_iters) : multi_kernel<false, false>(lim, local_iters));
+    return launch_pdl(k, dim3(nctas), dim3(kMultiThreadsX, kMultiThreadsY, 1), s, descs, counts, colour);
 }
 
 int reduction_blocks(const Layout &L) {

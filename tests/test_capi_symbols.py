@@ -100,7 +100,8 @@ def test_server_checks_its_parameters_before_touching_a_device():
     # the server checks its parameters, which happens before any device call
     import paper_1403_8105_gb300 as fld
     for bad, word in ((dict(anderson=17), "anderson"), (dict(anderson=4, scheme=1), "Anderson"),
-                      (dict(temporal_depth=3), "temporal_depth"), (dict(fp64_verify=2), "fp64_verify")):
+                      (dict(temporal_depth=3), "temporal_depth"), (dict(fp64_verify=2), "fp64_verify"),
+                      (dict(batch_launch=2), "batch_launch")):
         with pytest.raises(fld.FldError) as e:
             fld.fld_server_create(fld.params(**bad))
         assert e.value.status == fld.FLD_ERR_INVALID_ARG

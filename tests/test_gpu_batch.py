@@ -98,3 +98,30 @@ def test_batch_rejects_fp64_and_duplicates():
         with pytest.raises(fld.FldError) as e:
             fld.fld_solve_batch([g, g], fld.params())
         assert e.value.status == fld.FLD_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("limiter,precision,bf16,anderson", [
+    ("lp", "mixed", 0, 0), ("kershaw", "mixed", 0, 0), ("lp", "pair", 1, 0), ("larsen", "fp32", 0, 0),
+    ("lp", "mixed", 0, 4)])
+def test_multi_grid_launches_equal_per_grid_graphs(limiter, precision, bf16, anderson):
+    # batch_launch = 1 runs the grids in FP32 / hi-lo sweeps as one multi-grid
+    # launch per colour pass; it must give every grid the bits, iteration
+    # counts and checks of the per-grid graphs (batch_launch = 0)
+    ins = _inputs()
+    out = {}
+    for mode in (0, 1):
+        p = fld.params(limiter=limiter, precision=precision, tol=1e-7 if precision == "mixed" else 1e-6,
+                       check_every=32, max_iters=200000, medium_bf16=bf16, anderson=anderson, batch_launch=mode)
+        grids = [_grid(sig, alb, h, a % 2) for a, (sig, alb, h) in enumerate(ins)]
+        try:
+            st, rs = fld.fld_solve_batch(grids, p)
+            out[mode] = [(r.status, r.iterations, r.iterations_fp32, r.iterations_mid, r.iterations_corr, r.checks,
+                          r.anderson_steps, g.get_state()[0]) for r, g in zip(rs, grids)]
+        finally:
+            for g in grids:
+                g.close()
+    for a, (x, y) in enumerate(zip(out[0], out[1])):
+        assert x[:7] == y[:7], (a, x[:7], y[:7])
+        assert np.array_equal(x[7], y[7]), a
+    if precision == "mixed":
+        assert all(x[0] == fld.FLD_OK for x in out[1])
