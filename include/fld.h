@@ -171,7 +171,8 @@ typedef struct {
                              point; after a block, the next one starts from
                              sum_i a_i G(x_i), sum a_i = 1, with the weights that
                              minimise |sum_i a_i (G(x_i) - x_i)| (Gram matrix
-                             reduced in FP64 on the device, solved on the host).
+                             reduced on the device, solved on the host; images
+                             and mix in float-float).
                              The fixed point is the same; SOR's slow smooth
                              error is removed much faster.  The history restarts
                              after the warm-up, at precision switches and when

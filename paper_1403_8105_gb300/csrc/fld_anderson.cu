@@ -5,17 +5,24 @@
 // mixing keeps the last m images g_i = G(x_i) and residuals f_i = g_i - x_i
 // and starts the next block from x = sum_i a_i g_i, with the weights a
 // (summing to 1) that minimise |sum_i a_i f_i|.  The weights come from the
-// Gram matrix <f_i, f_j>, reduced here in FP64 and solved on the host.
+// Gram matrix <f_i, f_j>, reduced here and solved on the host.
 //
 // Per element of a padded field (both colours, ghosts and row padding
 // included -- there f is 0 and every g_i is the same value):
-//   k_and_collect: g = phi (hi + lo, or FP64), f = g - x_cur, stores g in its
-//                  slot (FP64) and f (FP32), and accumulates <f, f_j> for
-//                  every occupied slot j;
-//   k_and_reduce:  sums the per-CTA partials in a fixed order;
-//   k_and_mix:     x = g_s + sum_{j != s} a_j (g_j - g_s), written back as
-//                  phi (hi/lo, float, or FP64) and as the next x_cur.
-// The difference form leaves ghosts and padding exactly unchanged.
+//   k_and_collect: g = phi (hi/lo pair, or FP64 split into one), f = g - x_cur
+//                  rounded to float, stores g in its slot (float-float) and f
+//                  (FP32), and accumulates <f, f_j> for every occupied slot j
+//                  (exact products, float-float sums per thread and warp, FP64
+//                  across warps and CTAs);
+//   k_and_reduce:  sums the per-CTA partials in a fixed order (one warp per
+//                  slot, strided lanes, then a fixed shuffle tree);
+//   k_and_mix:     x = g_s + sum_{j != s} a_j (g_j - g_s) in float-float,
+//                  written back as phi (hi/lo, float, or FP64) and as the next
+//                  x_cur.
+// All per-element arithmetic runs on the FP32 pipes as float-float (about 48
+// bits): GB300 issues FP64 at a small fraction of its FP32 rate, and in FP64
+// these passes cost a third of an Anderson-mixed solve.  The difference form
+// leaves ghosts and padding exactly unchanged (every g_j - g_s is 0 there).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,98 +34,124 @@ namespace {
 constexpr int kAndThreads = 256;
 
 struct SlotPtrs {
-    const double *g[kAndersonMax];
+    const float2 *g[kAndersonMax];
     const float *f[kAndersonMax];
 };
 
+// the mixing weights split into float-float pairs (on the host)
 struct Coef {
-    double a[kAndersonMax];
+    float hi[kAndersonMax], lo[kAndersonMax];
 };
 
-__device__ __forceinline__ double state_at(const float *hi, const float *lo, const double *p64, long long e) {
-    if (p64) return p64[e];
-    return lo ? (double)hi[e] + (double)lo[e] : (double)hi[e];
+__device__ __forceinline__ ff ld_ff(const float2 *p, long long e) {
+    const float2 v = p[e];
+    return ff{v.x, v.y};
+}
+
+// The state at element e as a float-float pair: hi/lo (lo null: float), or
+// FP64 split (FP64 sweeps only).
+__device__ __forceinline__ ff state_at(const float *hi, const float *lo, const double *p64, long long e) {
+    if (p64) {
+        const double d = p64[e];
+        const float h = (float)d;
+        return ff{h, (float)(d - (double)h)};
+    }
+    return ff{hi[e], lo ? lo[e] : 0.0f};
+}
+
+// a * b for float-float a, b (the low-order cross term dropped: ~2^-48)
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const ff p = two_prod(a.hi, b.hi);
+    const float e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
+    return fast_two_sum(p.hi, e);
 }
 
 __global__ void __launch_bounds__(kAndThreads) k_and_capture(int n, const float *__restrict__ hi,
                                                               const float *__restrict__ lo,
                                                               const double *__restrict__ p64,
-                                                              double *__restrict__ x_cur) {
-    for (long long e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x)
-        x_cur[e] = state_at(hi, lo, p64, e);
+                                                              float2 *__restrict__ x_cur) {
+    for (long long e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const ff v = state_at(hi, lo, p64, e);
+        x_cur[e] = make_float2(v.hi, v.lo);
+    }
 }
 
 __global__ void __launch_bounds__(kAndThreads) k_and_collect(int n, const float *__restrict__ hi,
                                                               const float *__restrict__ lo,
                                                               const double *__restrict__ p64,
-                                                              const double *__restrict__ x_cur, SlotPtrs sl,
-                                                              double *__restrict__ g_out, float *__restrict__ f_out,
+                                                              const float2 *__restrict__ x_cur, SlotPtrs sl,
+                                                              float2 *__restrict__ g_out, float *__restrict__ f_out,
                                                               int w, int s, double *__restrict__ part) {
-    double acc[kAndersonMax];
+    ff acc[kAndersonMax];
 #pragma unroll
-    for (int j = 0; j < kAndersonMax; ++j) acc[j] = 0.0;
+    for (int j = 0; j < kAndersonMax; ++j) acc[j] = ff{0.0f, 0.0f};
     for (long long e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const double g = state_at(hi, lo, p64, e);
-        const float f = (float)(g - x_cur[e]);
-        g_out[e] = g;
+        const ff g = state_at(hi, lo, p64, e);
+        const ff d = ff_sub(g, ld_ff(x_cur, e));
+        const float f = __fadd_rn(d.hi, d.lo);
+        g_out[e] = make_float2(g.hi, g.lo);
         f_out[e] = f;
-        const double fd = (double)f;
 #pragma unroll
         for (int j = 0; j < kAndersonMax; ++j) {
-            if (j < w) acc[j] += fd * (double)(j == s ? f : sl.f[j][e]);
+            if (j < w) acc[j] = ff_add(acc[j], two_prod(f, j == s ? f : sl.f[j][e]));
         }
     }
-    // block reduction of every accumulator: warp shuffles, then one value
-    // per warp in shared memory, summed by the first warp in warp order
+    // block reduction of every accumulator: float-float warp shuffles, then
+    // one FP64 value per warp in shared memory, summed by the first threads
+    // in warp order
     __shared__ double red[kAndThreads / 32][kAndersonMax];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
     for (int j = 0; j < kAndersonMax; ++j) {
-        double v = acc[j];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-        if (lane == 0) red[wid][j] = v;
+        if (j >= w) break;
+        ff v = acc[j];
+        for (int o = 16; o > 0; o >>= 1) {
+            const ff u{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+            v = ff_add(v, u);
+        }
+        if (lane == 0) red[wid][j] = (double)v.hi + (double)v.lo;
     }
     __syncthreads();
     if (threadIdx.x < kAndersonMax) {
         double v = 0.0;
-        for (int q = 0; q < kAndThreads / 32; ++q) v += red[q][threadIdx.x];
+        if (threadIdx.x < w)
+            for (int q = 0; q < kAndThreads / 32; ++q) v += red[q][threadIdx.x];
         part[(size_t)blockIdx.x * kAndersonMax + threadIdx.x] = v;
     }
 }
 
-__global__ void k_and_reduce(const double *__restrict__ part, int nblocks, double *__restrict__ out) {
-    const int j = threadIdx.x;
-    if (j >= kAndersonMax) return;
+// one warp per slot j: lane l sums partials l, l + 32, ... in order, then a
+// fixed shuffle tree; the same order for the same number of CTAs
+__global__ void __launch_bounds__(32 * kAndersonMax) k_and_reduce(const double *__restrict__ part, int nblocks,
+                                                                  double *__restrict__ out) {
+    const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double v = 0.0;
-    for (int b = 0; b < nblocks; ++b) v += part[(size_t)b * kAndersonMax + j];
-    out[j] = v;
+    for (int b = lane; b < nblocks; b += 32) v += part[(size_t)b * kAndersonMax + j];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) out[j] = v;
 }
 
 __global__ void __launch_bounds__(kAndThreads) k_and_mix(int n, SlotPtrs sl, int w, int s, Coef c,
                                                           float *__restrict__ hi, float *__restrict__ lo,
-                                                          double *__restrict__ p64, double *__restrict__ x_cur) {
+                                                          double *__restrict__ p64, float2 *__restrict__ x_cur) {
     for (long long e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
-        const double gs = sl.g[s][e];
-        double x = gs;
+        const ff gs = ld_ff(sl.g[s], e);
+        ff acc{0.0f, 0.0f};
 #pragma unroll
         for (int j = 0; j < kAndersonMax; ++j) {
-            if (j < w && j != s) x += c.a[j] * (sl.g[j][e] - gs);
+            if (j < w && j != s) acc = ff_add(acc, ff_mul(ff{c.hi[j], c.lo[j]}, ff_sub(ld_ff(sl.g[j], e), gs)));
         }
+        ff x = ff_add(gs, acc);
         if (p64) {
-            p64[e] = x;
-            x_cur[e] = x;
+            p64[e] = (double)x.hi + (double)x.lo;
+        } else if (lo) {
+            hi[e] = x.hi;
+            lo[e] = x.lo;
         } else {
-            const float h = (float)x;
-            if (lo) {
-                const float l = (float)(x - (double)h);
-                hi[e] = h;
-                lo[e] = l;
-                x_cur[e] = (double)h + (double)l;
-            } else {
-                hi[e] = h;
-                x_cur[e] = (double)h;
-            }
+            hi[e] = x.hi;
+            x.lo = 0.0f;
         }
+        x_cur[e] = make_float2(x.hi, x.lo);
     }
 }
 
@@ -153,14 +186,18 @@ cudaError_t launch_anderson_collect(const AndersonBuffers &b, int n, const float
                                              b.f + (size_t)slot * n, w, slot, b.part);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    k_and_reduce<<<1, 32, 0, s>>>(b.part, nb, b.dots);
+    k_and_reduce<<<1, 32 * kAndersonMax, 0, s>>>(b.part, nb, b.dots);
     return cudaGetLastError();
 }
 
 cudaError_t launch_anderson_mix(const AndersonBuffers &b, int n, int slot, int w, const double *a, float *hi,
                                 float *lo, double *p64, int nsm, cudaStream_t s) {
     Coef c;
-    for (int j = 0; j < kAndersonMax; ++j) c.a[j] = j < w ? a[j] : 0.0;
+    for (int j = 0; j < kAndersonMax; ++j) {
+        const double v = j < w ? a[j] : 0.0;
+        c.hi[j] = (float)v;
+        c.lo[j] = (float)(v - (double)c.hi[j]);
+    }
     k_and_mix<<<and_grid(n, nsm), kAndThreads, 0, s>>>(n, slot_ptrs(b, n, w), w, slot, c, hi, lo, p64, b.x);
     return cudaGetLastError();
 }

@@ -185,9 +185,9 @@ fld_status ensure_anderson(fld_grid_s *g, int m) {
     }
     const size_t n = (size_t)g->L.total;
     AndersonBuffers &b = g->anderson;
-    if (cudaMalloc((void **)&b.g, sizeof(double) * n * m) != cudaSuccess ||
+    if (cudaMalloc((void **)&b.g, sizeof(float2) * n * m) != cudaSuccess ||
         cudaMalloc((void **)&b.f, sizeof(float) * n * m) != cudaSuccess ||
-        cudaMalloc((void **)&b.x, sizeof(double) * n) != cudaSuccess ||
+        cudaMalloc((void **)&b.x, sizeof(float2) * n) != cudaSuccess ||
         cudaMalloc((void **)&b.part, sizeof(double) * kAndersonMax * 4 * (size_t)g->nsm) != cudaSuccess ||
         cudaMalloc((void **)&b.dots, sizeof(double) * kAndersonMax) != cudaSuccess) {
         (void)cudaGetLastError();

@@ -201,13 +201,13 @@ cudaError_t launch_residual_batch(const BatchDesc *descs, const int *cta_grid, i
 void residual_dims(const Layout &L, int *bx, int *by);
 
 // Anderson mixing of blocks of sweeps (fld_anderson.cu): m history slots of
-// g (FP64) and f (FP32) per element of the padded field, the current start
-// point x (FP64), per-CTA partial dot products and their m sums.
+// g (float-float) and f (FP32) per element of the padded field, the current
+// start point x (float-float), per-CTA partial dot products and their m sums.
 constexpr int kAndersonMax = 16;
 struct AndersonBuffers {
-    double *g = nullptr;      // m * total
+    float2 *g = nullptr;      // m * total float-float images
     float *f = nullptr;       // m * total
-    double *x = nullptr;      // total
+    float2 *x = nullptr;      // total: the current start point (float-float)
     double *part = nullptr;   // (4 * SMs) * kAndersonMax
     double *dots = nullptr;   // kAndersonMax
 };
