@@ -59,13 +59,6 @@ __device__ __forceinline__ ff state_at(const float *hi, const float *lo, const d
     return ff{hi[e], lo ? lo[e] : 0.0f};
 }
 
-// a * b for float-float a, b (the low-order cross term dropped: ~2^-48)
-__device__ __forceinline__ ff ff_mul(ff a, ff b) {
-    const ff p = two_prod(a.hi, b.hi);
-    const float e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
-    return fast_two_sum(p.hi, e);
-}
-
 __global__ void __launch_bounds__(kAndThreads) k_and_capture(int n, const float *__restrict__ hi,
                                                               const float *__restrict__ lo,
                                                               const double *__restrict__ p64,

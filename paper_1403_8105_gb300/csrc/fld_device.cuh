@@ -193,6 +193,13 @@ __device__ __forceinline__ ff ff_mul_f(ff a, float b) {
     return fast_two_sum(p.hi, e);
 }
 
+// a * b for float-float a and b (the lo * lo term, ~2^-48 relative, dropped)
+__device__ __forceinline__ ff ff_mul(ff a, ff b) {
+    const ff p = two_prod(a.hi, b.hi);
+    const float e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
+    return fast_two_sum(p.hi, e);
+}
+
 __device__ __forceinline__ double ff_to_d(ff a) { return (double)a.hi + (double)a.lo; }
 
 // a / b rounded to single precision (b > 0): the quotient of the high word,

@@ -53,6 +53,29 @@ __device__ __forceinline__ double block_sum(double v, double *sh) {
     return r;
 }
 
+// Sum over the block of a float-float value per thread, valid in thread 0:
+// float-float shuffles within each warp, then the warps' sums in FP64 in
+// warp order (GB300's FP64 rate is a small fraction of its FP32 rate, so the
+// per-element sums stay on the FP32 pipes).
+__device__ __forceinline__ double block_sum_ff(ff v, double *sh) {
+    const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+    const int nthr = blockDim.x * blockDim.y * blockDim.z;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const ff u{__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)};
+        v = ff_add(v, u);
+    }
+    __syncthreads();
+    if ((tid & 31) == 0) sh[tid >> 5] = ff_to_d(v);
+    __syncthreads();
+    double r = 0.0;
+    if (tid < 32) {
+        r = (tid < (nthr + 31) / 32) ? sh[tid] : 0.0;
+        r = warp_sum(r);
+    }
+    return r;
+}
+
 // Second pass: fixed-order sum of the per-block partial pairs.
 __global__ void __launch_bounds__(kRedThreads) k_finalize(const double *__restrict__ partials, int nblocks,
                                                          double *__restrict__ result) {
@@ -855,9 +878,9 @@ __device__ __forceinline__ void residual_f_terms(const Layout &L, const float *_
                                                  const float *__restrict__ jh2, const float *__restrict__ phi,
                                                  const float *__restrict__ phlo, const float *__restrict__ Df,
                                                  const float *__restrict__ Dghost, int margin, int i, int j, int k,
-                                                 double &r2, double &j2) {
-    r2 = 0.0;
-    j2 = 0.0;
+                                                 ff &r2, ff &j2) {
+    r2 = ff{0.0f, 0.0f};
+    j2 = ff{0.0f, 0.0f};
     if (i >= L.nx || j >= L.ny) return;
     const int q = L.at(i, j, k);
     const int nb[6] = {L.at(i - 1, j, k), L.at(i + 1, j, k), L.at(i, j - 1, k),
@@ -874,12 +897,10 @@ __device__ __forceinline__ void residual_f_terms(const Layout &L, const float *_
     const float ah = ah2[q];
     const FFTerms T = ff_terms(phi[q], phlo ? phlo[q] : 0.0f, ps, ls, Ds, ah, jh2[q]);
     const ff S = ff_S(T, Df[q]);
-    const double Sd = ff_to_d(S);
     const bool in = i >= margin && i < L.nx - margin && j >= margin && j < L.ny - margin && k >= margin &&
                     k < L.nz - margin;
-    r2 = in ? Sd * Sd : 0.0;
-    const double jd = (double)jh2[q];
-    j2 = jd * jd;
+    if (in) r2 = ff_mul(S, S);
+    j2 = two_prod(jh2[q], jh2[q]);
 }
 
 __global__ void __launch_bounds__(256) k_residual_f(Layout L, const float *__restrict__ ah2,
@@ -888,12 +909,12 @@ __global__ void __launch_bounds__(256) k_residual_f(Layout L, const float *__res
                                                     const float *__restrict__ Dghost, int margin,
                                                     double *__restrict__ partials) {
     __shared__ double sh[32];
-    double r2, j2;
+    ff r2f, j2f;
     residual_f_terms(L, ah2, jh2, phi, phlo, Df, Dghost, margin, blockIdx.x * blockDim.x + threadIdx.x,
-                     blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z, r2, j2);
-    r2 = block_sum(r2, sh);
+                     blockIdx.y * blockDim.y + threadIdx.y, blockIdx.z, r2f, j2f);
+    const double r2 = block_sum_ff(r2f, sh);
     __syncthreads();
-    j2 = block_sum(j2, sh);
+    const double j2 = block_sum_ff(j2f, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         const long long b = blockIdx.x + (long long)gridDim.x * (blockIdx.y + (long long)gridDim.y * blockIdx.z);
         partials[2 * b] = r2;
@@ -924,12 +945,12 @@ __global__ void __launch_bounds__(256) k_residual_batch(const BatchDesc *__restr
     const int local = blockIdx.x - d.res_first;
     const int bx = local % d.res_bx, rest = local / d.res_bx;
     const int by = rest % d.res_by, bz = rest / d.res_by;
-    double r2, j2;
+    ff r2f, j2f;
     residual_f_terms(d.L, d.ah2, d.jh2, d.phi, d.mode ? d.phlo : nullptr, d.Df, d.D, margin,
-                     bx * blockDim.x + threadIdx.x, by * blockDim.y + threadIdx.y, bz, r2, j2);
-    r2 = block_sum(r2, sh);
+                     bx * blockDim.x + threadIdx.x, by * blockDim.y + threadIdx.y, bz, r2f, j2f);
+    const double r2 = block_sum_ff(r2f, sh);
     __syncthreads();
-    j2 = block_sum(j2, sh);
+    const double j2 = block_sum_ff(j2f, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) {
         partials[2 * (d.res_slot + local)] = r2;
         partials[2 * (d.res_slot + local) + 1] = j2;
