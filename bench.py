@@ -608,6 +608,19 @@ def cpu_baseline(sig_np, alb_np, n, seconds, acc_n=0, acc_phi=None):
     base = {"value": it * n ** 3 / el, "unit": UNIT, "cores": prob.nthreads, "kind": "oracle",
             "sample": f"{it} iterations of Algorithm 1 (FP64, local_iters=2) on the {n}^3 cloud from the paper's "
                       f"initial state, {el:.1f} s; the oracle's full solve to 1e-6 at omega 1.93 takes 158,976 iterations"}
+    # the same iterations on one host thread (a quarter of the time)
+    cores = prob.nthreads
+    prob.nthreads = 1
+    it1, t0 = 0, time.perf_counter()
+    while True:
+        oracle.rb_iteration(prob, 1)
+        it1 += 1
+        el1 = time.perf_counter() - t0
+        if el1 >= 0.25 * seconds or it1 >= 100000:
+            break
+    prob.nthreads = cores
+    base["single_thread"] = {"value": it1 * n ** 3 / el1, "unit": UNIT, "cores": 1,
+                             "sample": f"{it1} further iterations on one thread, {el1:.1f} s"}
     if not acc_n or acc_phi is None:
         return base, {}
     s2, a2 = workload_inputs(acc_n, seed=0)
