@@ -749,8 +749,11 @@ def run_batch(args):
         lat = sorted(r.ms for r in rs) if mode.startswith("batched") else sorted(done_ms)
         out[mode] = {"ms": ms, "updates": upd, "value": upd / (ms / 1e3),
                      "converged": sum(r.status == fld.FLD_OK for r in rs),
+                     "per_solve_fields": ["edge", "status", "iterations", "rel_residual", "fp64_iterations",
+                                          "anderson_resets", "omega_backoffs"],
                      "per_solve": [[g.shape[0], fld.fld_status_string(r.status), r.iterations,
-                                    float("%.3g" % r.rel_residual)] for r, g in zip(rs, grids)]}
+                                    float("%.3g" % r.rel_residual), r.iterations_fp64, r.anderson_resets,
+                                    r.omega_backoffs] for r, g in zip(rs, grids)]}
         if lat:
             out[mode]["latency_ms_p50"] = float(np.percentile(lat, 50))
             out[mode]["latency_ms_p99"] = float(np.percentile(lat, 99))

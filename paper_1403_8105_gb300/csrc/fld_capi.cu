@@ -901,9 +901,10 @@ struct Controller {
     // solve keeps the same windows in iterations per voxel of its largest
     // edge, i.e. 2 n / check_every checks per constant (never fewer than the
     // constant), so a shorter check interval or a larger grid does not make it
-    // give up sooner.  An Anderson-mixed solve, which progresses many times
-    // faster per iteration, and the FP64 sweeps that end a MIXED solve keep
-    // the constants.
+    // give up sooner; so do the FP64 sweeps that end its MIXED solve, at their
+    // own check interval.  An Anderson-mixed solve, which progresses many
+    // times faster per iteration, keeps the constants until it falls back to
+    // plain sweeps.
     int stall_w = kStallChecks, switch_w = kSwitchChecks, slow_w = kSlowDivergeChecks, flat_w = kFlatWindow;
 
     void scale_windows(int n, int check_every) {
@@ -946,14 +947,16 @@ struct Controller {
     }
     // The float-float phase met tol on its single-precision-D residual and the
     // FP64 residual (rel) is above it: FP64 sweeps continue from here, with
-    // progress measured against that FP64 value.
-    void enter_fp64(double rel) {
+    // progress measured against that FP64 value (windows scaled to the FP64
+    // check interval on a grid of largest edge n when `scale`).
+    void enter_fp64(double rel, int n, bool scale) {
         fam = FAM_F64;
         best = rel;
         stall_w = kStallChecks;
         switch_w = kSwitchChecks;
         slow_w = kSlowDivergeChecks;
         flat_w = kFlatWindow;
+        if (scale) scale_windows(n, kPolishBlock);
         begin_phase();
     }
     // First check (before any iteration): the state is kept as the fallback of
@@ -1653,7 +1656,7 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
         res.rel_residual_single = rel;
         rel = r64;
         fam = FAM_F64;
-        ctl.enter_fp64(r64);
+        ctl.enter_fp64(r64, std::max(g->nx, std::max(g->ny, g->nz)), p->anderson <= 1);
         if (r64 <= p->tol) outcome = FLD_OK;
         return FLD_OK;
     };
@@ -1732,7 +1735,7 @@ fld_status solve_core(fld_grid g, const fld_solve_params *p, fld_solve_result *r
                 rel = ctl.best;
                 mix_off = true;
                 have_x = false;
-                if (fam != FAM_F64) ctl.scale_windows(std::max(g->nx, std::max(g->ny, g->nz)), ce);
+                ctl.scale_windows(std::max(g->nx, std::max(g->ny, g->nz)), check_len(fam, p->precision, ce));
                 ctl.backoffs = 0;   // a fresh omega back-off budget for the plain sweeps
                 ctl.begin_phase();
                 ++res.anderson_resets;
@@ -2145,7 +2148,7 @@ fld_status fld_server_add(fld_server s, fld_grid g, long long tag) {
         e.res.rel_residual_single = rel;
         e.res.rel_residual = rel = r64;
         e.fam = FAM_F64;
-        e.ctl.enter_fp64(r64);
+        e.ctl.enter_fp64(r64, std::max(g->nx, std::max(g->ny, g->nz)), p->anderson <= 1);
         if (r64 <= p->tol) {
             if ((st = sync_family(g, FAM_FF)) != FLD_OK) return st;
         } else {
@@ -2364,7 +2367,7 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
                     e.res.rel_residual_single = rel;
                     e.res.rel_residual = rel = r64;
                     e.fam = FAM_F64;
-                    e.ctl.enter_fp64(r64);
+                    e.ctl.enter_fp64(r64, std::max(g->nx, std::max(g->ny, g->nz)), e.am <= 1 || e.mix_off);
                     if (r64 <= p->tol) retire.push_back({i, {FLD_OK, rel}});
                 } else {
                     retire.push_back({i, {FLD_OK, rel}});
@@ -2382,7 +2385,8 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
                     e.res.rel_residual = rel = e.ctl.best;
                     e.mix_off = true;
                     e.have_x = false;
-                    if (e.fam != FAM_F64) e.ctl.scale_windows(std::max(g->nx, std::max(g->ny, g->nz)), e.ce);
+                    e.ctl.scale_windows(std::max(g->nx, std::max(g->ny, g->nz)),
+                                        check_len(e.fam, p->precision, e.ce));
                     e.ctl.backoffs = 0;
                     e.ctl.begin_phase();
                     ++e.res.anderson_resets;
