@@ -467,7 +467,9 @@ typedef struct {
  * compression of Sec. 6.2, or NULL (one of the two must be given).  `where`
  * (fld_mem) applies to both outputs; with host outputs the call returns when
  * they are written.  Keeps a 16-byte-per-voxel sampling volume with the
- * grid.  Errors: FLD_ERR_INVALID_ARG for a bad camera, exposure <= 0 or
+ * grid, and for host outputs a device staging image of 5 bytes per pixel,
+ * grown only for a larger image (a render loop allocates nothing after its
+ * first frame).  Errors: FLD_ERR_INVALID_ARG for a bad camera, exposure <= 0 or
  * gamma <= 0; FLD_ERR_STATE without a medium or a state. */
 fld_status fld_render(fld_grid g, fld_grid phi_grid, const fld_camera *cam, float *radiance, unsigned char *codes,
                       double exposure, double gamma, int where);

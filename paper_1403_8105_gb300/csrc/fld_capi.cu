@@ -116,6 +116,10 @@ struct fld_grid_s {
     TiledMaps maps[kTiledConfigs][2];    // [config][0: input in phi/D/phlo, 1: input in alt_*]
     bool maps_ok[kTiledConfigs] = {};
     bool tiled_used = false;             // blocked launches since the status was last read
+    // device staging of fld_render's host outputs (kept, grown on demand)
+    float *stage_rad = nullptr;
+    unsigned char *stage_cod = nullptr;
+    size_t stage_px = 0;
 };
 
 namespace {
@@ -1171,7 +1175,7 @@ void fld_destroy(fld_grid g) {
     if (g->evb0) cudaEventDestroy(g->evb0);
     if (g->evb1) cudaEventDestroy(g->evb1);
     void *snaps[] = {g->snap_phi, g->snap_lo, g->snap_D, g->snap_phi64, g->snap_D64, g->alt_phi, g->alt_D,
-                     g->alt_lo, g->tiled_status};
+                     g->alt_lo, g->tiled_status, g->stage_rad, g->stage_cod};
     for (void *p : snaps)
         if (p) cudaFree(p);
     free_anderson(g);
@@ -1296,15 +1300,29 @@ fld_status fld_render(fld_grid g, fld_grid phi_grid, const fld_camera *cam, floa
     const size_t npx = (size_t)cam->width * (size_t)cam->height;
     float *rad = radiance;
     unsigned char *cod = codes;
-    if (where != FLD_MEM_DEVICE) {   // device staging for host outputs
-        if (radiance && cudaMalloc((void **)&rad, sizeof(float) * npx) != cudaSuccess) rad = nullptr;
-        if (codes && cudaMalloc((void **)&cod, npx) != cudaSuccess) cod = nullptr;
-        if ((radiance && !rad) || (codes && !cod)) {
-            (void)cudaGetLastError();
-            if (rad && rad != radiance) cudaFree(rad);
-            if (cod && cod != codes) cudaFree(cod);
-            return fail(FLD_ERR_OOM, "cudaMalloc of the image staging buffers failed");
+    if (where != FLD_MEM_DEVICE) {
+        // device staging for host outputs: the grid keeps its buffers and
+        // grows them only for a larger image, so a render loop allocates
+        // nothing after its first frame
+        if (npx > g->stage_px) {
+            FLD_CK(cudaStreamSynchronize(g->stream));
+            if (g->stage_rad) cudaFree(g->stage_rad);
+            if (g->stage_cod) cudaFree(g->stage_cod);
+            g->stage_rad = nullptr;
+            g->stage_cod = nullptr;
+            g->stage_px = 0;
+            if (cudaMalloc((void **)&g->stage_rad, sizeof(float) * npx) != cudaSuccess ||
+                cudaMalloc((void **)&g->stage_cod, npx) != cudaSuccess) {
+                (void)cudaGetLastError();
+                if (g->stage_rad) cudaFree(g->stage_rad);
+                g->stage_rad = nullptr;
+                g->stage_cod = nullptr;
+                return fail(FLD_ERR_OOM, "cudaMalloc of the image staging buffers failed");
+            }
+            g->stage_px = npx;
         }
+        rad = radiance ? g->stage_rad : nullptr;
+        cod = codes ? g->stage_cod : nullptr;
     }
     PhiSource ps;
     const bool use_f = pg->valid_float;
@@ -1322,10 +1340,6 @@ fld_status fld_render(fld_grid g, fld_grid phi_grid, const fld_camera *cam, floa
         if (radiance) e = cudaMemcpyAsync(radiance, rad, sizeof(float) * npx, cudaMemcpyDeviceToHost, g->stream);
         if (e == cudaSuccess && codes) e = cudaMemcpyAsync(codes, cod, npx, cudaMemcpyDeviceToHost, g->stream);
         if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
-    }
-    if (where != FLD_MEM_DEVICE) {
-        if (radiance) cudaFree(rad);
-        if (codes) cudaFree(cod);
     }
     if (e != cudaSuccess) return cuda_fail(e, "fld_render");
     return FLD_OK;

@@ -143,3 +143,28 @@ def test_downsample_rejects_mismatched_grids():
             with pytest.raises(fld.FldError) as e:
                 g.downsample_to(other, 4)
             assert e.value.status == fld.FLD_ERR_INVALID_ARG
+
+
+def test_host_render_loop_allocates_nothing_after_the_first_frame():
+    # host outputs go through the grid's own staging image, grown only for a
+    # larger image: repeated frames give the same pixels and leave the free
+    # device memory as it was after the first frame
+    g, sig, alb, h, q, phi = solved_cloud(16, 3)
+    kw = dict(eye=(0.5, 0.5, -1.5), target=(0.5, 0.5, 0.5), up=(0.0, 1.0, 0.0), fov_deg=40.0, width=48, height=40,
+              step=0.5 * h, background=0.2, t_min=1e-6)
+    try:
+        cam = fld.camera(**kw)
+        small = fld.camera(**{**kw, "width": 20, "height": 12})
+        rad0, cod0 = g.render(cam, exposure=2.0, codes=True)
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(4):
+            rad, cod = g.render(cam, exposure=2.0, codes=True)
+            assert np.array_equal(rad, rad0) and np.array_equal(cod, cod0)
+            g.render(small, exposure=2.0)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        want = oracle.render(sig, alb, q, phi, h, **kw)
+        assert np.abs(rad0 - want).max() <= 2e-5 * np.abs(want).max()
+    finally:
+        g.close()
