@@ -93,9 +93,13 @@ def test_noalloc_allocates_nothing_and_runs_on_a_given_stream():
     rel = ctypes.c_double(-1.0)
     assert fn(nx, ny, nz, h, ctypes.byref(p), *args, ctypes.byref(rel), None) == fld.FLD_OK
     first = rel.value
+    # the test's own stream is made (and used once) before the measurement:
+    # torch's first stream request sets up its stream pool, which takes
+    # device memory of its own
+    side = torch.cuda.Stream(device=dev)
+    assert fn(nx, ny, nz, h, ctypes.byref(p), *args, ctypes.byref(rel), ctypes.c_void_p(side.cuda_stream)) == fld.FLD_OK
     torch.cuda.synchronize()
     free0, _ = torch.cuda.mem_get_info(dev)
-    side = torch.cuda.Stream(device=dev)
     for k in range(6):
         rel = ctypes.c_double(-1.0)
         stream = ctypes.c_void_p(side.cuda_stream) if k % 2 else None
