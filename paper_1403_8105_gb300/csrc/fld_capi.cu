@@ -2216,7 +2216,7 @@ fld_status fld_server_step(fld_server s, long long *tags, fld_solve_result *resu
         // multi-grid launches: grids in FP32 / hi-lo red-black sweeps grouped
         // by block length; each group of two grids or more is split into
         // tables (at most kFuseSlots in all, two grids or more each, balanced
-        // by work items) that run on different streams, so the passes of one
+        // by voxels) that run on different streams, so the passes of one
         // table overlap the tails of another's; the rest run grid by grid
         std::vector<int> slot_of(n, -1);
         std::vector<std::pair<int, std::vector<size_t>>> groups;   // (block length, grids) per table
