@@ -329,10 +329,13 @@ def upsample(phi_c: np.ndarray, fine_shape, h: float, factor: int = 4) -> np.nda
     return out
 
 
-def tonemap(radiance: np.ndarray, exposure: float = 1.0, gamma: float = 2.2) -> np.ndarray:
-    """Gamma compression to 8 bits (Sec. 6.2): round(255 clamp((e L)^(1/gamma), 0, 1))."""
-    v = np.clip(exposure * np.asarray(radiance, dtype=np.float64), 0.0, None) ** (1.0 / gamma)
-    return np.floor(255.0 * np.clip(v, 0.0, 1.0) + 0.5).astype(np.uint8)
+def tonemap(radiance: np.ndarray, exposure: float = 1.0, gamma: float = 2.2, dtype=np.float64) -> np.ndarray:
+    """Gamma compression to 8 bits (Sec. 6.2): round(255 clamp((e L)^(1/gamma), 0, 1)).
+    dtype: the precision the rounding decision is taken in (the paper fixes
+    none; comparisons with the GPU's codes take it in float32, the kernel's)."""
+    t = np.dtype(dtype).type
+    v = np.clip(t(exposure) * np.asarray(radiance, dtype=dtype), t(0.0), None) ** t(1.0 / gamma)
+    return np.floor(t(255.0) * np.clip(v, t(0.0), t(1.0)) + t(0.5)).astype(np.uint8)
 
 
 def residual(p: Problem, phi: np.ndarray | None = None, margin: int = 0, field: bool = False):

@@ -113,6 +113,6 @@ def test_render_at_full_size_matches_oracle_pixels(c2):
     assert (np.abs(rad - cam["background"]) > 0.01 * cam["background"]).mean() > 0.05
     # tone map at the sampled pixels: the oracle's codes of its own radiance
     # (+-1 where the two radiances straddle a half-integer code boundary)
-    mine = oracle.tonemap(want, exposure=2.0)
+    mine = oracle.tonemap(want, exposure=2.0, dtype=np.float32)
     got_codes = np.array([codes[y, x] for x, y in pix])
     assert np.abs(mine.astype(int) - got_codes.astype(int)).max() <= 1

@@ -82,7 +82,7 @@ def test_device_outputs_codes_and_errors():
         # the two radiances straddle a half-integer code boundary
         want = oracle.render(sig, alb, q, phi, h, eye=(0.5, 0.5, -1.5), target=(0.5, 0.5, 0.5), width=33,
                              height=17, background=0.1)
-        mine = oracle.tonemap(want, exposure=3.0, gamma=2.2)
+        mine = oracle.tonemap(want, exposure=3.0, gamma=2.2, dtype=np.float32)
         assert np.abs(mine.astype(int) - codes.astype(int)).max() <= 1
         for bad in (dict(width=0), dict(fov_deg=180.0), dict(eye=(0.5, 0.5, 0.5)), dict(up=(0.0, 0.0, 1.0))):
             kw = dict(eye=(0.5, 0.5, -1.5), target=(0.5, 0.5, 0.5), width=8, height=8)

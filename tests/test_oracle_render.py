@@ -117,3 +117,7 @@ def test_tonemap_codes():
     L = np.array([0.0, 1.0, 4.0, 0.5 ** 2.2, -1.0])
     np.testing.assert_array_equal(oracle.tonemap(L), [0, 255, 255, 128, 0])
     np.testing.assert_array_equal(oracle.tonemap(np.array([0.25]), exposure=4.0, gamma=1.0), [255])
+    # the same codes with the decision taken in single precision
+    np.testing.assert_array_equal(oracle.tonemap(L, dtype=np.float32), [0, 255, 255, 128, 0])
+    np.testing.assert_array_equal(oracle.tonemap(np.array([0.25]), exposure=4.0, gamma=1.0, dtype=np.float32),
+                                  [255])
