@@ -1077,6 +1077,7 @@ const char *fld_status_string(fld_status s) {
     case FLD_ERR_NOT_CONVERGED: return "FLD_ERR_NOT_CONVERGED";
     case FLD_ERR_DIVERGED: return "FLD_ERR_DIVERGED";
     case FLD_ERR_NO_DEVICE: return "FLD_ERR_NO_DEVICE";
+    case FLD_ERR_TIMEOUT: return "FLD_ERR_TIMEOUT";
     }
     return "FLD_ERR_UNKNOWN";
 }

@@ -48,6 +48,12 @@ def test_default_params_and_status_strings():
     assert p.anderson == 0 and p.nested == 0          # plain red-black SOR from the paper's start
     assert fld.fld_status_string(fld.FLD_ERR_DIVERGED) == "FLD_ERR_DIVERGED"
     assert fld.fld_status_string(99) == "FLD_ERR_UNKNOWN"
+    # every status the header declares has its own name
+    header = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "fld.h")).read()
+    codes = {name: int(v) for name, v in re.findall(r"\b(FLD_(?:OK|ERR_\w+))\s*=\s*(\d+)", header)}
+    assert len(codes) >= 9
+    for name, v in codes.items():
+        assert fld.fld_status_string(v) == name
 
 
 def test_struct_layout_matches_header():
