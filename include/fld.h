@@ -163,7 +163,8 @@ typedef struct {
                              the start removes the smooth error SOR is slowest
                              on.  Coarse edges stay >= 8.  0 (default): the
                              paper's initial state.  Not in the paper.        */
-    int anderson;         /* fld_solve only: Anderson mixing over the last
+    int anderson;         /* fld_solve, fld_solve_batch and fld_server (per
+                             grid): Anderson mixing over the last
                              `anderson` blocks (at most 16; 1 mixes nothing) of
                              check_every sweeps.
                              Each block of red-black sweeps (Algorithm 1) is a
@@ -185,9 +186,10 @@ typedef struct {
                              modes near -1 the mix amplifies, diverged on the
                              oracle).  0 (default): plain red-black SOR.  Not
                              in the paper.                                     */
-    int fp64_verify;      /* MIXED only.  1 (default): once the float-float sweeps
-                             bring the residual (D evaluated in single precision)
-                             to tol, the state is converted to FP64 and the stop
+    int fp64_verify;      /* MIXED only.  1 (default): once the single-precision
+                             sweeps (FP32, hi/lo or float-float) bring the
+                             residual (D evaluated in single precision) to tol,
+                             the state is converted to FP64 and the stop
                              test of Algorithm 1 is taken on the residual of
                              Eq. 37 evaluated entirely in FP64 (D recomputed from
                              phi in double).  If that residual is still above tol
