@@ -345,7 +345,7 @@ fld_status fld_solve(fld_grid g, const fld_solve_params *p, fld_solve_result *r)
  * they converge.  Each grid follows
  * exactly the decisions fld_solve would take for it alone (same omega, check
  * schedule, precision switch and safeguard), so its result equals its solo
- * solve.  Precision FP32 or MIXED (FP64: FLD_ERR_INVALID_ARG).  All grids must
+ * solve.  Precision FP32, MIXED or PAIR (FP64: FLD_ERR_INVALID_ARG).  All grids must
  * live on one device and be distinct; the batch runs on grids[0]'s stream after
  * every grid's prior work finished.  results (may be NULL) receives count
  * entries; there `ms` is the time from the start of the batch to the check at
@@ -357,11 +357,14 @@ fld_status fld_solve_batch(fld_grid *grids, int count, const fld_solve_params *p
 /* ---------------------------------------------------------------------------
  * Server: continuous batching of independent solves (not a paper item).
  * A server holds a changing set of grids being solved with one set of
- * parameters (FP32 or MIXED).  fld_server_add admits a grid (medium and
- * source already set): it is initialised, its first residual evaluated, and it
- * joins the next step.  Each fld_server_step runs one block of p->check_every
- * iterations for every active grid -- each grid replays its own block graph
- * on a stream of a pool of 16, so grids run concurrently -- then evaluates the
+ * parameters (FP32, MIXED or PAIR).  fld_server_add admits a grid (medium
+ * and source already set): it is initialised, its first residual evaluated,
+ * and it joins the next step.  Each fld_server_step runs one block of
+ * p->check_every iterations (the grid's tuned interval when it is 0) for every
+ * active grid -- each grid replays its own block graph on a stream of a pool
+ * of 16, so grids run concurrently, or with p->batch_launch = 1 grids in the
+ * same single-precision family and block length share multi-grid launches --
+ * then evaluates the
  * residuals of all active grids in one batched reduction and applies each
  * grid's own decisions (tolerance, precision switch, safeguard), exactly as
  * fld_solve would for that grid alone; finished grids leave the set and are
