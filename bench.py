@@ -725,6 +725,10 @@ def run_batch(args):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     out = {}
     modes = tuple(m for m in args.batch_modes.split(",") if m)
+    known = ("sequential", "batched", "batched_multi", "sequential_anderson", "batched_anderson",
+             "batched_anderson_multi")
+    if not modes or any(m not in known for m in modes):
+        raise SystemExit(f"--batch-modes: choose from {', '.join(known)}")
     for mode in modes:
         grids = setup()
         pm = pa if "anderson" in mode else p
