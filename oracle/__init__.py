@@ -456,3 +456,126 @@ def flux_magnitude(p: Problem, phi: np.ndarray | None = None) -> np.ndarray:
     E = np.empty((p.nz, p.ny, p.nx), dtype=np.float64)
     lib.fldo_flux(ctypes.byref(c), _d(p.sp), _d(ph), _d(E))
     return E
+
+
+# --------------------------------------------------------------------------
+# Picard iteration with an aggregation-multigrid linear solver: a reference
+# solver for the nonlinear-multigrid direction (not in the paper; the paper
+# names multigrid only as future work).  Test infrastructure like the rest.
+# --------------------------------------------------------------------------
+
+def fresh_D_field(p: Problem, phi: np.ndarray) -> np.ndarray:
+    """D = F(R(phi))/sigma' at every unknown from phi (Eq. 33-35), ghost D as
+    in p.D: the D^k of one Jacobi iteration (`fldo_jacobi_iteration`), taken
+    on a copy of the state."""
+    q = dataclasses.replace(p, phi=np.array(phi, dtype=np.float64), D=p.D.copy(), omega=1.0)
+    jacobi_iteration(q, 1)
+    return q.D
+
+
+def lagged_system(p: Problem, D: np.ndarray):
+    """Eq. 31 with D frozen: A phi = b over the unknowns (x fastest), with
+    D_ps = (D_p + D_s)/2, A_pp = sigma_a' h^2 + sum_s D_ps, A_ps = -D_ps for
+    unknown neighbours, and the Dirichlet ghosts' D_ps phi_s moved into b = j h^2 + ...
+    Returns (A as scipy CSR, b)."""
+    import scipy.sparse as sps
+    nz, ny, nx = p.nz, p.ny, p.nx
+    h2 = p.h * p.h
+    n = nx * ny * nz
+    idx = np.arange(n).reshape(nz, ny, nx)
+    Dp = D[1:-1, 1:-1, 1:-1]
+    diag = (p.sa * h2).ravel().copy()
+    b = (p.j * h2).ravel().copy()
+    rows, cols, vals = [idx.ravel()], [idx.ravel()], []
+    k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    off = []
+    for dz, dy, dx in ((0, 0, -1), (0, 0, 1), (0, -1, 0), (0, 1, 0), (-1, 0, 0), (1, 0, 0)):
+        Dn = D[1 + dz:1 + dz + nz, 1 + dy:1 + dy + ny, 1 + dx:1 + dx + nx]
+        Dps = 0.5 * (Dp + Dn)
+        diag += Dps.ravel()
+        kk, jj, ii = k + dz, j + dy, i + dx
+        inside = (kk >= 0) & (kk < nz) & (jj >= 0) & (jj < ny) & (ii >= 0) & (ii < nx)
+        rows.append(idx[inside])
+        cols.append((kk[inside] * ny + jj[inside]) * nx + ii[inside])
+        off.append(-Dps[inside])
+        ghost_phi = p.phi[1 + dz:1 + dz + nz, 1 + dy:1 + dy + ny, 1 + dx:1 + dx + nx]
+        np.add.at(b, idx[~inside], (Dps * ghost_phi)[~inside])
+    vals = [diag] + off
+    A = sps.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(n, n))
+    return A, b
+
+
+class AggregationMG:
+    """V-cycle over Galerkin coarse operators P^T A P of 2x2x2 aggregates
+    (piecewise-constant P, so the coarse operators follow the fine
+    coefficients across their jumps), damped-Jacobi smoothing (2 + 2 sweeps,
+    weight 2/3) and a direct solve on the coarsest level; symmetric, so it
+    preconditions CG."""
+
+    def __init__(self, A, shape, coarsest: int = 2000):
+        import scipy.sparse as sps
+        import scipy.sparse.linalg as spla
+        self.A, self.P = [A.tocsr()], []
+        while self.A[-1].shape[0] > coarsest and min(shape) > 1:
+            nz, ny, nx = shape
+            cz, cy, cx = (nz + 1) // 2, (ny + 1) // 2, (nx + 1) // 2
+            k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+            agg = (((k // 2) * cy + j // 2) * cx + i // 2).ravel()
+            P = sps.csr_matrix((np.ones(agg.size), (np.arange(agg.size), agg)), shape=(agg.size, cz * cy * cx))
+            self.P.append(P)
+            self.A.append((P.T @ self.A[-1] @ P).tocsr())
+            shape = (cz, cy, cx)
+        self.dinv = [1.0 / M.diagonal() for M in self.A]
+        self.lu = spla.splu(self.A[-1].tocsc())
+
+    def vcycle(self, b, level: int = 0):
+        if level == len(self.A) - 1:
+            return self.lu.solve(b)
+        A, dinv = self.A[level], self.dinv[level]
+        x = np.zeros_like(b)
+        for _ in range(2):
+            x = x + (2.0 / 3.0) * dinv * (b - A @ x)
+        x = x + self.P[level] @ self.vcycle(self.P[level].T @ (b - A @ x), level + 1)
+        for _ in range(2):
+            x = x + (2.0 / 3.0) * dinv * (b - A @ x)
+        return x
+
+
+def solve_picard_mg(p: Problem, tol: float, m: int = 5, inner_tol: float = 1e-4, max_steps: int = 400):
+    """The fixed point of Eq. 31 by Picard steps -- D from the current phi,
+    then the linear system with that D (`lagged_system`) solved by CG
+    preconditioned with one `AggregationMG` V-cycle to `inner_tol` relative
+    -- with Anderson mixing of the last m steps.  Stops when the fresh-D
+    residual of Eq. 37 is <= tol (the definition `solve` uses).  Returns
+    (picard_steps, cg_iterations, rel)."""
+    import scipy.sparse.linalg as spla
+    inner = (slice(1, -1),) * 3
+    shape = (p.nz, p.ny, p.nx)
+    x = p.phi[inner].copy()
+    G, F = [], []
+    cg_its = 0
+    for step in range(1, max_steps + 1):
+        A, b = lagged_system(p, fresh_D_field(p, p.phi))
+        mg = AggregationMG(A, shape)
+        count = [0]
+        M = spla.LinearOperator(A.shape, matvec=mg.vcycle)
+        r0 = float(np.linalg.norm(b - A @ x.ravel()))
+        g, _ = spla.cg(A, b, x0=x.ravel(), rtol=0.0, atol=inner_tol * r0, maxiter=500, M=M,
+                       callback=lambda _xk: count.__setitem__(0, count[0] + 1))
+        cg_its += count[0]
+        g = g.reshape(shape)
+        G.append(g)
+        F.append(g - x)
+        G, F = G[-m:], F[-m:]
+        gram = np.array([[np.vdot(a, c) for c in F] for a in F])
+        if np.trace(gram) > 0.0:
+            y = np.linalg.solve(gram + 1e-12 * np.trace(gram) / len(F) * np.eye(len(F)), np.ones(len(F)))
+            a = y / y.sum()
+            x = sum(ai * gi for ai, gi in zip(a, G))
+        else:
+            x = g
+        p.phi[inner] = x
+        rel = residual(p)[0]
+        if rel <= tol:
+            return step, cg_its, rel
+    return max_steps, cg_its, residual(p)[0]
