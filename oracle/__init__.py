@@ -579,3 +579,60 @@ def solve_picard_mg(p: Problem, tol: float, m: int = 5, inner_tol: float = 1e-4,
         if rel <= tol:
             return step, cg_its, rel
     return max_steps, cg_its, residual(p)[0]
+
+
+def solve_newton_mg(p: Problem, tol: float, start_tol: float = 1e-2, max_newton: int = 30):
+    """Newton's method on the residual of Eq. 37 (with D recomputed from phi),
+    started from `solve_picard_mg` to `start_tol`: each step solves J d = -R
+    by GMRES with Jacobian-vector products by forward differences of the
+    residual field (`residual`) and one `AggregationMG` V-cycle of the lagged
+    operator (J ~ -A / h^2) as preconditioner, then backtracks on |R|.
+    Stops when the relative residual is <= tol.  Returns
+    (picard_steps, newton_steps, v_cycles, residual_evaluations, rel_history)."""
+    import scipy.sparse.linalg as spla
+    inner = (slice(1, -1),) * 3
+    shape = (p.nz, p.ny, p.nx)
+    pic, cg_its, rel = solve_picard_mg(p, start_tol)
+    counts = {"v": cg_its, "f": 0}
+    history = [rel]
+
+    def field(x):
+        ph = p.phi.copy()
+        ph[inner] = x.reshape(shape)
+        counts["f"] += 1
+        return residual(p, ph, field=True)[3].ravel()
+
+    x = p.phi[inner].ravel().copy()
+    for step in range(1, max_newton + 1):
+        if rel <= tol:
+            return pic, step - 1, counts["v"], counts["f"], history
+        R = field(x)
+        A, _ = lagged_system(p, fresh_D_field(p, p.phi))
+        mg = AggregationMG(A, shape)
+        scale = np.linalg.norm(x)
+
+        def jv(v):
+            nv = np.linalg.norm(v)
+            if nv == 0.0:
+                return np.zeros_like(v)
+            e = 1e-7 * (1.0 + scale) / nv
+            return (field(x + e * v) - R) / e
+
+        def pre(r):
+            counts["v"] += 1
+            return -p.h * p.h * mg.vcycle(r)
+
+        n = x.size
+        d, _ = spla.gmres(spla.LinearOperator((n, n), matvec=jv), -R, rtol=1e-2, restart=30, maxiter=3,
+                          M=spla.LinearOperator((n, n), matvec=pre))
+        r0, lam = np.linalg.norm(R), 1.0
+        while True:
+            xn = x + lam * d
+            if np.linalg.norm(field(xn)) < r0 or lam < 1e-3:
+                break
+            lam *= 0.5
+        x = xn
+        p.phi[inner] = x.reshape(shape)
+        rel = residual(p)[0]
+        history.append(rel)
+    return pic, max_newton, counts["v"], counts["f"], history

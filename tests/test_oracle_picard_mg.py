@@ -75,3 +75,19 @@ def test_aggregation_multigrid_preconditions_the_jumps():
         assert np.linalg.norm(b - A @ x) <= 1e-7 * np.linalg.norm(b)
         its[name] = count[0]
     assert its["mg"] * 3 < its["jacobi"], its
+
+
+def test_newton_with_multigrid_preconditioning_converges_fast_to_the_same_point():
+    # from Picard steps to rel. 1e-2, Newton steps (Jacobian-vector products
+    # by differences of the residual of Eq. 37, the V-cycle of the lagged
+    # operator as preconditioner) cut the residual at least tenfold per step
+    # and land on Algorithm 1's fixed point
+    sig, alb, q, h = _cloud((12, 12, 12), 3)
+    ref = _sor_fixed_point(sig, alb, q, h)
+    p = oracle.make_problem(sig, alb, q, h, limiter="lp", local_iters=2)
+    oracle.init_state(p)
+    pic, newton, vcycles, fevals, hist = oracle.solve_newton_mg(p, 1e-10)
+    assert hist[-1] <= 1e-10 and newton <= 6, hist
+    assert all(b <= 0.1 * a for a, b in zip(hist[1:], hist[2:])), hist
+    err = np.linalg.norm(p.phi[INNER] - ref.phi[INNER]) / np.linalg.norm(ref.phi[INNER])
+    assert err <= 1e-9, err
