@@ -507,12 +507,13 @@ def lagged_system(p: Problem, D: np.ndarray):
 
 class AggregationMG:
     """V-cycle over Galerkin coarse operators P^T A P of 2x2x2 aggregates
-    (piecewise-constant P, so the coarse operators follow the fine
-    coefficients across their jumps), damped-Jacobi smoothing (2 + 2 sweeps,
-    weight 2/3) and a direct solve on the coarsest level; symmetric, so it
-    preconditions CG."""
+    (P piecewise constant, or with `smooth` one damped-Jacobi step applied
+    to it -- smoothed aggregation; either way the coarse operators follow the
+    fine coefficients across their jumps), damped-Jacobi smoothing (2 + 2
+    sweeps, weight 2/3) and a direct solve on the coarsest level; symmetric,
+    so it preconditions CG."""
 
-    def __init__(self, A, shape, coarsest: int = 2000):
+    def __init__(self, A, shape, coarsest: int = 2000, smooth: bool = False):
         import scipy.sparse as sps
         import scipy.sparse.linalg as spla
         self.A, self.P = [A.tocsr()], []
@@ -522,6 +523,14 @@ class AggregationMG:
             k, j, i = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
             agg = (((k // 2) * cy + j // 2) * cx + i // 2).ravel()
             P = sps.csr_matrix((np.ones(agg.size), (np.arange(agg.size), agg)), shape=(agg.size, cz * cy * cx))
+            if smooth:
+                # smoothed aggregation: P = (I - w D^-1 A) P_tent, w = 4 / (3 rho(D^-1 A)),
+                # rho bounded by the largest absolute row sum of D^-1 A
+                Af = self.A[-1]
+                dinv = 1.0 / Af.diagonal()
+                DA = sps.diags(dinv) @ Af
+                rho = float(np.abs(DA).sum(axis=1).max())
+                P = (P - (4.0 / (3.0 * rho)) * (DA @ P)).tocsr()
             self.P.append(P)
             self.A.append((P.T @ self.A[-1] @ P).tocsr())
             shape = (cz, cy, cx)
@@ -541,7 +550,8 @@ class AggregationMG:
         return x
 
 
-def solve_picard_mg(p: Problem, tol: float, m: int = 5, inner_tol: float = 1e-4, max_steps: int = 400):
+def solve_picard_mg(p: Problem, tol: float, m: int = 5, inner_tol: float = 1e-4, max_steps: int = 400,
+                    smooth: bool = True):
     """The fixed point of Eq. 31 by Picard steps -- D from the current phi,
     then the linear system with that D (`lagged_system`) solved by CG
     preconditioned with one `AggregationMG` V-cycle to `inner_tol` relative
@@ -556,7 +566,7 @@ def solve_picard_mg(p: Problem, tol: float, m: int = 5, inner_tol: float = 1e-4,
     cg_its = 0
     for step in range(1, max_steps + 1):
         A, b = lagged_system(p, fresh_D_field(p, p.phi))
-        mg = AggregationMG(A, shape)
+        mg = AggregationMG(A, shape, smooth=smooth)
         count = [0]
         M = spla.LinearOperator(A.shape, matvec=mg.vcycle)
         r0 = float(np.linalg.norm(b - A @ x.ravel()))
@@ -581,7 +591,7 @@ def solve_picard_mg(p: Problem, tol: float, m: int = 5, inner_tol: float = 1e-4,
     return max_steps, cg_its, residual(p)[0]
 
 
-def solve_newton_mg(p: Problem, tol: float, start_tol: float = 1e-2, max_newton: int = 30):
+def solve_newton_mg(p: Problem, tol: float, start_tol: float = 1e-2, max_newton: int = 30, smooth: bool = True):
     """Newton's method on the residual of Eq. 37 (with D recomputed from phi),
     started from `solve_picard_mg` to `start_tol`: each step solves J d = -R
     by GMRES with Jacobian-vector products by forward differences of the
@@ -592,7 +602,7 @@ def solve_newton_mg(p: Problem, tol: float, start_tol: float = 1e-2, max_newton:
     import scipy.sparse.linalg as spla
     inner = (slice(1, -1),) * 3
     shape = (p.nz, p.ny, p.nx)
-    pic, cg_its, rel = solve_picard_mg(p, start_tol)
+    pic, cg_its, rel = solve_picard_mg(p, start_tol, smooth=smooth)
     counts = {"v": cg_its, "f": 0}
     history = [rel]
 
@@ -608,7 +618,7 @@ def solve_newton_mg(p: Problem, tol: float, start_tol: float = 1e-2, max_newton:
             return pic, step - 1, counts["v"], counts["f"], history
         R = field(x)
         A, _ = lagged_system(p, fresh_D_field(p, p.phi))
-        mg = AggregationMG(A, shape)
+        mg = AggregationMG(A, shape, smooth=smooth)
         scale = np.linalg.norm(x)
 
         def jv(v):
